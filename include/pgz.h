@@ -1,0 +1,187 @@
+/*
+ * pgz.h -- C ABI of libpgz: two-pass parallel gzip decompression on one GB300
+ * (sm_103a), after Kerbiriou & Chikhi, "Parallel decompression of
+ * gzip-compressed files and random access to DNA sequences" (arXiv 1905.07224).
+ *
+ * The method (Section "Full file decompression in two passes (pugz)"):
+ *   (a) the compressed stream of a gzip member is cut into parts of equal
+ *       compressed size; every part after the first finds the first DEFLATE
+ *       block start at or after its nominal offset by trial decoding at every
+ *       bit (Section "Detection of DEFLATE block start positions", Appendix
+ *       "DEFLATE block decompression checks");
+ *   (b) pass 1 decodes every part against a symbolic context
+ *       [U_0 .. U_32767]: back-references into the unknown 32 KiB before the
+ *       part stay as placeholders U_j;
+ *   (c) pass 2 resolves the windows w_i (the last 32 KiB before part i) from
+ *       part to part and replaces every U_j by w_i[j]; the output is then
+ *       checked against the gzip trailer's CRC-32 and ISIZE (RFC 1952; the
+ *       paper's own implementation does not compute the CRC, Section
+ *       "Discussion").
+ *
+ * Conventions for every call:
+ *  - Pointers named "device" must point to memory of the context's device
+ *    (cudaMalloc / torch tensors); "host" pointers to host memory.  The
+ *    compressed input must be 4-byte aligned; otherwise PGZ_E_ARG.
+ *  - The caller owns every input and output buffer.  The context owns its
+ *    scratch memory, which grows on demand and is kept between calls.
+ *  - Work is issued on the context's CUDA stream (pgz_config.cuda_stream);
+ *    calls return after their final status has been read back, i.e. they
+ *    synchronise that stream once or twice.
+ *  - Return values are pgz_status codes; pgz_strerror() names them.  No call
+ *    aborts the process or faults the GPU on malformed input: every device
+ *    read is bounds-checked against the buffer sizes given here.
+ *  - The output of a successful call is byte-exact: identical to sequential
+ *    gunzip (Algorithm "DEFLATE decompression" applied from the stream start).
+ */
+#ifndef PGZ_H
+#define PGZ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pgz_status {
+    PGZ_OK = 0,
+    PGZ_E_ARG = 1,          /* bad argument (NULL, size, alignment, config) */
+    PGZ_E_HEADER = 2,       /* not an RFC 1952 member header */
+    PGZ_E_DATA = 3,         /* invalid or truncated DEFLATE data */
+    PGZ_E_CRC = 4,          /* CRC-32 of the output differs from the trailer */
+    PGZ_E_ISIZE = 5,        /* output length mod 2^32 differs from the trailer */
+    PGZ_E_CAPACITY = 6,     /* out_cap too small; *out_len holds the size needed */
+    PGZ_E_NOSYNC = 7,       /* no block start after the requested offset */
+    PGZ_E_UNSUPPORTED = 8,  /* data after the first member (multi-member gzip) */
+    PGZ_E_TIMEOUT = 9,      /* a bounded device wait gave up */
+    PGZ_E_CUDA = 10,        /* a CUDA runtime call failed */
+    PGZ_E_NOMEM = 11        /* scratch allocation failed or exceeds the budget */
+} pgz_status;
+
+typedef struct pgz_ctx pgz_ctx;
+
+typedef struct pgz_config {
+    int device;                 /* CUDA device ordinal */
+    void* cuda_stream;          /* cudaStream_t to issue work on; NULL = default stream */
+    uint64_t chunk_bytes;       /* compressed bytes per part; 0 = default (see pgz_config_init) */
+    int n_chunks;               /* > 0: exactly this many parts per file (overrides chunk_bytes) */
+    int threads_per_chunk;      /* threads decoding one part: 32 (one warp) is the only value */
+    uint8_t allowed[32];        /* literal bytes accepted at a block start, bit b of byte b/8 */
+    int confirm_blocks;         /* blocks after a block start that must also decode (5) */
+    uint32_t min_block;         /* a block start's block yields >= min_block bytes (1024) */
+    uint32_t max_block;         /* ... and < max_block bytes (4 MiB) */
+    uint64_t dev_mem_budget;    /* upper bound on scratch bytes; 0 = none */
+    uint64_t spin_cap;          /* reserved for bounded device waits; 0 = default */
+} pgz_config;
+
+/* per-call statistics; the ms_* fields are CUDA-event times of the stages */
+typedef struct pgz_stats {
+    uint64_t in_bytes, out_bytes;
+    uint64_t chunks;            /* parts planned */
+    uint64_t empty_chunks;      /* parts that held no accepted block start */
+    uint64_t false_syncs;       /* accepted block starts rejected by the chain check */
+    uint64_t retries;           /* re-runs (false start, confirmation, capacity) */
+    uint64_t placeholders;      /* placeholder symbols produced by pass 1 */
+    uint64_t symbols;           /* symbols produced by pass 1 (= out_bytes) */
+    float ms_sync, ms_inflate, ms_chain, ms_translate, ms_crc, ms_total;
+} pgz_stats;
+
+/* One entry of a batch: device pointers; results are written back. */
+typedef struct pgz_job {
+    const uint8_t* gz;          /* device: one gzip member */
+    uint64_t gz_len;
+    uint8_t* out;               /* device: output buffer */
+    uint64_t out_cap;
+    uint64_t out_len;           /* result: bytes written (or needed, with PGZ_E_CAPACITY) */
+    int status;                 /* result: pgz_status of this job */
+} pgz_job;
+
+typedef struct pgz_index pgz_index;
+typedef struct pgz_batch pgz_batch;
+
+/* Defaults: device 0, default stream, 1024 parts of the member's compressed
+   data (the part count of the paper's setting is a free parameter, Section
+   "Full file decompression in two passes"), ASCII bytes 9, 10, 13, 32..126
+   (reading of the Appendix's "valid ASCII characters"), confirm_blocks 5
+   (Section "Detection of DEFLATE block start positions"), block bounds
+   1 KiB .. 4 MiB (Appendix "DEFLATE block decompression checks"). */
+void pgz_config_init(pgz_config* cfg);
+
+/* Creates a context on cfg->device.  *out receives it; PGZ_E_ARG for a bad
+   config, PGZ_E_CUDA if the device cannot be used. */
+int pgz_create(pgz_ctx** out, const pgz_config* cfg);
+void pgz_destroy(pgz_ctx* ctx);
+
+/* Exact decompression of one whole gzip member (Section "Full file
+   decompression in two passes (pugz)"; the result is that of Algorithm
+   "DEFLATE decompression" from the stream start).
+   gz [device, gz_len bytes]: the gzip file; out [device, out_cap bytes].
+   *out_len: bytes written; with PGZ_E_CAPACITY the bytes needed.
+   st (nullable): statistics of this call. */
+int pgz_decompress(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len,
+                   uint8_t* out, uint64_t out_cap, uint64_t* out_len, pgz_stats* st);
+
+/* The same with HOST buffers: the input is copied to the device and the
+   output back to `out`, both inside the call. */
+int pgz_decompress_host(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len,
+                        uint8_t* out, uint64_t out_cap, uint64_t* out_len, pgz_stats* st);
+
+/* Problem "Random access in DEFLATE stream" (Section "Feasibility of random
+   access"): from compressed BIT offset start_bit of a gzip member, find the
+   first accepted block start b >= start_bit (Section "Detection of DEFLATE
+   block start positions"; if start_bit is at or before the first block, b is
+   the first block and the context is known to be empty), then decode from b
+   to the end of the member against the symbolic context.
+   sym_out [device, nullable, out_cap u16]: symbols, 0x00..0xFF a byte,
+     0x8000|j the placeholder U_j of the 32 KiB before b;
+   byte_out [device, nullable, out_cap bytes]: the same with every U_j
+     replaced by `fill` (the undetermined '?' context of Section
+     "Undetermined context propagation technique");
+   *out_len: symbols decoded; *block_bit: b; *first_determined: one past the
+   last placeholder (0 if none).  PGZ_E_NOSYNC if no block start follows. */
+int pgz_decompress_at(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, uint64_t start_bit,
+                      uint16_t* sym_out, uint8_t* byte_out, uint8_t fill, uint64_t out_cap,
+                      uint64_t* out_len, uint64_t* block_bit, uint64_t* first_determined);
+
+/* Many independent gzip members decoded together: every stage is one launch
+   over the parts of all jobs.  jobs [host array of n]; their gz/out are device
+   pointers.  Returns PGZ_OK if every job succeeded, else the first failing
+   job's status; each job's own status and out_len are filled in. */
+int pgz_decompress_batch(pgz_ctx* ctx, int n, pgz_job* jobs, pgz_stats* st);
+
+/* A batch planned once and replayed as one CUDA graph: pgz_batch_prepare
+   reads the jobs' headers, sizes the scratch and captures the stage
+   launches; pgz_batch_run replays them on the context's stream and reads the
+   results back into `jobs` (same inputs as at prepare time, which the caller
+   must keep alive); pgz_batch_free releases the plan's scratch. */
+int pgz_batch_prepare(pgz_ctx* ctx, int n, const pgz_job* jobs, pgz_batch** out);
+int pgz_batch_run(pgz_batch* b, pgz_job* jobs, pgz_stats* st);
+void pgz_batch_free(pgz_batch* b);
+
+/* A resident random-access index of one member (the per-part block start,
+   decompressed offset and resolved 32 KiB window w_i of pass 2): built by a
+   full decompression, then pgz_decompress_range decodes only the parts that
+   cover [d_off, d_off + len) of the decompressed stream into out [device].
+   gz must stay valid and unchanged while the index is used. */
+int pgz_index_build(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, pgz_index** idx);
+int pgz_index_info(const pgz_index* idx, uint64_t* total_out, uint64_t* nparts);
+int pgz_decompress_range(pgz_ctx* ctx, const pgz_index* idx, uint64_t d_off, uint64_t len, uint8_t* out);
+void pgz_index_free(pgz_index* idx);
+
+/* Inspection of the last pgz_decompress / pgz_decompress_at call on ctx, for
+   tests: per part i < n the start bit (UINT64_MAX if empty), the symbol count
+   of pass 1, the placeholder count, and the pass-1 symbols / the window w_i
+   (copied to HOST buffers).  PGZ_E_ARG if i is out of range. */
+int pgz_inspect_parts(pgz_ctx* ctx, int n, uint64_t* start_bit, uint64_t* nsym,
+                      uint64_t* nph, int* nparts);
+int pgz_inspect_symbols(pgz_ctx* ctx, int part, uint16_t* host_dst, uint64_t cap, uint64_t* nsym);
+int pgz_inspect_window(pgz_ctx* ctx, int part, uint8_t* host_dst /* 32768 bytes */);
+
+/* Number of kernels this library launched on ctx since it was created. */
+uint64_t pgz_kernel_launches(const pgz_ctx* ctx);
+
+const char* pgz_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PGZ_H */

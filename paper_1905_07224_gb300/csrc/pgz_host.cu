@@ -1,0 +1,1014 @@
+// pgz_host.cu -- the C ABI of libpgz (include/pgz.h): gzip header parsing,
+// part planning, the launch sequence of the two passes, recovery from false
+// block starts, batches replayed as CUDA graphs, and the random-access index.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "pgz_internal.h"
+#include "../../include/pgz.h"
+
+using namespace pgz;
+
+namespace {
+
+constexpr uint64_t kSegBytes = 4096;
+constexpr int kMaxRetries = 32;
+
+struct DBuf {
+    void* p = nullptr;
+    size_t n = 0;
+    cudaError_t ensure(size_t bytes) {
+        if (bytes == 0) bytes = 16;
+        if (bytes <= n) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e == cudaSuccess) n = bytes;
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    template <class T>
+    T* as() const {
+        return static_cast<T*>(p);
+    }
+};
+
+struct PBuf {   // pinned host staging
+    void* p = nullptr;
+    size_t n = 0;
+    cudaError_t ensure(size_t bytes) {
+        if (bytes == 0) bytes = 16;
+        if (bytes <= n) return cudaSuccess;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        n = 0;
+        cudaError_t e = cudaMallocHost(&p, bytes);
+        if (e == cudaSuccess) n = bytes;
+        return e;
+    }
+    void release() {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        n = 0;
+    }
+    template <class T>
+    T* as() const {
+        return static_cast<T*>(p);
+    }
+};
+
+// CRC-32 of RFC 1952 section 8 (host; used for the optional header CRC only)
+uint32_t host_crc32(const uint8_t* p, size_t n) {
+    uint32_t c = 0xffffffffu;
+    for (size_t i = 0; i < n; ++i) {
+        c ^= p[i];
+        for (int k = 0; k < 8; ++k) c = (c & 1u) ? (c >> 1) ^ 0xEDB88320u : (c >> 1);
+    }
+    return ~c;
+}
+
+// RFC 1952 2.3 member header.  Returns PGZ_OK and the offset of the DEFLATE
+// data, PGZ_E_HEADER, or -1 if the header runs past the hlen bytes given.
+int parse_header(const uint8_t* h, uint64_t hlen, uint64_t gz_len, uint64_t* s0) {
+    if (gz_len < 18 || hlen < 10) return PGZ_E_HEADER;
+    if (h[0] != 0x1f || h[1] != 0x8b || h[2] != 8 || (h[3] & 0xe0)) return PGZ_E_HEADER;
+    const uint8_t flg = h[3];
+    uint64_t pos = 10;
+    if (flg & 4) {
+        if (pos + 2 > hlen) return -1;
+        pos += 2 + (h[pos] | ((uint64_t)h[pos + 1] << 8));
+    }
+    for (int f = 8; f <= 16; f <<= 1) {
+        if (flg & f) {
+            while (pos < hlen && h[pos]) ++pos;
+            if (pos >= hlen) return hlen < gz_len ? -1 : PGZ_E_HEADER;
+            ++pos;
+        }
+    }
+    if (flg & 2) {
+        if (pos + 2 > hlen) return -1;
+        const uint32_t c = host_crc32(h, pos) & 0xffffu;
+        if (c != (h[pos] | ((uint32_t)h[pos + 1] << 8))) return PGZ_E_HEADER;
+        pos += 2;
+    }
+    if (pos > hlen) return -1;
+    if (pos + 8 > gz_len) return PGZ_E_HEADER;
+    *s0 = pos;
+    return PGZ_OK;
+}
+
+struct MemberInfo {
+    uint64_t s0;
+    uint32_t crc, isize;
+};
+
+// a planned set of members and their parts, with device buffers
+struct Plan {
+    std::vector<FileDesc> files;
+    std::vector<ChunkDesc> chunks;
+    std::vector<int32_t> g0, gn, gfile;
+    std::vector<uint64_t> seg0;
+    uint64_t sym_total = 0, max_cap = 0, total_seg = 0;
+    bool chain = true, translate = true, crc = true;
+    bool results_valid = false;   // the device chunk array holds the last run's results
+    const uint8_t* fill = nullptr;   // device window of fill bytes (mode 1)
+    DBuf d_files, d_chunks, d_g0, d_gn, d_gfile, d_seg0, d_sym, d_windows, d_gmaps, d_wstart;
+    PBuf h_files, h_chunks;
+    cudaGraphExec_t graph = nullptr;
+    void release() {
+        d_files.release();
+        d_chunks.release();
+        d_g0.release();
+        d_gn.release();
+        d_gfile.release();
+        d_seg0.release();
+        d_sym.release();
+        d_windows.release();
+        d_gmaps.release();
+        d_wstart.release();
+        h_files.release();
+        h_chunks.release();
+        if (graph) cudaGraphExecDestroy(graph);
+        graph = nullptr;
+    }
+};
+
+}  // namespace
+
+struct pgz_ctx {
+    pgz_config cfg;
+    KParams kp;
+    cudaStream_t stream = nullptr;
+    Plan plan;                 // the last call's plan (kept for inspection)
+    PBuf hdr;                  // header / trailer staging
+    DBuf in_buf, out_buf, fill_buf;
+    uint64_t launches = 0;
+    cudaEvent_t ev[8] = {};
+};
+
+struct pgz_batch {
+    pgz_ctx* ctx;
+    Plan plan;
+    std::vector<pgz_job> jobs;
+};
+
+struct pgz_index {
+    const uint8_t* gz;
+    uint64_t gz_len;
+    uint64_t total;
+    std::vector<uint64_t> sync, off, n, stop;   // per non-empty part
+    std::vector<MemberInfo> info;
+    DBuf windows;                                // resolved w_i, 32 KiB each
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? PGZ_OK : (e == cudaErrorMemoryAllocation ? PGZ_E_NOMEM : PGZ_E_CUDA); }
+
+uint64_t round_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+// header and trailer of a member in device memory
+int read_member(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, MemberInfo* mi) {
+    if (gz_len < 18) return PGZ_E_HEADER;
+    uint64_t want = std::min<uint64_t>(gz_len, 4096);
+    for (;;) {
+        if (cuda_status(ctx->hdr.ensure(want + 8))) return PGZ_E_NOMEM;
+        uint8_t* h = ctx->hdr.as<uint8_t>();
+        if (cudaMemcpyAsync(h, gz, want, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess) return PGZ_E_CUDA;
+        if (cudaMemcpyAsync(h + want, gz + gz_len - 8, 8, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+            return PGZ_E_CUDA;
+        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return PGZ_E_CUDA;
+        uint64_t s0 = 0;
+        const int r = parse_header(h, want, gz_len, &s0);
+        if (r == -1 && want < gz_len) {
+            want = std::min<uint64_t>(gz_len, want * 4);
+            continue;
+        }
+        if (r != PGZ_OK) return PGZ_E_HEADER;
+        const uint8_t* t = h + want;
+        mi->s0 = s0;
+        mi->crc = t[0] | ((uint32_t)t[1] << 8) | ((uint32_t)t[2] << 16) | ((uint32_t)t[3] << 24);
+        mi->isize = t[4] | ((uint32_t)t[5] << 8) | ((uint32_t)t[6] << 16) | ((uint32_t)t[7] << 24);
+        return PGZ_OK;
+    }
+}
+
+// parts of one member: equal compressed size (Section "Full file decompression
+// in two passes": n roughly equal parts)
+void plan_member(pgz_ctx* ctx, Plan& P, const uint8_t* gz, uint64_t gz_len, uint8_t* out, uint64_t out_cap,
+                 const MemberInfo& mi, uint32_t mode) {
+    FileDesc F{};
+    F.gz = gz;
+    F.gz_len = gz_len;
+    F.out = out;
+    F.out_cap = out_cap;
+    F.s0_bit = mi.s0 * 8;
+    F.end_bit = (gz_len - 8) * 8;
+    F.crc_expect = mi.crc;
+    F.isize_expect = mi.isize;
+    F.mode = mode;
+    F.out_hi = kNone;
+    const uint64_t csize = gz_len - 8 - mi.s0;
+    uint64_t n;
+    if (ctx->cfg.n_chunks > 0) n = (uint64_t)ctx->cfg.n_chunks;
+    else n = std::max<uint64_t>(1, (csize + ctx->cfg.chunk_bytes - 1) / ctx->cfg.chunk_bytes);
+    n = std::max<uint64_t>(1, std::min<uint64_t>(n, std::max<uint64_t>(1, csize / 64)));
+    const uint64_t per = (csize + n - 1) / n;
+    // symbols expected per part: ISIZE is exact below 4 GiB; 2x the compressed size bounds text otherwise
+    const uint64_t d_est = std::max<uint64_t>(mi.isize, 2 * csize);
+    const uint64_t cap = round_up(2 * d_est / n + 65536, 8);
+    F.chunk0 = (int32_t)P.chunks.size();
+    F.nchunks = (int32_t)n;
+    for (uint64_t i = 0; i < n; ++i) {
+        ChunkDesc C{};
+        C.lo = (mi.s0 + i * per) * 8;
+        C.hi = std::min<uint64_t>((mi.s0 + (i + 1) * per) * 8, F.end_bit);
+        C.file = (int32_t)P.files.size();
+        C.index = (int32_t)i;
+        C.disabled = (i > 0 && C.lo >= F.end_bit) ? 1u : 0u;
+        C.cap = cap;
+        C.stop_hint = kNone;
+        C.sync = kNone;
+        P.chunks.push_back(C);
+    }
+    // window-chain groups of about sqrt(n) parts
+    const uint64_t gsz = std::max<uint64_t>(1, (uint64_t)std::ceil(std::sqrt((double)n)));
+    F.group0 = (int32_t)P.g0.size();
+    F.ngroups = 0;
+    for (uint64_t a = 0; a < n; a += gsz) {
+        P.g0.push_back(F.chunk0 + (int32_t)a);
+        P.gn.push_back((int32_t)std::min<uint64_t>(gsz, n - a));
+        P.gfile.push_back((int32_t)P.files.size());
+        F.ngroups++;
+    }
+    P.files.push_back(F);
+}
+
+// symbol offsets, CRC segments, device buffers
+int layout(Plan& P) {
+    uint64_t base = 0, mx = 0;
+    for (auto& C : P.chunks) {
+        C.cap = round_up(C.cap, 8);
+        C.sym_base = base;
+        base += C.cap;
+        mx = std::max(mx, C.cap);
+    }
+    P.sym_total = base;
+    P.max_cap = mx;
+    P.seg0.clear();
+    uint64_t seg = 0;
+    for (auto& F : P.files) {
+        uint64_t cap_sum = 0;
+        for (int c = F.chunk0; c < F.chunk0 + F.nchunks; ++c) cap_sum += P.chunks[c].cap;
+        const uint64_t bound = std::min(F.out_cap, cap_sum);
+        F.seg0 = seg;
+        F.nseg = (bound + kSegBytes - 1) / kSegBytes;
+        P.seg0.push_back(seg);
+        seg += F.nseg;
+    }
+    P.total_seg = seg;
+    const size_t nf = P.files.size(), nc = P.chunks.size(), ng = P.g0.size();
+    cudaError_t e = cudaSuccess;
+    if (!e) e = P.d_files.ensure(nf * sizeof(FileDesc));
+    if (!e) e = P.d_chunks.ensure(nc * sizeof(ChunkDesc));
+    if (!e) e = P.d_g0.ensure(ng * sizeof(int32_t));
+    if (!e) e = P.d_gn.ensure(ng * sizeof(int32_t));
+    if (!e) e = P.d_gfile.ensure(ng * sizeof(int32_t));
+    if (!e) e = P.d_seg0.ensure(nf * sizeof(uint64_t));
+    if (!e) e = P.d_sym.ensure(P.sym_total * sizeof(uint16_t));
+    if (!e && P.chain) e = P.d_windows.ensure(nc * (size_t)kWin);
+    if (!e && P.chain) e = P.d_gmaps.ensure(ng * (size_t)kWin * sizeof(uint16_t));
+    if (!e && P.chain) e = P.d_wstart.ensure(ng * (size_t)kWin);
+    if (!e) e = P.h_files.ensure(nf * sizeof(FileDesc));
+    if (!e) e = P.h_chunks.ensure(nc * sizeof(ChunkDesc));
+    return cuda_status(e);
+}
+
+// the device-resident part of a run: uploads, every stage, result download
+// the plan's static arrays (pageable host memory: never inside a graph capture)
+void upload_static(Plan& P, cudaStream_t s) {
+    const size_t nf = P.files.size(), ng = P.g0.size();
+    cudaMemcpyAsync(P.d_g0.p, P.g0.data(), ng * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(P.d_gn.p, P.gn.data(), ng * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(P.d_gfile.p, P.gfile.data(), ng * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(P.d_seg0.p, P.seg0.data(), nf * sizeof(uint64_t), cudaMemcpyHostToDevice, s);
+}
+
+int enqueue(pgz_ctx* ctx, Plan& P, cudaStream_t s, bool timed) {
+    const size_t nf = P.files.size(), nc = P.chunks.size(), ng = P.g0.size();
+    memcpy(P.h_files.p, P.files.data(), nf * sizeof(FileDesc));
+    memcpy(P.h_chunks.p, P.chunks.data(), nc * sizeof(ChunkDesc));
+    cudaMemcpyAsync(P.d_files.p, P.h_files.p, nf * sizeof(FileDesc), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(P.d_chunks.p, P.h_chunks.p, nc * sizeof(ChunkDesc), cudaMemcpyHostToDevice, s);
+    FileDesc* df = P.d_files.as<FileDesc>();
+    ChunkDesc* dc = P.d_chunks.as<ChunkDesc>();
+    uint16_t* sym = P.d_sym.as<uint16_t>();
+    int k = 0;
+    if (timed) cudaEventRecord(ctx->ev[0], s);
+    launch_sync(df, dc, (int)nc, sym, ctx->kp, s);
+    if (timed) cudaEventRecord(ctx->ev[1], s);
+    launch_inflate(df, dc, (int)nc, sym, ctx->kp, s);
+    launch_plan(df, dc, (int)nf, s);
+    k += 3;
+    if (timed) cudaEventRecord(ctx->ev[2], s);
+    if (P.chain) {
+        launch_chain(df, dc, (int)nf, (int)ng, P.d_g0.as<int32_t>(), P.d_gn.as<int32_t>(), P.d_gfile.as<int32_t>(),
+                     sym, P.d_gmaps.as<uint16_t>(), P.d_wstart.as<uint8_t>(), P.d_windows.as<uint8_t>(), s);
+        k += 3;
+    }
+    if (timed) cudaEventRecord(ctx->ev[3], s);
+    if (P.translate) {
+        launch_translate(df, dc, (int)nc, P.max_cap, sym, P.d_windows.as<uint8_t>(), P.fill, s);
+        k += 1;
+    }
+    if (timed) cudaEventRecord(ctx->ev[4], s);
+    if (P.crc) {
+        launch_crc(df, (int)nf, P.total_seg, P.d_seg0.as<uint64_t>(), s);
+        launch_finalize(df, (int)nf, s);
+        k += 2;
+    }
+    if (timed) cudaEventRecord(ctx->ev[5], s);
+    cudaMemcpyAsync(P.h_files.p, P.d_files.p, nf * sizeof(FileDesc), cudaMemcpyDeviceToHost, s);
+    ctx->launches += (uint64_t)k;
+    return cuda_status(cudaGetLastError());
+}
+
+int read_chunks(pgz_ctx* ctx, Plan& P) {
+    cudaMemcpyAsync(P.h_chunks.p, P.d_chunks.p, P.chunks.size() * sizeof(ChunkDesc), cudaMemcpyDeviceToHost,
+                    ctx->stream);
+    return cuda_status(cudaStreamSynchronize(ctx->stream));
+}
+
+// Adjusts the plan after a failed run; returns true if a re-run may succeed.
+//  - a part that overflowed its symbol capacity gets twice the capacity;
+//  - a part that did not end exactly on the next accepted block start shows
+//    that start was false: that part is merged into its predecessor;
+//  - a part whose confirmation blocks failed searches again from the bit
+//    after its start (Section "Detection of DEFLATE block start positions");
+//  - any other decoding error of a part after the first marks its start as
+//    false (merge); an error in the first part is final.
+bool recover(Plan& P, int f, const ChunkDesc* res, uint64_t* false_syncs) {
+    FileDesc& F = P.files[f];
+    for (int c = F.chunk0; c < F.chunk0 + F.nchunks; ++c) {
+        const ChunkDesc& R = res[c];
+        if (R.state != CS_ERROR) continue;
+        ChunkDesc& C = P.chunks[c];
+        if (R.err == CE_OVERFLOW) {
+            C.cap *= 2;
+            return true;
+        }
+        if (R.err == CE_TRAIL) return false;
+        if (R.err == CE_CHAIN) {
+            for (int j = c + 1; j < F.chunk0 + F.nchunks; ++j) {
+                if (res[j].state == CS_EMPTY || P.chunks[j].disabled) continue;
+                if (res[j].state == CS_ERROR && res[j].err == CE_OVERFLOW) {
+                    P.chunks[j].cap *= 2;
+                    return true;
+                }
+                P.chunks[j].disabled = 1;
+                ++*false_syncs;
+                return true;
+            }
+            return false;
+        }
+        if (C.index == 0 && C.lo == F.s0_bit) return false;
+        if (C.given) return false;
+        if (R.err == CE_CONFIRM && R.sync != kNone) {
+            C.lo = R.sync + 1;
+            return true;
+        }
+        C.disabled = 1;
+        ++*false_syncs;
+        return true;
+    }
+    return false;
+}
+
+void reset_results(Plan& P) {
+    for (auto& C : P.chunks) {
+        C.sync = kNone;
+        C.state = CS_PENDING;
+        C.err = 0;
+        C.n = C.nph = C.last_ph = C.end = C.out_off = C.resume = 0;
+        C.blocks = C.final = 0;
+    }
+    for (auto& F : P.files) {
+        F.total = 0;
+        F.crc_acc = F.crc = 0;
+        F.status = PGZ_OK;
+        F.bad_chunk = 0xffffffffu;
+        F.bad_err = 0;
+    }
+}
+
+void fill_stats(pgz_ctx* ctx, const Plan& P, pgz_stats* st, uint64_t retries, uint64_t false_syncs, bool timed,
+                const ChunkDesc* res) {
+    if (!st) return;
+    memset(st, 0, sizeof *st);
+    for (const auto& F : P.files) {
+        st->in_bytes += F.gz_len;
+    }
+    const FileDesc* hf = P.h_files.as<FileDesc>();
+    for (size_t f = 0; f < P.files.size(); ++f) st->out_bytes += hf[f].total;
+    st->chunks = P.chunks.size();
+    st->retries = retries;
+    st->false_syncs = false_syncs;
+    if (res) {
+        for (size_t c = 0; c < P.chunks.size(); ++c) {
+            if (res[c].state == CS_EMPTY) st->empty_chunks++;
+            st->placeholders += res[c].nph;
+            st->symbols += res[c].n;
+        }
+    }
+    if (timed) {
+        cudaEventElapsedTime(&st->ms_sync, ctx->ev[0], ctx->ev[1]);
+        cudaEventElapsedTime(&st->ms_inflate, ctx->ev[1], ctx->ev[2]);
+        cudaEventElapsedTime(&st->ms_chain, ctx->ev[2], ctx->ev[3]);
+        cudaEventElapsedTime(&st->ms_translate, ctx->ev[3], ctx->ev[4]);
+        cudaEventElapsedTime(&st->ms_crc, ctx->ev[4], ctx->ev[5]);
+        cudaEventElapsedTime(&st->ms_total, ctx->ev[0], ctx->ev[5]);
+    }
+}
+
+// runs a plan to completion, with recovery re-runs
+int execute(pgz_ctx* ctx, Plan& P, pgz_stats* st) {
+    uint64_t retries = 0, false_syncs = 0;
+    const bool timed = st != nullptr;
+    int status = PGZ_OK;
+    for (;;) {
+        reset_results(P);
+        int e = layout(P);
+        if (e) return e;
+        upload_static(P, ctx->stream);
+        e = enqueue(ctx, P, ctx->stream, timed);
+        if (e) return e;
+        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return PGZ_E_CUDA;
+        const FileDesc* hf = P.h_files.as<FileDesc>();
+        bool again = false;
+        status = PGZ_OK;
+        bool need_chunks = false;
+        for (size_t f = 0; f < P.files.size(); ++f)
+            if (hf[f].bad_chunk != 0xffffffffu) need_chunks = true;
+        if (need_chunks || st) {
+            e = read_chunks(ctx, P);
+            if (e) return e;
+        }
+        P.results_valid = true;
+        const ChunkDesc* res = P.h_chunks.as<ChunkDesc>();
+        for (size_t f = 0; f < P.files.size(); ++f) {
+            P.files[f].total = hf[f].total;
+            P.files[f].status = hf[f].status;
+            if (hf[f].status == PGZ_OK) continue;
+            if (hf[f].bad_chunk != 0xffffffffu && retries < (uint64_t)kMaxRetries &&
+                recover(P, (int)f, res, &false_syncs)) {
+                again = true;
+            } else if (status == PGZ_OK) {
+                status = (int)hf[f].status;
+            }
+        }
+        if (again) {
+            ++retries;
+            continue;
+        }
+        if (need_chunks || st) {
+            for (size_t c = 0; c < P.chunks.size(); ++c) {   // keep the results for inspection
+                P.chunks[c].sync = res[c].sync;
+                P.chunks[c].n = res[c].n;
+                P.chunks[c].nph = res[c].nph;
+                P.chunks[c].last_ph = res[c].last_ph;
+                P.chunks[c].state = res[c].state;
+                P.chunks[c].out_off = res[c].out_off;
+            }
+        }
+        fill_stats(ctx, P, st, retries, false_syncs, timed, (need_chunks || st) ? res : nullptr);
+        return status;
+    }
+}
+
+void begin_plan(Plan& P) {
+    P.files.clear();
+    P.chunks.clear();
+    P.g0.clear();
+    P.gn.clear();
+    P.gfile.clear();
+    P.seg0.clear();
+    P.chain = P.translate = P.crc = true;
+    P.results_valid = false;
+    P.fill = nullptr;
+    if (P.graph) cudaGraphExecDestroy(P.graph);
+    P.graph = nullptr;
+}
+
+bool aligned4(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3) == 0; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void pgz_config_init(pgz_config* cfg) {
+    if (!cfg) return;
+    memset(cfg, 0, sizeof *cfg);
+    cfg->device = 0;
+    cfg->cuda_stream = nullptr;
+    cfg->chunk_bytes = 0;
+    cfg->n_chunks = 1024;
+    cfg->threads_per_chunk = 32;
+    for (int b = 0; b < 256; ++b)
+        if (b == 9 || b == 10 || b == 13 || (b >= 32 && b <= 126)) cfg->allowed[b >> 3] |= (uint8_t)(1u << (b & 7));
+    cfg->confirm_blocks = 5;
+    cfg->min_block = 1024;
+    cfg->max_block = 4u << 20;
+    cfg->dev_mem_budget = 0;
+    cfg->spin_cap = 0;
+}
+
+int pgz_create(pgz_ctx** out, const pgz_config* cfg) {
+    if (!out || !cfg) return PGZ_E_ARG;
+    *out = nullptr;
+    if (cfg->threads_per_chunk != 32 || cfg->confirm_blocks < 0 || (cfg->n_chunks <= 0 && cfg->chunk_bytes == 0))
+        return PGZ_E_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) return PGZ_E_CUDA;
+    if (cudaSetDevice(cfg->device) != cudaSuccess) return PGZ_E_CUDA;
+    pgz_ctx* ctx = new (std::nothrow) pgz_ctx();
+    if (!ctx) return PGZ_E_NOMEM;
+    ctx->cfg = *cfg;
+    ctx->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+    for (int k = 0; k < 8; ++k) ctx->kp.allowed[k] = 0;
+    for (int b = 0; b < 256; ++b)
+        if ((cfg->allowed[b >> 3] >> (b & 7)) & 1) ctx->kp.allowed[b >> 5] |= 1u << (b & 31);
+    ctx->kp.min_block = cfg->min_block;
+    ctx->kp.max_block = cfg->max_block;
+    ctx->kp.confirm_blocks = cfg->confirm_blocks;
+    upload_crc_tables();
+    for (int k = 0; k < 8; ++k) cudaEventCreate(&ctx->ev[k]);
+    if (cudaGetLastError() != cudaSuccess) {
+        delete ctx;
+        return PGZ_E_CUDA;
+    }
+    *out = ctx;
+    return PGZ_OK;
+}
+
+void pgz_destroy(pgz_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->cfg.device);
+    cudaStreamSynchronize(ctx->stream);
+    ctx->plan.release();
+    ctx->hdr.release();
+    ctx->in_buf.release();
+    ctx->out_buf.release();
+    ctx->fill_buf.release();
+    for (int k = 0; k < 8; ++k)
+        if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
+    delete ctx;
+}
+
+int pgz_decompress(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, uint8_t* out, uint64_t out_cap,
+                   uint64_t* out_len, pgz_stats* st) {
+    if (!ctx || !gz || !out_len || (!out && out_cap) || !aligned4(gz)) return PGZ_E_ARG;
+    cudaSetDevice(ctx->cfg.device);
+    *out_len = 0;
+    MemberInfo mi;
+    int e = read_member(ctx, gz, gz_len, &mi);
+    if (e) return e;
+    Plan& P = ctx->plan;
+    begin_plan(P);
+    plan_member(ctx, P, gz, gz_len, out, out_cap, mi, 0);
+    e = execute(ctx, P, st);
+    *out_len = P.files[0].total;
+    return e;
+}
+
+int pgz_decompress_host(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, uint8_t* out, uint64_t out_cap,
+                        uint64_t* out_len, pgz_stats* st) {
+    if (!ctx || !gz || !out_len || (!out && out_cap)) return PGZ_E_ARG;
+    cudaSetDevice(ctx->cfg.device);
+    *out_len = 0;
+    uint64_t s0 = 0;
+    if (parse_header(gz, gz_len, gz_len, &s0) != PGZ_OK) return PGZ_E_HEADER;
+    MemberInfo mi;
+    mi.s0 = s0;
+    const uint8_t* t = gz + gz_len - 8;
+    mi.crc = t[0] | ((uint32_t)t[1] << 8) | ((uint32_t)t[2] << 16) | ((uint32_t)t[3] << 24);
+    mi.isize = t[4] | ((uint32_t)t[5] << 8) | ((uint32_t)t[6] << 16) | ((uint32_t)t[7] << 24);
+    if (cuda_status(ctx->in_buf.ensure(gz_len)) || cuda_status(ctx->out_buf.ensure(out_cap))) return PGZ_E_NOMEM;
+    if (cudaMemcpyAsync(ctx->in_buf.p, gz, gz_len, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+        return PGZ_E_CUDA;
+    Plan& P = ctx->plan;
+    begin_plan(P);
+    plan_member(ctx, P, ctx->in_buf.as<uint8_t>(), gz_len, ctx->out_buf.as<uint8_t>(), out_cap, mi, 0);
+    int e = execute(ctx, P, st);
+    *out_len = P.files[0].total;
+    if (e == PGZ_OK && *out_len) {
+        if (cudaMemcpyAsync(out, ctx->out_buf.p, *out_len, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+            cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+            return PGZ_E_CUDA;
+    }
+    return e;
+}
+
+int pgz_decompress_at(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, uint64_t start_bit, uint16_t* sym_out,
+                      uint8_t* byte_out, uint8_t fill, uint64_t out_cap, uint64_t* out_len, uint64_t* block_bit,
+                      uint64_t* first_determined) {
+    if (!ctx || !gz || !out_len || !aligned4(gz)) return PGZ_E_ARG;
+    cudaSetDevice(ctx->cfg.device);
+    *out_len = 0;
+    MemberInfo mi;
+    int e = read_member(ctx, gz, gz_len, &mi);
+    if (e) return e;
+    Plan& P = ctx->plan;
+    begin_plan(P);
+    const uint64_t s0_bit = mi.s0 * 8, end_bit = (gz_len - 8) * 8;
+    FileDesc F{};
+    F.gz = gz;
+    F.gz_len = gz_len;
+    F.out = byte_out;
+    F.out_cap = out_cap;
+    F.s0_bit = s0_bit;
+    F.end_bit = end_bit;
+    F.mode = 1;
+    F.out_hi = kNone;
+    F.chunk0 = 0;
+    F.nchunks = 1;
+    F.group0 = 0;
+    F.ngroups = 0;
+    P.files.push_back(F);
+    ChunkDesc C{};
+    const bool at_start = start_bit <= s0_bit;
+    C.lo = at_start ? s0_bit : start_bit;
+    C.hi = end_bit;
+    C.index = at_start ? 0 : 1;
+    C.stop_hint = kNone;
+    C.sync = kNone;
+    C.cap = round_up(std::max<uint64_t>(out_cap, 65536), 8);
+    P.chunks.push_back(C);
+    P.chain = false;
+    P.crc = false;
+    P.translate = byte_out != nullptr;
+    if (cuda_status(ctx->fill_buf.ensure(kWin))) return PGZ_E_NOMEM;
+    cudaMemsetAsync(ctx->fill_buf.p, fill, kWin, ctx->stream);
+    P.fill = ctx->fill_buf.as<uint8_t>();
+    e = execute(ctx, P, nullptr);
+    if (e == PGZ_OK || e == PGZ_E_CAPACITY) {
+        if (read_chunks(ctx, P)) return PGZ_E_CUDA;
+    }
+    const ChunkDesc* res = P.h_chunks.as<ChunkDesc>();
+    if (e == PGZ_OK && res[0].state != CS_DONE) e = PGZ_E_NOSYNC;
+    if (e == PGZ_E_DATA) {
+        if (read_chunks(ctx, P)) return PGZ_E_CUDA;
+        if (res[0].state == CS_EMPTY) e = PGZ_E_NOSYNC;
+    }
+    if (e == PGZ_OK) {
+        *out_len = res[0].n;
+        if (block_bit) *block_bit = res[0].sync;
+        if (first_determined) *first_determined = res[0].last_ph;
+        if (sym_out && res[0].n) {
+            if (cudaMemcpyAsync(sym_out, P.d_sym.as<uint16_t>() + res[0].sym_base, res[0].n * sizeof(uint16_t),
+                                cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess ||
+                cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+                return PGZ_E_CUDA;
+        }
+    } else if (e == PGZ_E_CAPACITY) {
+        *out_len = res[0].n;
+    }
+    return e;
+}
+
+int pgz_decompress_batch(pgz_ctx* ctx, int n, pgz_job* jobs, pgz_stats* st) {
+    if (!ctx || n < 0 || (n && !jobs)) return PGZ_E_ARG;
+    cudaSetDevice(ctx->cfg.device);
+    Plan& P = ctx->plan;
+    begin_plan(P);
+    std::vector<int> idx;
+    int first_bad = PGZ_OK;
+    for (int k = 0; k < n; ++k) {
+        jobs[k].out_len = 0;
+        if (!jobs[k].gz || !aligned4(jobs[k].gz) || (!jobs[k].out && jobs[k].out_cap)) {
+            jobs[k].status = PGZ_E_ARG;
+            continue;
+        }
+        MemberInfo mi;
+        const int e = read_member(ctx, jobs[k].gz, jobs[k].gz_len, &mi);
+        if (e) {
+            jobs[k].status = e;
+            continue;
+        }
+        plan_member(ctx, P, jobs[k].gz, jobs[k].gz_len, jobs[k].out, jobs[k].out_cap, mi, 0);
+        idx.push_back(k);
+    }
+    int e = idx.empty() ? PGZ_OK : execute(ctx, P, st);
+    if (e == PGZ_E_CUDA || e == PGZ_E_NOMEM) return e;
+    for (size_t f = 0; f < idx.size(); ++f) {
+        jobs[idx[f]].status = (int)P.files[f].status;
+        jobs[idx[f]].out_len = P.files[f].total;
+    }
+    for (int k = 0; k < n; ++k)
+        if (jobs[k].status != PGZ_OK && first_bad == PGZ_OK) first_bad = jobs[k].status;
+    return first_bad;
+}
+
+int pgz_batch_prepare(pgz_ctx* ctx, int n, const pgz_job* jobs, pgz_batch** out) {
+    if (!ctx || !out || n <= 0 || !jobs) return PGZ_E_ARG;
+    cudaSetDevice(ctx->cfg.device);
+    *out = nullptr;
+    pgz_batch* b = new (std::nothrow) pgz_batch();
+    if (!b) return PGZ_E_NOMEM;
+    b->ctx = ctx;
+    b->jobs.assign(jobs, jobs + n);
+    Plan& P = b->plan;
+    begin_plan(P);
+    for (int k = 0; k < n; ++k) {
+        if (!jobs[k].gz || !aligned4(jobs[k].gz) || (!jobs[k].out && jobs[k].out_cap)) {
+            delete b;
+            return PGZ_E_ARG;
+        }
+        MemberInfo mi;
+        const int e = read_member(ctx, jobs[k].gz, jobs[k].gz_len, &mi);
+        if (e) {
+            delete b;
+            return e;
+        }
+        plan_member(ctx, P, jobs[k].gz, jobs[k].gz_len, jobs[k].out, jobs[k].out_cap, mi, 0);
+    }
+    // one untimed run settles the plan (capacities, false starts), then the
+    // settled plan is captured
+    int e = execute(ctx, P, nullptr);
+    if (e == PGZ_E_CUDA || e == PGZ_E_NOMEM) {
+        P.release();
+        delete b;
+        return e;
+    }
+    reset_results(P);
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        P.release();
+        delete b;
+        return PGZ_E_CUDA;
+    }
+    cudaGraph_t g = nullptr;
+    cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    const uint64_t before = ctx->launches;
+    enqueue(ctx, P, cs, false);
+    ctx->launches = before;
+    cudaError_t ce = cudaStreamEndCapture(cs, &g);
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&P.graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (ce != cudaSuccess) {
+        P.release();
+        delete b;
+        return PGZ_E_CUDA;
+    }
+    *out = b;
+    return PGZ_OK;
+}
+
+int pgz_batch_run(pgz_batch* b, pgz_job* jobs, pgz_stats* st) {
+    if (!b || !jobs) return PGZ_E_ARG;
+    pgz_ctx* ctx = b->ctx;
+    cudaSetDevice(ctx->cfg.device);
+    Plan& P = b->plan;
+    if (st) {
+        memset(st, 0, sizeof *st);
+        cudaEventRecord(ctx->ev[6], ctx->stream);
+    }
+    if (cudaGraphLaunch(P.graph, ctx->stream) != cudaSuccess) return PGZ_E_CUDA;
+    ctx->launches += (uint64_t)kernels_per_run();
+    if (st) cudaEventRecord(ctx->ev[7], ctx->stream);
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return PGZ_E_CUDA;
+    const FileDesc* hf = P.h_files.as<FileDesc>();
+    int first_bad = PGZ_OK;
+    for (size_t f = 0; f < b->jobs.size(); ++f) {
+        jobs[f].status = (int)hf[f].status;
+        jobs[f].out_len = hf[f].total;
+        if (hf[f].status != PGZ_OK && first_bad == PGZ_OK) first_bad = (int)hf[f].status;
+    }
+    if (st) {
+        for (size_t f = 0; f < b->jobs.size(); ++f) {
+            st->in_bytes += P.files[f].gz_len;
+            st->out_bytes += hf[f].total;
+        }
+        st->chunks = P.chunks.size();
+        cudaEventElapsedTime(&st->ms_total, ctx->ev[6], ctx->ev[7]);
+    }
+    return first_bad;
+}
+
+void pgz_batch_free(pgz_batch* b) {
+    if (!b) return;
+    cudaSetDevice(b->ctx->cfg.device);
+    cudaStreamSynchronize(b->ctx->stream);
+    b->plan.release();
+    delete b;
+}
+
+static const ChunkDesc* inspect_results(pgz_ctx* ctx) {
+    Plan& P = ctx->plan;
+    if (!P.results_valid || P.chunks.empty()) return nullptr;
+    cudaSetDevice(ctx->cfg.device);
+    if (read_chunks(ctx, P)) return nullptr;
+    return P.h_chunks.as<ChunkDesc>();
+}
+
+int pgz_inspect_parts(pgz_ctx* ctx, int n, uint64_t* start_bit, uint64_t* nsym, uint64_t* nph, int* nparts) {
+    if (!ctx) return PGZ_E_ARG;
+    const ChunkDesc* R = inspect_results(ctx);
+    if (!R) return PGZ_E_ARG;
+    const Plan& P = ctx->plan;
+    if (nparts) *nparts = (int)P.chunks.size();
+    for (int i = 0; i < n && i < (int)P.chunks.size(); ++i) {
+        const bool used = R[i].state == CS_DONE;
+        if (start_bit) start_bit[i] = used ? R[i].sync : kNone;
+        if (nsym) nsym[i] = used ? R[i].n : 0;
+        if (nph) nph[i] = used ? R[i].nph : 0;
+    }
+    return PGZ_OK;
+}
+
+int pgz_inspect_symbols(pgz_ctx* ctx, int part, uint16_t* host_dst, uint64_t cap, uint64_t* nsym) {
+    if (!ctx || part < 0 || part >= (int)ctx->plan.chunks.size()) return PGZ_E_ARG;
+    const ChunkDesc* R = inspect_results(ctx);
+    if (!R) return PGZ_E_ARG;
+    const ChunkDesc& C = R[part];
+    const uint64_t n = C.state == CS_DONE ? C.n : 0;
+    if (nsym) *nsym = n;
+    if (!host_dst || n == 0) return PGZ_OK;
+    if (cap < n) return PGZ_E_CAPACITY;
+    if (cudaMemcpy(host_dst, ctx->plan.d_sym.as<uint16_t>() + C.sym_base, n * sizeof(uint16_t),
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+        return PGZ_E_CUDA;
+    return PGZ_OK;
+}
+
+int pgz_inspect_window(pgz_ctx* ctx, int part, uint8_t* host_dst) {
+    if (!ctx || !host_dst || part < 0 || part >= (int)ctx->plan.chunks.size() || !ctx->plan.chain ||
+        !ctx->plan.d_windows.p)
+        return PGZ_E_ARG;
+    cudaSetDevice(ctx->cfg.device);
+    if (cudaMemcpy(host_dst, ctx->plan.d_windows.as<uint8_t>() + (uint64_t)part * kWin, kWin,
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+        return PGZ_E_CUDA;
+    return PGZ_OK;
+}
+
+uint64_t pgz_kernel_launches(const pgz_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+// --------------------------------------------------------------------------- index / range
+int pgz_index_build(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, pgz_index** idx) {
+    if (!ctx || !gz || !idx || !aligned4(gz)) return PGZ_E_ARG;
+    cudaSetDevice(ctx->cfg.device);
+    *idx = nullptr;
+    MemberInfo mi;
+    int e = read_member(ctx, gz, gz_len, &mi);
+    if (e) return e;
+    // decompress once into scratch (verifies CRC-32/ISIZE), keep the windows
+    const uint64_t csize = gz_len - 8 - mi.s0;
+    uint64_t cap = std::max<uint64_t>(mi.isize, 2 * csize) + 65536;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        if (cuda_status(ctx->out_buf.ensure(cap))) return PGZ_E_NOMEM;
+        Plan& P = ctx->plan;
+        begin_plan(P);
+        plan_member(ctx, P, gz, gz_len, ctx->out_buf.as<uint8_t>(), cap, mi, 0);
+        pgz_stats st;
+        e = execute(ctx, P, &st);
+        if (e == PGZ_E_CAPACITY) {
+            cap = P.files[0].total + 65536;
+            continue;
+        }
+        if (e) return e;
+        pgz_index* I = new (std::nothrow) pgz_index();
+        if (!I) return PGZ_E_NOMEM;
+        I->gz = gz;
+        I->gz_len = gz_len;
+        I->total = P.files[0].total;
+        I->info.push_back(mi);
+        std::vector<int> parts;
+        for (size_t c = 0; c < P.chunks.size(); ++c)
+            if (P.chunks[c].state == CS_DONE) parts.push_back((int)c);
+        for (size_t k = 0; k < parts.size(); ++k) {
+            const ChunkDesc& C = P.chunks[parts[k]];
+            I->sync.push_back(C.sync);
+            I->off.push_back(C.out_off);
+            I->n.push_back(C.n);
+            I->stop.push_back(k + 1 < parts.size() ? P.chunks[parts[k + 1]].sync : kNone);
+        }
+        if (cuda_status(I->windows.ensure(parts.size() * (size_t)kWin))) {
+            delete I;
+            return PGZ_E_NOMEM;
+        }
+        for (size_t k = 0; k < parts.size(); ++k)
+            cudaMemcpyAsync(I->windows.as<uint8_t>() + k * kWin, P.d_windows.as<uint8_t>() + (uint64_t)parts[k] * kWin,
+                            kWin, cudaMemcpyDeviceToDevice, ctx->stream);
+        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+            I->windows.release();
+            delete I;
+            return PGZ_E_CUDA;
+        }
+        *idx = I;
+        return PGZ_OK;
+    }
+    return PGZ_E_CAPACITY;
+}
+
+int pgz_index_info(const pgz_index* idx, uint64_t* total_out, uint64_t* nparts) {
+    if (!idx) return PGZ_E_ARG;
+    if (total_out) *total_out = idx->total;
+    if (nparts) *nparts = idx->sync.size();
+    return PGZ_OK;
+}
+
+int pgz_decompress_range(pgz_ctx* ctx, const pgz_index* idx, uint64_t d_off, uint64_t len, uint8_t* out) {
+    if (!ctx || !idx || (!out && len)) return PGZ_E_ARG;
+    if (d_off > idx->total || len > idx->total - d_off) return PGZ_E_ARG;
+    if (len == 0) return PGZ_OK;
+    cudaSetDevice(ctx->cfg.device);
+    // parts covering [d_off, d_off + len)
+    const size_t np = idx->sync.size();
+    size_t a = 0;
+    while (a + 1 < np && idx->off[a + 1] <= d_off) ++a;
+    size_t b = a;
+    while (b + 1 < np && idx->off[b + 1] < d_off + len) ++b;
+    Plan& P = ctx->plan;
+    begin_plan(P);
+    const MemberInfo& mi = idx->info[0];
+    FileDesc F{};
+    F.gz = idx->gz;
+    F.gz_len = idx->gz_len;
+    F.out = out;
+    F.out_cap = len;
+    F.s0_bit = mi.s0 * 8;
+    F.end_bit = (idx->gz_len - 8) * 8;
+    F.mode = 2;
+    F.out_base = idx->off[a];
+    F.out_lo = d_off;
+    F.out_hi = d_off + len;
+    F.chunk0 = 0;
+    F.nchunks = (int32_t)(b - a + 1);
+    F.group0 = 0;
+    F.ngroups = 0;
+    P.files.push_back(F);
+    for (size_t k = a; k <= b; ++k) {
+        ChunkDesc C{};
+        C.lo = idx->sync[k];
+        C.hi = idx->sync[k] + 1;
+        C.index = (int32_t)k;
+        C.given = 1;
+        C.stop_hint = (k == b) ? idx->stop[k] : kNone;
+        C.sync = kNone;
+        C.cap = round_up(idx->n[k] + 8, 8);
+        P.chunks.push_back(C);
+    }
+    P.chain = false;
+    P.crc = false;
+    int e = layout(P);
+    if (e) return e;
+    // the windows of these parts come from the index
+    if (cuda_status(P.d_windows.ensure(P.chunks.size() * (size_t)kWin))) return PGZ_E_NOMEM;
+    for (size_t k = a; k <= b; ++k)
+        cudaMemcpyAsync(P.d_windows.as<uint8_t>() + (k - a) * kWin, idx->windows.as<uint8_t>() + k * kWin, kWin,
+                        cudaMemcpyDeviceToDevice, ctx->stream);
+    e = execute(ctx, P, nullptr);
+    return e;
+}
+
+void pgz_index_free(pgz_index* idx) {
+    if (!idx) return;
+    idx->windows.release();
+    delete idx;
+}
+
+const char* pgz_strerror(int status) {
+    switch (status) {
+        case PGZ_OK: return "ok";
+        case PGZ_E_ARG: return "invalid argument";
+        case PGZ_E_HEADER: return "not a gzip member header";
+        case PGZ_E_DATA: return "invalid or truncated DEFLATE data";
+        case PGZ_E_CRC: return "CRC-32 mismatch";
+        case PGZ_E_ISIZE: return "ISIZE mismatch";
+        case PGZ_E_CAPACITY: return "output buffer too small";
+        case PGZ_E_NOSYNC: return "no block start after the offset";
+        case PGZ_E_UNSUPPORTED: return "data after the first gzip member";
+        case PGZ_E_TIMEOUT: return "device wait timed out";
+        case PGZ_E_CUDA: return "CUDA error";
+        case PGZ_E_NOMEM: return "out of device memory";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

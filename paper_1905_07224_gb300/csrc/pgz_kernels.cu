@@ -1,0 +1,1312 @@
+// pgz_kernels.cu -- sm_103a kernels of the two-pass parallel gzip decompression
+// (Kerbiriou & Chikhi, arXiv 1905.07224, Section "Full file decompression in
+// two passes (pugz)").
+//
+//   k_sync      pass 1a: per part, the first bit of [lo, hi) where a DEFLATE
+//               block starts (Section "Detection of DEFLATE block start
+//               positions", Appendix "DEFLATE block decompression checks"):
+//               a warp tests 1024 bit offsets per step (one 32-bit window per
+//               lane, bit-parallel header tests), __ballot_sync + __ffs elect
+//               the lowest candidate, and the candidate's whole block is then
+//               decoded as the final check -- into the part's own output, so
+//               pass 1 resumes after it.
+//   k_inflate   pass 1b: decode(C_i, w^_i) (Algorithm "DEFLATE decompression"
+//               with the symbolic context [U_0..U_32767]) up to the next
+//               part's block start.  One warp per part: all lanes run the
+//               Huffman decoder in lock step (shared-memory lookup tables),
+//               each lane keeping one of 32 tokens; the warp then writes the
+//               32 tokens' symbols cooperatively (prefix sum of lengths,
+//               parallel copies, in-order copies only where a copy reads
+//               symbols of its own batch).  The 32 KiB window is the part's
+//               own u16 output in global memory; a source before the part
+//               start p < 0 is the placeholder U_{32768+p}, computed, not
+//               stored.
+//   k_plan      output offsets of the parts (prefix of their lengths), error
+//               aggregation, ISIZE and capacity checks.
+//   k_chain_*   pass 2a: w_{i+1} from w_i and the tail of D_i (Section "Full
+//               file decompression in two passes").  Each part's tail is a map
+//               from w_i to w_{i+1} whose entries are bytes or indices; maps
+//               compose, so groups of parts are composed in parallel, walked
+//               across groups, then expanded per part.
+//   k_translate pass 2b: U_j -> w_i[j] for every symbol, written to the
+//               final output with 8-byte aligned stores (HBM-bound).
+//   k_crc       CRC-32 (RFC 1952) of the output: raw CRCs of 128-byte pieces,
+//               combined by multiplication with x^(8n) mod P in GF(2) and
+//               XOR-accumulated per member.
+//   k_finalize  finished CRC-32 against the trailer.
+//
+// No kernel waits on another block or warp; every read of the compressed
+// data, the symbol scratch and the output is bounds-checked.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pgz_internal.h"
+#include "../../include/pgz.h"
+
+namespace pgz {
+namespace {
+
+constexpr uint32_t FULL = 0xffffffffu;
+constexpr int LB = 10;          // literal/length lookup bits
+constexpr int DB = 8;           // distance lookup bits
+constexpr uint32_t kPoly = 0xEDB88320u;
+
+// RFC 1951 3.2.5: length codes 257..285 and distance codes 0..29
+__constant__ uint16_t c_lbase[29] = {3, 4, 5, 6, 7, 8, 9, 10, 11, 13, 15, 17, 19, 23, 27, 31,
+                                     35, 43, 51, 59, 67, 83, 99, 115, 131, 163, 195, 227, 258};
+__constant__ uint8_t c_lext[29] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 2, 2, 2, 2,
+                                   3, 3, 3, 3, 4, 4, 4, 4, 5, 5, 5, 5, 0};
+__constant__ uint16_t c_dbase[30] = {1, 2, 3, 4, 5, 7, 9, 13, 17, 25, 33, 49, 65, 97, 129,
+                                     193, 257, 385, 513, 769, 1025, 1537, 2049, 3073, 4097,
+                                     6145, 8193, 12289, 16385, 24577};
+__constant__ uint8_t c_dext[30] = {0, 0, 0, 0, 1, 1, 2, 2, 3, 3, 4, 4, 5, 5, 6, 6,
+                                   7, 7, 8, 8, 9, 9, 10, 10, 11, 11, 12, 12, 13, 13};
+// RFC 1951 3.2.7: order of the code-length code lengths
+__constant__ uint8_t c_clorder[19] = {16, 17, 18, 0, 8, 7, 9, 6, 10, 5, 11, 4, 12, 3, 13, 2, 14, 1, 15};
+// CRC-32 tables (filled by upload_crc_tables)
+__constant__ uint32_t c_crc_tab[256];   // register after one byte b from a zero register
+__constant__ uint32_t c_x2k[64];        // x^(2^k) mod P
+__constant__ uint32_t c_lane_shift[32]; // x^(8*128*k) mod P
+
+// literal/length lookup entry: bits 0-3 code length, 4-7 extra bits,
+// 8-15 literal, 16-24 base length, 28-31 kind
+enum : uint32_t { EK_LIT = 0, EK_LEN = 1, EK_EOB = 2, EK_LONG = 3, EK_BAD = 4 };
+// distance lookup entry: bits 0-3 code length, 4-7 extra bits, 8-9 kind, 16-31 base
+enum : uint32_t { DK_OK = 0, DK_LONG = 1, DK_BAD = 2 };
+
+struct WarpSmem {
+    uint32_t lit[1 << LB];
+    uint32_t dist[1 << DB];
+    uint16_t lsym[288];
+    uint16_t dsym[32];
+    uint16_t lfirst[16], lcount[16], loff[16];
+    uint16_t dfirst[16], dcount[16], doff[16];
+    uint32_t cnt[16];
+    uint32_t allowed[8];
+    uint32_t lmax, dmax, table_kind, pad;
+    uint8_t lens[320];
+    uint8_t cllens[32];
+};
+
+__device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
+    uint32_t lo = __shfl_sync(FULL, (uint32_t)v, src), hi = __shfl_sync(FULL, (uint32_t)(v >> 32), src);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+__device__ __forceinline__ uint64_t warp_sum64(uint64_t v) {
+    for (int d = 16; d; d >>= 1) {
+        uint32_t lo = __shfl_xor_sync(FULL, (uint32_t)v, d), hi = __shfl_xor_sync(FULL, (uint32_t)(v >> 32), d);
+        v += ((uint64_t)hi << 32) | lo;
+    }
+    return v;
+}
+
+__device__ __forceinline__ uint64_t warp_max64(uint64_t v) {
+    for (int d = 16; d; d >>= 1) {
+        uint32_t lo = __shfl_xor_sync(FULL, (uint32_t)v, d), hi = __shfl_xor_sync(FULL, (uint32_t)(v >> 32), d);
+        uint64_t o = ((uint64_t)hi << 32) | lo;
+        v = o > v ? o : v;
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// bit input: RFC 1951 3.1.1, LSB first; 32-bit words, bounds-checked
+// ---------------------------------------------------------------------------
+struct BitIn {
+    const uint32_t* w;
+    const uint8_t* b;
+    uint64_t nbytes, nfull;
+    uint64_t buf;
+    uint32_t cnt;
+    uint64_t widx;
+
+    __device__ __forceinline__ void setup(const uint8_t* gz, uint64_t len) {
+        w = reinterpret_cast<const uint32_t*>(gz);
+        b = gz;
+        nbytes = len;
+        nfull = len >> 2;
+    }
+    __device__ __forceinline__ uint32_t word(uint64_t i) const {
+        if (i < nfull) return __ldg(w + i);
+        uint32_t v = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint64_t p = i * 4 + k;
+            if (p < nbytes) v |= (uint32_t)__ldg(b + p) << (8 * k);
+        }
+        return v;
+    }
+    __device__ __forceinline__ void refill() {
+        if (cnt <= 32) {
+            buf |= (uint64_t)word(widx) << cnt;
+            ++widx;
+            cnt += 32;
+        }
+    }
+    __device__ __forceinline__ void seek(uint64_t bit) {
+        widx = bit >> 5;
+        const uint32_t s = (uint32_t)(bit & 31);
+        buf = (uint64_t)(word(widx) >> s);
+        cnt = 32 - s;
+        ++widx;
+        refill();
+    }
+    __device__ __forceinline__ uint64_t pos() const { return widx * 32 - cnt; }
+    __device__ __forceinline__ uint32_t peek(uint32_t n) const { return (uint32_t)buf & ((1u << n) - 1u); }
+    __device__ __forceinline__ void drop(uint32_t n) {
+        buf >>= n;
+        cnt -= n;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// canonical Huffman codes (RFC 1951 3.2.2), built by one warp
+// ---------------------------------------------------------------------------
+struct CodeInfo {
+    int status;   // 0 complete, 1 incomplete, -1 over-subscribed
+    int ncodes;
+    int maxlen;
+};
+
+__device__ CodeInfo build_code(WarpSmem& S, const uint8_t* lens, int n, uint16_t* first, uint16_t* count,
+                               uint16_t* off, uint16_t* sym, int lane) {
+    if (lane < 16) S.cnt[lane] = 0;
+    __syncwarp();
+    for (int s = lane; s < n; s += 32) {
+        const uint32_t l = lens[s];
+        if (l) atomicAdd(&S.cnt[l], 1u);
+    }
+    __syncwarp();
+    CodeInfo ci{0, 0, 0};
+    int left = 1;
+    uint32_t code = 0, o = 0, prev = 0;
+    for (int L = 1; L <= 15; ++L) {
+        const uint32_t c = S.cnt[L];
+        left = 2 * left - (int)c;
+        if (left < 0) ci.status = -1;
+        if (c) ci.maxlen = L;
+        ci.ncodes += (int)c;
+        code = (code + prev) << 1;
+        prev = c;
+        if (lane == 0) {
+            first[L] = (uint16_t)code;
+            count[L] = (uint16_t)c;
+            off[L] = (uint16_t)o;
+        }
+        o += c;
+    }
+    if (lane == 0) first[0] = count[0] = off[0] = 0;
+    if (ci.status == 0 && left > 0) ci.status = 1;
+    __syncwarp();
+    if (ci.status < 0) return ci;
+    if (lane < 16) S.cnt[lane] = off[lane];
+    __syncwarp();
+    for (int s0 = 0; s0 < n; s0 += 32) {          // symbols in (length, value) order
+        const int s = s0 + lane;
+        const uint32_t l = (s < n) ? lens[s] : 0u;
+        const uint32_t peers = __match_any_sync(FULL, l);
+        const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+        const uint32_t base = S.cnt[l];
+        if (s < n && l) sym[base + rank] = (uint16_t)s;
+        __syncwarp();
+        if (rank == 0 && l) S.cnt[l] = base + __popc(peers);
+        __syncwarp();
+    }
+    return ci;
+}
+
+// lut[stream bits] for every NB-bit pattern: the code of length <= NB that
+// prefixes it, else `miss` (a longer code, or no code)
+template <int NB, typename Make>
+__device__ void fill_lut(uint32_t* lut, const uint16_t* first, const uint16_t* count, const uint16_t* off,
+                         const uint16_t* sym, int maxlen, uint32_t miss, Make make, int lane) {
+    const int top = maxlen < NB ? maxlen : NB;
+    for (uint32_t v = lane; v < (1u << NB); v += 32) {      // v: NB code bits, first bit most significant
+        uint32_t e = miss;
+        for (int L = 1; L <= top; ++L) {
+            const uint32_t d = (v >> (NB - L)) - first[L];
+            if (d < count[L]) {
+                e = make(sym[off[L] + d], (uint32_t)L);
+                break;
+            }
+        }
+        lut[__brev(v) >> (32 - NB)] = e;
+    }
+}
+
+// codes longer than the lookup width: compare the first L bits with each
+// length's code range
+__device__ __forceinline__ int decode_long(uint32_t bits15, int nb, const uint16_t* first, const uint16_t* count,
+                                           const uint16_t* off, const uint16_t* sym, int maxlen, uint32_t& len) {
+    const uint32_t v = __brev(bits15) >> 17;
+    for (int L = nb + 1; L <= maxlen; ++L) {
+        const uint32_t d = (v >> (15 - L)) - first[L];
+        if (d < count[L]) {
+            len = (uint32_t)L;
+            return sym[off[L] + d];
+        }
+    }
+    return -1;
+}
+
+__device__ __forceinline__ uint32_t lit_entry(uint32_t s, uint32_t L) {
+    if (s < 256) return (EK_LIT << 28) | (s << 8) | L;
+    if (s == 256) return (EK_EOB << 28) | L;
+    if (s < 286) {
+        const uint32_t k = s - 257;
+        return (EK_LEN << 28) | ((uint32_t)c_lbase[k] << 16) | ((uint32_t)c_lext[k] << 4) | L;
+    }
+    return (EK_BAD << 28) | L;
+}
+
+__device__ __forceinline__ uint32_t dist_entry(uint32_t s, uint32_t L) {
+    if (s < 30) return ((uint32_t)c_dbase[s] << 16) | ((uint32_t)c_dext[s] << 4) | L;
+    return (DK_BAD << 8) | L;
+}
+
+struct LitMake {
+    __device__ uint32_t operator()(uint32_t s, uint32_t L) const { return lit_entry(s, L); }
+};
+struct DistMake {
+    __device__ uint32_t operator()(uint32_t s, uint32_t L) const { return dist_entry(s, L); }
+};
+struct ClMake {
+    __device__ uint32_t operator()(uint32_t s, uint32_t L) const { return s | (L << 8); }
+};
+
+// Reading of valid codes, as RFC 1951 3.2.7 and its producer zlib use them:
+// code-length code complete; literal/length code complete or one code of
+// length 1, with an end-of-block code; distance code complete, one code of
+// length 1, or empty.
+__device__ int read_dynamic(WarpSmem& S, BitIn& br, int lane) {
+    if (lane == 0) S.table_kind = 0;
+    br.refill();
+    const uint32_t hlit = br.peek(5) + 257;
+    br.drop(5);
+    const uint32_t hdist = br.peek(5) + 1;
+    br.drop(5);
+    const uint32_t hclen = br.peek(4) + 4;
+    br.drop(4);
+    if (hlit > 286 || hdist > 30) return CE_DATA;
+    S.cllens[lane] = 0;
+    __syncwarp();
+    br.refill();
+    const uint32_t n1 = hclen < 11 ? hclen : 11;
+    if ((uint32_t)lane < n1) S.cllens[c_clorder[lane]] = (uint8_t)((br.buf >> (3 * lane)) & 7);
+    br.drop(3 * n1);
+    br.refill();
+    if (hclen > 11) {
+        if ((uint32_t)lane >= 11 && (uint32_t)lane < hclen)
+            S.cllens[c_clorder[lane]] = (uint8_t)((br.buf >> (3 * (lane - 11))) & 7);
+        br.drop(3 * (hclen - 11));
+    }
+    __syncwarp();
+    CodeInfo ci = build_code(S, S.cllens, 19, S.dfirst, S.dcount, S.doff, S.dsym, lane);
+    if (ci.status != 0) return CE_DATA;
+    __syncwarp();
+    fill_lut<7>(S.dist, S.dfirst, S.dcount, S.doff, S.dsym, ci.maxlen, 0u, ClMake(), lane);
+    __syncwarp();
+    const uint32_t total = hlit + hdist;
+    uint32_t i = 0, prev = 0;
+    while (i < total) {
+        br.refill();
+        const uint32_t e = S.dist[br.peek(7)];
+        const uint32_t s = e & 0xffu;
+        br.drop(e >> 8);
+        if (s < 16) {
+            if (lane == 0) S.lens[i] = (uint8_t)s;
+            prev = s;
+            ++i;
+            continue;
+        }
+        uint32_t rep, val = 0;
+        if (s == 16) {
+            if (i == 0) return CE_DATA;
+            val = prev;
+            rep = 3 + br.peek(2);
+            br.drop(2);
+        } else if (s == 17) {
+            rep = 3 + br.peek(3);
+            br.drop(3);
+            prev = 0;
+        } else {
+            rep = 11 + br.peek(7);
+            br.drop(7);
+            prev = 0;
+        }
+        if (i + rep > total) return CE_DATA;
+        for (uint32_t j = lane; j < rep; j += 32) S.lens[i + j] = (uint8_t)val;
+        i += rep;
+    }
+    __syncwarp();
+    if (S.lens[256] == 0) return CE_DATA;
+    ci = build_code(S, S.lens, (int)hlit, S.lfirst, S.lcount, S.loff, S.lsym, lane);
+    if (ci.status < 0 || (ci.status > 0 && !(ci.ncodes == 1 && ci.maxlen == 1))) return CE_DATA;
+    __syncwarp();
+    fill_lut<LB>(S.lit, S.lfirst, S.lcount, S.loff, S.lsym, ci.maxlen, EK_LONG << 28, LitMake(), lane);
+    if (lane == 0) S.lmax = (uint32_t)ci.maxlen;
+    ci = build_code(S, S.lens + hlit, (int)hdist, S.dfirst, S.dcount, S.doff, S.dsym, lane);
+    if (ci.status < 0 || (ci.status > 0 && !(ci.ncodes == 0 || (ci.ncodes == 1 && ci.maxlen == 1))))
+        return CE_DATA;
+    __syncwarp();
+    fill_lut<DB>(S.dist, S.dfirst, S.dcount, S.doff, S.dsym, ci.maxlen, DK_LONG << 8, DistMake(), lane);
+    if (lane == 0) {
+        S.dmax = (uint32_t)ci.maxlen;
+        S.table_kind = 2;
+    }
+    __syncwarp();
+    return CE_OK;
+}
+
+// the fixed code of RFC 1951 3.2.6
+__device__ void build_fixed(WarpSmem& S, int lane) {
+    for (int s = lane; s < 320; s += 32)
+        S.lens[s] = (uint8_t)(s < 144 ? 8 : s < 256 ? 9 : s < 280 ? 7 : s < 288 ? 8 : 5);
+    __syncwarp();
+    CodeInfo ci = build_code(S, S.lens, 288, S.lfirst, S.lcount, S.loff, S.lsym, lane);
+    __syncwarp();
+    fill_lut<LB>(S.lit, S.lfirst, S.lcount, S.loff, S.lsym, ci.maxlen, EK_LONG << 28, LitMake(), lane);
+    if (lane == 0) S.lmax = (uint32_t)ci.maxlen;
+    ci = build_code(S, S.lens + 288, 32, S.dfirst, S.dcount, S.doff, S.dsym, lane);
+    __syncwarp();
+    fill_lut<DB>(S.dist, S.dfirst, S.dcount, S.doff, S.dsym, ci.maxlen, DK_LONG << 8, DistMake(), lane);
+    if (lane == 0) {
+        S.dmax = (uint32_t)ci.maxlen;
+        S.table_kind = 1;
+    }
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// symbol output of one part
+// ---------------------------------------------------------------------------
+struct OutState {
+    uint16_t* sym;     // the part's symbols; also its window
+    uint64_t cap;
+    uint64_t n;        // symbols so far (uniform)
+    uint64_t nph;      // this lane's placeholder count
+    uint64_t last_ph;  // this lane's largest (placeholder index + 1)
+    bool known;        // the context before the part is empty (member start)
+};
+
+// the symbol at part position q: q < 0 lies in the symbolic context
+__device__ __forceinline__ uint16_t sym_at(const uint16_t* out, int64_t q) {
+    return q >= 0 ? out[q] : (uint16_t)(kPH | (uint32_t)(kWin + q));
+}
+
+__device__ __forceinline__ void note_ph(OutState& o, uint16_t v, uint64_t pos) {
+    if (v & kPH) {
+        o.nph++;
+        o.last_ph = pos + 1 > o.last_ph ? pos + 1 : o.last_ph;
+    }
+}
+
+// a copy whose source lies wholly before this batch: loads first, then stores
+__device__ __forceinline__ void copy_run(OutState& o, int64_t src, uint64_t dst, uint32_t len) {
+    uint16_t* out = o.sym;
+    for (uint32_t j0 = 0; j0 < len; j0 += 8) {
+        uint16_t v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = (j0 + k < len) ? sym_at(out, src + j0 + k) : (uint16_t)0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (j0 + k < len) {
+                out[dst + j0 + k] = v[k];
+                note_ph(o, v[k], dst + j0 + k);
+            }
+        }
+    }
+}
+
+// token: literal = (1 << 16) | byte; match = bit 31 | length << 16 | (distance - 1)
+__device__ int exec_batch(OutState& o, uint32_t tok, int ntok, int lane, uint64_t& block_n) {
+    const bool valid = lane < ntok;
+    const bool ism = valid && (tok >> 31);
+    const uint32_t len = valid ? ((tok >> 16) & 0x1ffu) : 0u;
+    uint32_t incl = len;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += t;
+    }
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    const uint64_t base = o.n;
+    if (base + total > o.cap) return CE_OVERFLOW;
+    const uint64_t start = base + incl - len;
+    uint16_t* out = o.sym;
+    const uint32_t dist = (tok & 0xffffu) + 1u;
+    bool dep = false, bad = false;
+    if (valid && !ism) out[start] = (uint16_t)(tok & 0xffu);
+    if (ism) {
+        const int64_t src = (int64_t)start - (int64_t)dist;
+        if (o.known && src < 0) bad = true;
+        else if (src + (int64_t)len <= (int64_t)base) copy_run(o, src, start, len);
+        else dep = true;
+    }
+    if (__any_sync(FULL, bad)) return CE_DIST;
+    __syncwarp();
+    uint32_t dm = __ballot_sync(FULL, dep);
+    while (dm) {                                    // copies that read this batch, in order
+        const int k = __ffs(dm) - 1;
+        dm &= dm - 1;
+        const uint64_t ks = shfl64(start, k);
+        const uint32_t kl = __shfl_sync(FULL, len, k);
+        const uint32_t kd = __shfl_sync(FULL, dist, k);
+        for (uint32_t j = lane; j < kl; j += 32) {
+            const uint32_t jj = kd >= kl ? j : j % kd;
+            const uint16_t v = sym_at(out, (int64_t)ks - (int64_t)kd + jj);
+            out[ks + j] = v;
+            note_ph(o, v, ks + j);
+        }
+        __syncwarp();
+    }
+    o.n = base + total;
+    block_n += total;
+    return CE_OK;
+}
+
+__device__ __forceinline__ bool allowed_has(const uint32_t* a, uint32_t b) { return (a[b >> 5] >> (b & 31)) & 1u; }
+
+__device__ int huff_block(WarpSmem& S, BitIn& br, OutState& o, bool check, uint64_t max_block, uint64_t end_bit,
+                          uint64_t& block_n, int lane) {
+    for (;;) {
+        uint32_t mytok = 0;
+        int ntok = 0;
+        int st = CE_OK;
+        bool eob = false;
+        while (ntok < 32) {
+            br.refill();
+            uint32_t e = S.lit[br.peek(LB)];
+            if ((e >> 28) == EK_LONG) {
+                uint32_t L = 0;
+                const int s = decode_long(br.peek(15), LB, S.lfirst, S.lcount, S.loff, S.lsym, (int)S.lmax, L);
+                if (s < 0) {
+                    st = CE_DATA;
+                    break;
+                }
+                e = lit_entry((uint32_t)s, L);
+            }
+            const uint32_t kind = e >> 28;
+            uint32_t tok;
+            if (kind == EK_LIT) {
+                const uint32_t b = (e >> 8) & 0xffu;
+                br.drop(e & 15u);
+                if (check && !allowed_has(S.allowed, b)) {
+                    st = CE_BYTE;
+                    break;
+                }
+                tok = (1u << 16) | b;
+            } else if (kind == EK_LEN) {
+                const uint32_t cl = e & 15u, eb = (e >> 4) & 15u;
+                const uint32_t len = ((e >> 16) & 0x1ffu) + ((uint32_t)(br.buf >> cl) & ((1u << eb) - 1u));
+                br.drop(cl + eb);
+                br.refill();
+                uint32_t d = S.dist[br.peek(DB)];
+                if ((d >> 8) & 3u) {
+                    if (((d >> 8) & 3u) != DK_LONG) {
+                        st = CE_DATA;
+                        break;
+                    }
+                    uint32_t L = 0;
+                    const int s = decode_long(br.peek(15), DB, S.dfirst, S.dcount, S.doff, S.dsym, (int)S.dmax, L);
+                    if (s < 0) {
+                        st = CE_DATA;
+                        break;
+                    }
+                    d = dist_entry((uint32_t)s, L);
+                    if ((d >> 8) & 3u) {
+                        st = CE_DATA;
+                        break;
+                    }
+                }
+                const uint32_t dl = d & 15u, de = (d >> 4) & 15u;
+                const uint32_t dist = (d >> 16) + ((uint32_t)(br.buf >> dl) & ((1u << de) - 1u));
+                br.drop(dl + de);
+                tok = 0x80000000u | (len << 16) | (dist - 1u);
+            } else if (kind == EK_EOB) {
+                br.drop(e & 15u);
+                eob = true;
+                break;
+            } else {
+                st = CE_DATA;
+                break;
+            }
+            if (lane == ntok) mytok = tok;
+            ++ntok;
+        }
+        if (st) return st;
+        if (ntok) {
+            st = exec_batch(o, mytok, ntok, lane, block_n);
+            if (st) return st;
+        }
+        if (br.pos() > end_bit) return CE_TRUNC;
+        if (max_block && block_n >= max_block) return CE_SIZE;
+        if (eob) return CE_OK;
+    }
+}
+
+__device__ int stored_block(BitIn& br, OutState& o, bool check, const uint32_t* allowed, uint64_t end_bit,
+                            uint64_t& block_n, int lane) {
+    const uint64_t p = (br.pos() + 7) & ~7ull;
+    if (p + 32 > end_bit) return CE_TRUNC;
+    const uint64_t byte = p >> 3;
+    const uint8_t* g = br.b;
+    const uint32_t len = (uint32_t)__ldg(g + byte) | ((uint32_t)__ldg(g + byte + 1) << 8);
+    const uint32_t nlen = (uint32_t)__ldg(g + byte + 2) | ((uint32_t)__ldg(g + byte + 3) << 8);
+    if ((len ^ 0xffffu) != nlen) return CE_DATA;
+    if (p + 32 + 8ull * len > end_bit) return CE_TRUNC;
+    if (o.n + len > o.cap) return CE_OVERFLOW;
+    bool bad = false;
+    for (uint32_t j = lane; j < len; j += 32) {
+        const uint32_t v = __ldg(g + byte + 4 + j);
+        if (check && !allowed_has(allowed, v)) bad = true;
+        o.sym[o.n + j] = (uint16_t)v;
+    }
+    if (__any_sync(FULL, bad)) return CE_BYTE;
+    o.n += len;
+    block_n += len;
+    br.seek(p + 32 + 8ull * len);
+    __syncwarp();
+    return CE_OK;
+}
+
+// one block.  candidate: the block must be a non-final dynamic block (the
+// block-start checks); min/max_block bound its size; check: its literals must
+// be allowed bytes.
+__device__ int one_block(WarpSmem& S, BitIn& br, OutState& o, bool check, uint64_t min_block, uint64_t max_block,
+                         bool candidate, uint64_t end_bit, uint32_t& final, int lane) {
+    br.refill();
+    final = br.peek(1);
+    const uint32_t type = br.peek(3) >> 1;
+    br.drop(3);
+    if (br.pos() > end_bit) return CE_TRUNC;
+    if (candidate) {
+        if (final) return CE_FINAL;
+        if (type != 2) return CE_TYPE;
+    }
+    uint64_t block_n = 0;
+    int st;
+    if (type == 0) {
+        st = stored_block(br, o, check, S.allowed, end_bit, block_n, lane);
+    } else if (type == 1) {
+        if (S.table_kind != 1) build_fixed(S, lane);
+        st = huff_block(S, br, o, check, max_block, end_bit, block_n, lane);
+    } else if (type == 2) {
+        st = read_dynamic(S, br, lane);
+        if (st == CE_OK && br.pos() > end_bit) st = CE_TRUNC;
+        if (st == CE_OK) st = huff_block(S, br, o, check, max_block, end_bit, block_n, lane);
+    } else {
+        st = CE_DATA;
+    }
+    if (st == CE_OK && max_block && block_n >= max_block) st = CE_SIZE;
+    if (st == CE_OK && block_n < min_block) st = CE_SIZE;
+    return st;
+}
+
+// ---------------------------------------------------------------------------
+// block-start candidates: header checks of one bit offset, by one lane.
+// A necessary condition for the full checks (which one_block repeats
+// exactly): every offset that passes them passes here.
+// ---------------------------------------------------------------------------
+__device__ bool header_ok(const FileDesc& F, uint64_t p) {
+    BitIn br;
+    br.setup(F.gz, F.gz_len);
+    br.seek(p + 3);
+    const uint32_t hlit = br.peek(5) + 257;
+    br.drop(5);
+    const uint32_t hdist = br.peek(5) + 1;
+    br.drop(5);
+    const uint32_t hclen = br.peek(4) + 4;
+    br.drop(4);
+    br.refill();
+    uint64_t clb = 0;
+    uint32_t kraft = 0;
+    for (uint32_t k = 0; k < hclen; ++k) {
+        if (k == 10) br.refill();
+        const uint32_t l = br.peek(3);
+        br.drop(3);
+        clb |= (uint64_t)l << (3 * c_clorder[k]);
+        if (l) kraft += 128u >> l;
+    }
+    if (kraft != 128u) return false;                 // code-length code must be complete
+    uint32_t cnt[8], first[8], off[8], nxt[8];
+    uint8_t sorted[19];
+    for (int L = 0; L < 8; ++L) cnt[L] = 0;
+    for (int s = 0; s < 19; ++s) cnt[(clb >> (3 * s)) & 7]++;
+    cnt[0] = 0;
+    uint32_t code = 0, o = 0;
+    first[0] = off[0] = 0;
+    for (int L = 1; L < 8; ++L) {
+        code = (code + cnt[L - 1]) << 1;
+        first[L] = code;
+        off[L] = o;
+        nxt[L] = o;
+        o += cnt[L];
+    }
+    for (int s = 0; s < 19; ++s) {
+        const uint32_t l = (clb >> (3 * s)) & 7;
+        if (l) sorted[nxt[l]++] = (uint8_t)s;
+    }
+    uint32_t kl = 0, kd = 0, nl = 0, nd = 0, ml = 0, md = 0, i = 0, prev = 0;
+    bool eob = false;
+    const uint32_t total = hlit + hdist;
+    while (i < total) {
+        br.refill();
+        const uint32_t v = __brev(br.peek(7)) >> 25;
+        int s = -1;
+        uint32_t L = 1;
+        for (; L < 8; ++L) {
+            const uint32_t d = (v >> (7 - L)) - first[L];
+            if (d < cnt[L]) {
+                s = sorted[off[L] + d];
+                break;
+            }
+        }
+        if (s < 0) return false;
+        br.drop(L);
+        uint32_t val, rep;
+        if (s < 16) {
+            val = (uint32_t)s;
+            rep = 1;
+            prev = val;
+        } else if (s == 16) {
+            if (i == 0) return false;
+            val = prev;
+            rep = 3 + br.peek(2);
+            br.drop(2);
+        } else if (s == 17) {
+            val = 0;
+            rep = 3 + br.peek(3);
+            br.drop(3);
+            prev = 0;
+        } else {
+            val = 0;
+            rep = 11 + br.peek(7);
+            br.drop(7);
+            prev = 0;
+        }
+        if (i + rep > total) return false;
+        if (val) {
+            const uint32_t e = i + rep;
+            const uint32_t nlit = i < hlit ? ((e < hlit ? e : hlit) - i) : 0u;
+            const uint32_t ndst = rep - nlit;
+            kl += nlit * (32768u >> val);
+            kd += ndst * (32768u >> val);
+            nl += nlit;
+            nd += ndst;
+            if (nlit && val > ml) ml = val;
+            if (ndst && val > md) md = val;
+            if (i <= 256 && 256 < e) eob = true;
+            if (kl > 32768u || kd > 32768u) return false;   // over-subscribed
+        }
+        i += rep;
+        if (br.pos() > F.end_bit) return false;
+    }
+    if (!eob) return false;
+    if (!(kl == 32768u || (nl == 1 && ml == 1))) return false;
+    if (!(kd == 32768u || nd == 0 || (nd == 1 && md == 1))) return false;
+    return true;
+}
+
+// least bit of [lo, hi) passing header_ok; the warp tests 1024 offsets per step
+__device__ uint64_t find_candidate(const FileDesc& F, uint64_t lo, uint64_t hi, int lane) {
+    BitIn w;
+    w.setup(F.gz, F.gz_len);
+    if (hi > F.end_bit) hi = F.end_bit;
+    for (uint64_t T = lo & ~1023ull; T < hi; T += 1024) {
+        const uint64_t base = T + 32ull * (uint64_t)lane;
+        const uint64_t wi = base >> 5;
+        const uint64_t x = (uint64_t)w.word(wi) | ((uint64_t)w.word(wi + 1) << 32);
+        uint64_t y = ~x & ~(x >> 1) & (x >> 2);                // BFINAL = 0, BTYPE = 10
+        y &= ~((x >> 4) & (x >> 5) & (x >> 6) & (x >> 7));     // HLIT <= 29
+        y &= ~((x >> 9) & (x >> 10) & (x >> 11) & (x >> 12));  // HDIST <= 29
+        uint32_t m = (uint32_t)y;
+        if (base < lo) {
+            const uint64_t d = lo - base;
+            m = d >= 32 ? 0u : (m & (~0u << d));
+        }
+        if (base + 32 > hi) m = base >= hi ? 0u : (m & ((1u << (uint32_t)(hi - base)) - 1u));
+        uint64_t found = kNone;
+        while (m) {
+            const int k = __ffs(m) - 1;
+            m &= m - 1;
+            if (header_ok(F, base + (uint64_t)k)) {
+                found = base + (uint64_t)k;
+                break;
+            }
+        }
+        const uint32_t b = __ballot_sync(FULL, found != kNone);
+        if (b) return shfl64(found, __ffs(b) - 1);
+    }
+    return kNone;
+}
+
+__device__ __forceinline__ WarpSmem& warp_smem() {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    return reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
+}
+
+__device__ __forceinline__ void init_smem(WarpSmem& S, const KParams& p, int lane) {
+    if (lane < 8) S.allowed[lane] = p.allowed[lane];
+    if (lane == 0) S.table_kind = 0;
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// k_sync: block start of each part and its first block
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_sync(const FileDesc* __restrict__ files, ChunkDesc* chunks, int nchunks,
+                                              uint16_t* symbuf, KParams p) {
+    WarpSmem& S = warp_smem();
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= nchunks) return;
+    ChunkDesc& C = chunks[c];
+    const FileDesc& F = files[C.file];
+    init_smem(S, p, lane);
+    OutState o{symbuf + C.sym_base, C.cap, 0, 0, 0, C.index == 0 && C.lo <= F.s0_bit};
+    BitIn br;
+    br.setup(F.gz, F.gz_len);
+    uint32_t state = CS_EMPTY, err = CE_OK, final = 0;
+    uint64_t sync = kNone, resume = 0;
+    if (C.disabled) {
+        state = CS_EMPTY;
+    } else if (o.known || C.given) {          // the member start (empty context) or a known block start
+        br.seek(C.lo);
+        const int st = one_block(S, br, o, false, 0, 0, false, F.end_bit, final, lane);
+        sync = C.lo;
+        resume = br.pos();
+        if (st) {
+            state = CS_ERROR;
+            err = (uint32_t)st;
+        } else {
+            state = CS_FOUND;
+        }
+    } else {
+        uint64_t lo = C.lo;
+        for (;;) {
+            const uint64_t cand = find_candidate(F, lo, C.hi, lane);
+            if (cand == kNone) break;
+            br.seek(cand);
+            o.n = 0;
+            o.nph = 0;
+            o.last_ph = 0;
+            const int st = one_block(S, br, o, true, p.min_block, p.max_block, true, F.end_bit, final, lane);
+            if (st == CE_OK) {
+                state = CS_FOUND;
+                sync = cand;
+                resume = br.pos();
+                break;
+            }
+            if (st == CE_OVERFLOW) {             // the candidate's block does not fit: cannot judge it here
+                state = CS_ERROR;
+                err = CE_OVERFLOW;
+                sync = cand;
+                break;
+            }
+            lo = cand + 1;
+        }
+    }
+    const uint64_t nph = warp_sum64(o.nph), last_ph = warp_max64(o.last_ph);
+    if (lane == 0) {
+        C.state = state;
+        C.err = err;
+        C.sync = sync;
+        C.resume = resume;
+        C.n = state == CS_FOUND ? o.n : 0;
+        C.nph = nph;
+        C.last_ph = last_ph;
+        C.blocks = state == CS_FOUND ? 1u : 0u;
+        C.final = final && state == CS_FOUND;
+        C.end = resume;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_inflate: pass 1 of each part up to the next part's block start
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_inflate(const FileDesc* __restrict__ files, ChunkDesc* chunks, int nchunks,
+                                                 uint16_t* symbuf, KParams p) {
+    WarpSmem& S = warp_smem();
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= nchunks) return;
+    ChunkDesc& C = chunks[c];
+    if (C.state != CS_FOUND) return;
+    const FileDesc& F = files[C.file];
+    init_smem(S, p, lane);
+    // the next part that holds a block start; a part whose search failed
+    // stops this one at its nominal start (the run is repeated anyway)
+    uint64_t stop = C.stop_hint;
+    for (int j = c + 1; j < F.chunk0 + F.nchunks; ++j) {
+        const uint32_t s = chunks[j].state;
+        if (s == CS_FOUND) {
+            stop = chunks[j].sync;
+            break;
+        }
+        if (s == CS_ERROR) {
+            stop = chunks[j].lo;
+            break;
+        }
+    }
+    OutState o{symbuf + C.sym_base, C.cap, C.n, lane == 0 ? C.nph : 0, lane == 0 ? C.last_ph : 0,
+               C.index == 0 && C.sync == F.s0_bit};
+    uint32_t blocks = C.blocks, final = C.final, err = CE_OK;
+    uint64_t end = C.resume;
+    if (final) {
+        if (stop != kNone) err = CE_CHAIN;
+    } else {
+        BitIn br;
+        br.setup(F.gz, F.gz_len);
+        br.seek(C.resume);
+        for (;;) {
+            const uint64_t pos = br.pos();
+            if (stop != kNone && pos >= stop) {
+                if (pos != stop) err = CE_CHAIN;
+                break;
+            }
+            const bool check = !o.known && blocks <= (uint32_t)p.confirm_blocks;
+            uint32_t fin = 0;
+            const int st = one_block(S, br, o, check, 0, 0, false, F.end_bit, fin, lane);
+            if (st) {
+                err = (check && st != CE_OVERFLOW) ? (uint32_t)CE_CONFIRM : (uint32_t)st;
+                break;
+            }
+            ++blocks;
+            if (fin) {
+                final = 1;
+                if (stop != kNone) err = CE_CHAIN;
+                break;
+            }
+        }
+        end = br.pos();
+    }
+    if (err == CE_OK && final && F.mode != 2) {          // the trailer must follow the final block
+        if (((end + 7) >> 3) + 8 != F.gz_len) err = CE_TRAIL;
+    }
+    const uint64_t nph = warp_sum64(o.nph), last_ph = warp_max64(o.last_ph);
+    if (lane == 0) {
+        C.state = err ? CS_ERROR : CS_DONE;
+        C.err = err;
+        C.n = o.n;
+        C.nph = nph;
+        C.last_ph = last_ph;
+        C.blocks = blocks;
+        C.final = final;
+        C.end = end;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_plan: output offsets, error aggregation, length checks (one block per member)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_plan(FileDesc* files, ChunkDesc* chunks) {
+    FileDesc& F = files[blockIdx.x];
+    __shared__ uint64_t part[1024];
+    __shared__ uint32_t bad;
+    __shared__ int any_final;
+    const int t = threadIdx.x;
+    if (t == 0) {
+        bad = 0xffffffffu;
+        any_final = 0;
+    }
+    __syncthreads();
+    uint64_t carry = F.out_base;
+    for (int b0 = 0; b0 < F.nchunks; b0 += 1024) {
+        const int c = F.chunk0 + b0 + t;
+        uint64_t n = 0;
+        if (b0 + t < F.nchunks) {
+            ChunkDesc& C = chunks[c];
+            if (C.state == CS_DONE) {
+                n = C.n;
+                if (C.final) atomicOr(&any_final, 1);
+            } else if (C.state == CS_ERROR) {
+                atomicMin(&bad, (uint32_t)(b0 + t));
+            }
+        }
+        part[t] = n;
+        __syncthreads();
+        for (int d = 1; d < 1024; d <<= 1) {          // inclusive scan
+            const uint64_t v = t >= d ? part[t - d] : 0;
+            __syncthreads();
+            part[t] += v;
+            __syncthreads();
+        }
+        if (b0 + t < F.nchunks) chunks[c].out_off = carry + part[t] - n;
+        carry += part[1023];
+        __syncthreads();
+    }
+    if (t == 0) {
+        const uint64_t total = carry - F.out_base;
+        F.total = total;
+        F.bad_chunk = bad;
+        F.crc_acc = 0;
+        uint32_t st = PGZ_OK;
+        if (bad != 0xffffffffu) {
+            F.bad_err = chunks[F.chunk0 + bad].err;
+            st = F.bad_err == CE_TRAIL ? PGZ_E_UNSUPPORTED : PGZ_E_DATA;
+        } else if (!any_final && F.mode != 2) {
+            st = PGZ_E_DATA;
+        } else if (F.mode == 0 && total > F.out_cap) {
+            st = PGZ_E_CAPACITY;
+        } else if (F.mode == 1 && total > F.out_cap) {
+            st = PGZ_E_CAPACITY;
+        } else if (F.mode == 0 && (uint32_t)total != F.isize_expect) {
+            st = PGZ_E_ISIZE;
+        }
+        F.status = st;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// pass 2a: the window chain
+// map of part c: entry k of w_{c+1} is D_c[n-32768+k] if that exists (a byte
+// or U_j -> w_c[j]), else w_c[k+n]
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint16_t map_entry(const uint16_t* d, uint64_t n, uint32_t k) {
+    const int64_t t = (int64_t)n - (int64_t)kWin + (int64_t)k;
+    return t >= 0 ? d[t] : (uint16_t)(kPH | (uint32_t)(k + n));
+}
+
+__global__ void __launch_bounds__(1024) k_chain_compose(const FileDesc* __restrict__ files,
+                                                        const ChunkDesc* __restrict__ chunks, const int32_t* g0,
+                                                        const int32_t* gn, const int32_t* gfile,
+                                                        const uint16_t* __restrict__ sym, uint16_t* gmaps) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint16_t* acc = reinterpret_cast<uint16_t*>(smem_raw);
+    uint16_t* tmp = acc + kWin;
+    const int g = blockIdx.x;
+    if (files[gfile[g]].status != PGZ_OK) return;
+    bool have = false;
+    for (int c = g0[g]; c < g0[g] + gn[g]; ++c) {
+        const ChunkDesc& C = chunks[c];
+        if (C.state != CS_DONE || C.n == 0) continue;
+        const uint16_t* d = sym + C.sym_base;
+        for (uint32_t k = threadIdx.x; k < kWin; k += blockDim.x) {
+            uint16_t m = map_entry(d, C.n, k);
+            if (have && (m & kPH)) m = acc[m & (kWin - 1)];
+            tmp[k] = m;
+        }
+        __syncthreads();
+        uint16_t* x = acc;
+        acc = tmp;
+        tmp = x;
+        have = true;
+    }
+    uint16_t* dst = gmaps + (uint64_t)g * kWin;
+    for (uint32_t k = threadIdx.x; k < kWin; k += blockDim.x) dst[k] = have ? acc[k] : (uint16_t)(kPH | k);
+}
+
+__global__ void __launch_bounds__(1024) k_chain_walk(const FileDesc* __restrict__ files, const uint16_t* __restrict__ gmaps,
+                                                     uint8_t* wstart) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint8_t* W = smem_raw;
+    uint8_t* W2 = smem_raw + kWin;
+    const FileDesc& F = files[blockIdx.x];
+    if (F.status != PGZ_OK) return;
+    for (uint32_t k = threadIdx.x; k < kWin; k += blockDim.x) W[k] = 0;   // before the member: never referenced
+    __syncthreads();
+    for (int g = F.group0; g < F.group0 + F.ngroups; ++g) {
+        uint8_t* ws = wstart + (uint64_t)g * kWin;
+        const uint16_t* m = gmaps + (uint64_t)g * kWin;
+        for (uint32_t k = threadIdx.x; k < kWin; k += blockDim.x) {
+            ws[k] = W[k];
+            const uint16_t e = m[k];
+            W2[k] = (e & kPH) ? W[e & (kWin - 1)] : (uint8_t)e;
+        }
+        __syncthreads();
+        uint8_t* x = W;
+        W = W2;
+        W2 = x;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_chain_expand(const FileDesc* __restrict__ files,
+                                                       const ChunkDesc* __restrict__ chunks, const int32_t* g0,
+                                                       const int32_t* gn, const int32_t* gfile,
+                                                       const uint16_t* __restrict__ sym, const uint8_t* wstart,
+                                                       uint8_t* windows) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint8_t* W = smem_raw;
+    uint8_t* W2 = smem_raw + kWin;
+    const int g = blockIdx.x;
+    if (files[gfile[g]].status != PGZ_OK) return;
+    const uint8_t* ws = wstart + (uint64_t)g * kWin;
+    for (uint32_t k = threadIdx.x; k < kWin; k += blockDim.x) W[k] = ws[k];
+    __syncthreads();
+    for (int c = g0[g]; c < g0[g] + gn[g]; ++c) {
+        const ChunkDesc& C = chunks[c];
+        uint8_t* wc = windows + (uint64_t)c * kWin;
+        const bool apply = C.state == CS_DONE && C.n > 0;
+        const uint16_t* d = sym + C.sym_base;
+        for (uint32_t k = threadIdx.x; k < kWin; k += blockDim.x) {
+            wc[k] = W[k];
+            if (apply) {
+                const uint16_t e = map_entry(d, C.n, k);
+                W2[k] = (e & kPH) ? W[e & (kWin - 1)] : (uint8_t)e;
+            }
+        }
+        __syncthreads();
+        if (apply) {
+            uint8_t* x = W;
+            W = W2;
+            W2 = x;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// pass 2b: translation U_j -> w_i[j], 8 symbols per thread per step
+// ---------------------------------------------------------------------------
+constexpr uint32_t kTile = 65536;   // symbols per block
+
+__global__ void __launch_bounds__(1024) k_translate(const FileDesc* __restrict__ files,
+                                                    const ChunkDesc* __restrict__ chunks, uint32_t tiles_per_chunk,
+                                                    const uint16_t* __restrict__ sym, const uint8_t* __restrict__ windows,
+                                                    const uint8_t* __restrict__ fillw) {
+    __shared__ __align__(16) uint8_t W[kWin];
+    const uint32_t c = blockIdx.x / tiles_per_chunk, tile = blockIdx.x % tiles_per_chunk;
+    const ChunkDesc& C = chunks[c];
+    const FileDesc& F = files[C.file];
+    if (F.status != PGZ_OK || C.state != CS_DONE) return;
+    const uint64_t t0 = (uint64_t)tile * kTile;
+    if (t0 >= C.n) return;
+    const uint64_t t1 = t0 + kTile < C.n ? t0 + kTile : C.n;
+    if (t0 < C.last_ph) {
+        const uint4* src = reinterpret_cast<const uint4*>(fillw ? fillw : windows + (uint64_t)c * kWin);
+        for (uint32_t k = threadIdx.x; k < kWin / 16; k += blockDim.x) reinterpret_cast<uint4*>(W)[k] = src[k];
+        __syncthreads();
+    }
+    const uint16_t* s = sym + C.sym_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    // output byte P of the member goes to out[P - out_lo] when out_lo <= P < out_hi
+    uint8_t* out = F.out;
+    const uint64_t lo = F.out_lo, hi = F.out_hi;
+    const bool vec = F.out_lo == 0 && F.out_hi == kNone && ((reinterpret_cast<uintptr_t>(out) & 7) == 0);
+    const uint32_t m = (uint32_t)(C.out_off & 7);
+    for (uint64_t wb = t0 + 256ull * warp; wb < t1; wb += 256ull * nwarp) {
+        const uint64_t i = wb + 8ull * lane;
+        uint32_t nv = 0;
+        uint64_t val = 0;
+        if (i < t1) {
+            nv = t1 - i >= 8 ? 8u : (uint32_t)(t1 - i);
+            const uint4 q = *reinterpret_cast<const uint4*>(s + i);   // symbols past n lie within the capacity
+            const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const uint32_t v = (w4[k >> 1] >> (16 * (k & 1))) & 0xffffu;
+                const uint32_t b = (v & kPH) ? W[v & (kWin - 1)] : (v & 0xffu);
+                if ((uint32_t)k < nv) val |= (uint64_t)b << (8 * k);
+            }
+        }
+        const uint64_t P = C.out_off + i;
+        if (!vec) {                                   // byte stores, clipped to [lo, hi)
+            for (uint32_t k = 0; k < nv; ++k)
+                if (P + k >= lo && P + k < hi) out[P + k - lo] = (uint8_t)(val >> (8 * k));
+            continue;
+        }
+        if (m == 0) {
+            if (nv == 8) *reinterpret_cast<uint64_t*>(out + P) = val;
+            else
+                for (uint32_t k = 0; k < nv; ++k) out[P + k] = (uint8_t)(val >> (8 * k));
+            continue;
+        }
+        const uint64_t prev = __shfl_up_sync(FULL, val, 1);
+        const uint32_t prev_nv = __shfl_up_sync(FULL, nv, 1);
+        const uint32_t next_nv = __shfl_down_sync(FULL, nv, 1);
+        const uint32_t head = 8 - m;                  // my bytes in the aligned word at P - m
+        if (lane > 0 && prev_nv == 8 && nv >= head) {
+            *reinterpret_cast<uint64_t*>(out + P - m) = (val << (8 * m)) | (prev >> (64 - 8 * m));
+        } else {
+            for (uint32_t k = 0; k < nv && k < head; ++k) out[P + k] = (uint8_t)(val >> (8 * k));
+        }
+        const bool tail_by_next = lane < 31 && nv == 8 && next_nv >= head;
+        if (!tail_by_next)
+            for (uint32_t k = head; k < nv; ++k) out[P + k] = (uint8_t)(val >> (8 * k));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CRC-32 in GF(2): reflected representation, bit 31-k = coefficient of x^k
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t gf2_mul(uint32_t a, uint32_t b) {
+    uint32_t p = 0;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        p ^= b & (0u - ((a >> (31 - k)) & 1u));
+        b = (b >> 1) ^ (kPoly & (0u - (b & 1u)));
+    }
+    return p;
+}
+
+__device__ uint32_t xpow8(uint64_t n) {       // x^(8n) mod P
+    uint64_t e = n << 3;
+    uint32_t r = 0x80000000u;
+    for (int k = 0; e; ++k, e >>= 1)
+        if (e & 1) r = gf2_mul(r, c_x2k[k]);
+    return r;
+}
+
+constexpr uint32_t kSeg = 4096;    // bytes per warp
+constexpr uint32_t kPiece = 128;   // bytes per lane
+
+__global__ void __launch_bounds__(256) k_crc(FileDesc* files, int nfiles, uint64_t total_seg, const uint64_t* seg0) {
+    __shared__ uint32_t T[256];
+    __shared__ uint32_t LS[32];
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) T[k] = c_crc_tab[k];
+    if (threadIdx.x < 32) LS[threadIdx.x] = c_lane_shift[threadIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t sg = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); sg < total_seg; sg += nw) {
+        int lo = 0, hi = nfiles - 1;                  // member holding segment sg
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (seg0[mid] <= sg) lo = mid;
+            else hi = mid - 1;
+        }
+        FileDesc& F = files[lo];
+        if (F.status != PGZ_OK || F.mode != 0) continue;
+        const uint64_t D = F.total;
+        const uint64_t a = (sg - seg0[lo]) * kSeg;
+        if (a >= D) continue;
+        const uint64_t se = a + kSeg < D ? a + kSeg : D;
+        const uint64_t pa = a + (uint64_t)kPiece * lane;
+        const uint64_t pb = pa + kPiece < se ? pa + kPiece : se;
+        uint32_t r = 0;
+        const uint8_t* out = F.out;
+        if (pa < pb) {
+            if (pb - pa == kPiece && ((reinterpret_cast<uintptr_t>(out + pa) & 15) == 0)) {
+                const uint4* v = reinterpret_cast<const uint4*>(out + pa);
+#pragma unroll 2
+                for (int q = 0; q < 8; ++q) {
+                    const uint4 x = v[q];
+                    const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        uint32_t wv = w4[j];
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            r = T[(r ^ wv) & 0xffu] ^ (r >> 8);
+                            wv >>= 8;
+                        }
+                    }
+                }
+            } else {
+                for (uint64_t x = pa; x < pb; ++x) r = T[(r ^ out[x]) & 0xffu] ^ (r >> 8);
+            }
+            // shift to the end of the segment
+            if (se - a == kSeg) r = gf2_mul(r, LS[31 - lane]);
+            else r = gf2_mul(r, xpow8(se - pb));
+        }
+        for (int d = 16; d; d >>= 1) r ^= __shfl_xor_sync(FULL, r, d);
+        if (lane == 0) atomicXor(&F.crc_acc, gf2_mul(r, xpow8(D - se)));
+    }
+}
+
+__global__ void k_finalize(FileDesc* files, int nfiles) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nfiles) return;
+    FileDesc& F = files[f];
+    if (F.status != PGZ_OK || F.mode != 0) return;
+    // register after D bytes from the initial all-ones register, then inverted
+    const uint32_t crc = F.crc_acc ^ gf2_mul(0xffffffffu, xpow8(F.total)) ^ 0xffffffffu;
+    F.crc = crc;
+    if (crc != F.crc_expect) F.status = PGZ_E_CRC;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host wrappers
+// ---------------------------------------------------------------------------
+static size_t warp_smem_bytes() { return sizeof(WarpSmem); }
+
+void launch_sync(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, const KParams& p,
+                 cudaStream_t s) {
+    if (nchunks <= 0) return;
+    const int wpb = 4;
+    k_sync<<<(nchunks + wpb - 1) / wpb, 32 * wpb, wpb * warp_smem_bytes(), s>>>(files, chunks, nchunks, sym, p);
+}
+
+void launch_inflate(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, const KParams& p,
+                    cudaStream_t s) {
+    if (nchunks <= 0) return;
+    const int wpb = 4;
+    k_inflate<<<(nchunks + wpb - 1) / wpb, 32 * wpb, wpb * warp_smem_bytes(), s>>>(files, chunks, nchunks, sym, p);
+}
+
+void launch_plan(FileDesc* files, ChunkDesc* chunks, int nfiles, cudaStream_t s) {
+    if (nfiles <= 0) return;
+    k_plan<<<nfiles, 1024, 0, s>>>(files, chunks);
+}
+
+void launch_chain(const FileDesc* files, const ChunkDesc* chunks, int nfiles, int ngroups,
+                  const int32_t* g0, const int32_t* gn, const int32_t* gfile, const uint16_t* sym,
+                  uint16_t* gmaps, uint8_t* wstart, uint8_t* windows, cudaStream_t s) {
+    if (ngroups <= 0) return;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_chain_compose, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kWin);
+        cudaFuncSetAttribute(k_chain_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kWin);
+        cudaFuncSetAttribute(k_chain_expand, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kWin);
+        attr = true;
+    }
+    k_chain_compose<<<ngroups, 1024, 4 * kWin, s>>>(files, chunks, g0, gn, gfile, sym, gmaps);
+    k_chain_walk<<<nfiles, 1024, 2 * kWin, s>>>(files, gmaps, wstart);
+    k_chain_expand<<<ngroups, 1024, 2 * kWin, s>>>(files, chunks, g0, gn, gfile, sym, wstart, windows);
+}
+
+void launch_translate(const FileDesc* files, const ChunkDesc* chunks, int nchunks, uint64_t max_cap,
+                      const uint16_t* sym, const uint8_t* windows, const uint8_t* fillw, cudaStream_t s) {
+    if (nchunks <= 0) return;
+    const uint32_t tpc = (uint32_t)((max_cap + kTile - 1) / kTile);
+    k_translate<<<(unsigned)(tpc * (uint64_t)nchunks), 1024, 0, s>>>(files, chunks, tpc, sym, windows, fillw);
+}
+
+void launch_crc(FileDesc* files, int nfiles, uint64_t total_seg, const uint64_t* seg0, cudaStream_t s) {
+    if (nfiles <= 0 || total_seg == 0) return;
+    const uint64_t warps = total_seg < 152ull * 64 ? total_seg : 152ull * 64;
+    k_crc<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(files, nfiles, total_seg, seg0);
+}
+
+void launch_finalize(FileDesc* files, int nfiles, cudaStream_t s) {
+    if (nfiles <= 0) return;
+    k_finalize<<<(nfiles + 127) / 128, 128, 0, s>>>(files, nfiles);
+}
+
+int kernels_per_run() { return 9; }
+
+// CRC-32 constants from the polynomial (RFC 1952 section 8)
+static uint32_t h_mul(uint32_t a, uint32_t b) {
+    uint32_t p = 0;
+    for (int k = 0; k < 32; ++k) {
+        if ((a >> (31 - k)) & 1u) p ^= b;
+        b = (b & 1u) ? (b >> 1) ^ kPoly : (b >> 1);
+    }
+    return p;
+}
+
+void upload_crc_tables() {
+    uint32_t tab[256], x2k[64], ls[32];
+    for (uint32_t b = 0; b < 256; ++b) {
+        uint32_t r = b;
+        for (int k = 0; k < 8; ++k) r = (r & 1u) ? (r >> 1) ^ kPoly : (r >> 1);
+        tab[b] = r;
+    }
+    x2k[0] = 0x40000000u;                      // x
+    for (int k = 1; k < 64; ++k) x2k[k] = h_mul(x2k[k - 1], x2k[k - 1]);
+    for (int l = 0; l < 32; ++l) {             // x^(8*128*l)
+        uint64_t e = 8ull * kPiece * (uint64_t)l;
+        uint32_t r = 0x80000000u;
+        for (int k = 0; e; ++k, e >>= 1)
+            if (e & 1) r = h_mul(r, x2k[k]);
+        ls[l] = r;
+    }
+    cudaMemcpyToSymbol(c_crc_tab, tab, sizeof tab);
+    cudaMemcpyToSymbol(c_x2k, x2k, sizeof x2k);
+    cudaMemcpyToSymbol(c_lane_shift, ls, sizeof ls);
+}
+
+}  // namespace pgz

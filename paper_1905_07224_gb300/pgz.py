@@ -1,0 +1,254 @@
+"""Thin ctypes binding of libpgz (include/pgz.h), same names as the C ABI.
+
+Argument marshalling only: every step of the decompression runs in the CUDA
+kernels of libpgz.so.  Device buffers are passed as integer addresses (e.g.
+``tensor.data_ptr()``), host buffers as numpy arrays or bytes.  Importing this
+module raises if the library has not been built: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpgz.so")
+
+PGZ_OK = 0
+PGZ_E_ARG, PGZ_E_HEADER, PGZ_E_DATA, PGZ_E_CRC, PGZ_E_ISIZE, PGZ_E_CAPACITY = 1, 2, 3, 4, 5, 6
+PGZ_E_NOSYNC, PGZ_E_UNSUPPORTED, PGZ_E_TIMEOUT, PGZ_E_CUDA, PGZ_E_NOMEM = 7, 8, 9, 10, 11
+NONE = (1 << 64) - 1
+
+U64 = ctypes.c_uint64
+VP = ctypes.c_void_p
+
+
+class pgz_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("cuda_stream", VP), ("chunk_bytes", U64), ("n_chunks", ctypes.c_int),
+                ("threads_per_chunk", ctypes.c_int), ("allowed", ctypes.c_uint8 * 32),
+                ("confirm_blocks", ctypes.c_int), ("min_block", ctypes.c_uint32), ("max_block", ctypes.c_uint32),
+                ("dev_mem_budget", U64), ("spin_cap", U64)]
+
+
+class pgz_stats(ctypes.Structure):
+    _fields_ = [("in_bytes", U64), ("out_bytes", U64), ("chunks", U64), ("empty_chunks", U64),
+                ("false_syncs", U64), ("retries", U64), ("placeholders", U64), ("symbols", U64),
+                ("ms_sync", ctypes.c_float), ("ms_inflate", ctypes.c_float), ("ms_chain", ctypes.c_float),
+                ("ms_translate", ctypes.c_float), ("ms_crc", ctypes.c_float), ("ms_total", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class pgz_job(ctypes.Structure):
+    _fields_ = [("gz", VP), ("gz_len", U64), ("out", VP), ("out_cap", U64), ("out_len", U64),
+                ("status", ctypes.c_int)]
+
+
+class PgzError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {pgz_strerror(status)} ({status})" if what else pgz_strerror(status))
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libpgz.so is not built ({LIB_PATH}); run paper_1905_07224_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    sig = {
+        "pgz_config_init": (None, [P(pgz_config)]),
+        "pgz_create": (ctypes.c_int, [P(VP), P(pgz_config)]),
+        "pgz_destroy": (None, [VP]),
+        "pgz_decompress": (ctypes.c_int, [VP, VP, U64, VP, U64, P(U64), P(pgz_stats)]),
+        "pgz_decompress_host": (ctypes.c_int, [VP, VP, U64, VP, U64, P(U64), P(pgz_stats)]),
+        "pgz_decompress_at": (ctypes.c_int, [VP, VP, U64, U64, VP, VP, ctypes.c_uint8, U64, P(U64), P(U64), P(U64)]),
+        "pgz_decompress_batch": (ctypes.c_int, [VP, ctypes.c_int, P(pgz_job), P(pgz_stats)]),
+        "pgz_batch_prepare": (ctypes.c_int, [VP, ctypes.c_int, P(pgz_job), P(VP)]),
+        "pgz_batch_run": (ctypes.c_int, [VP, P(pgz_job), P(pgz_stats)]),
+        "pgz_batch_free": (None, [VP]),
+        "pgz_index_build": (ctypes.c_int, [VP, VP, U64, P(VP)]),
+        "pgz_index_info": (ctypes.c_int, [VP, P(U64), P(U64)]),
+        "pgz_decompress_range": (ctypes.c_int, [VP, VP, U64, U64, VP]),
+        "pgz_index_free": (None, [VP]),
+        "pgz_inspect_parts": (ctypes.c_int, [VP, ctypes.c_int, VP, VP, VP, P(ctypes.c_int)]),
+        "pgz_inspect_symbols": (ctypes.c_int, [VP, ctypes.c_int, VP, U64, P(U64)]),
+        "pgz_inspect_window": (ctypes.c_int, [VP, ctypes.c_int, VP]),
+        "pgz_kernel_launches": (U64, [VP]),
+        "pgz_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = _load()
+    return _lib
+
+
+EXPORTED = ["pgz_config_init", "pgz_create", "pgz_destroy", "pgz_decompress", "pgz_decompress_host",
+            "pgz_decompress_at", "pgz_decompress_batch", "pgz_batch_prepare", "pgz_batch_run", "pgz_batch_free",
+            "pgz_index_build", "pgz_index_info", "pgz_decompress_range", "pgz_index_free", "pgz_inspect_parts",
+            "pgz_inspect_symbols", "pgz_inspect_window", "pgz_kernel_launches", "pgz_strerror"]
+
+
+def pgz_strerror(status: int) -> str:
+    return lib().pgz_strerror(status).decode()
+
+
+def pgz_config_init(**overrides) -> pgz_config:
+    cfg = pgz_config()
+    lib().pgz_config_init(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        if k == "allowed":
+            for i in range(32):
+                cfg.allowed[i] = int(v[i])
+        else:
+            setattr(cfg, k, v)
+    return cfg
+
+
+def pgz_create(cfg: pgz_config) -> int:
+    h = VP()
+    st = lib().pgz_create(ctypes.byref(h), ctypes.byref(cfg))
+    if st:
+        raise PgzError(st, "pgz_create")
+    return h.value
+
+
+def pgz_destroy(ctx: int) -> None:
+    lib().pgz_destroy(ctx)
+
+
+def pgz_decompress(ctx: int, gz_ptr: int, gz_len: int, out_ptr: int, out_cap: int, stats: bool = False):
+    """(status, out_len, stats dict or None); device addresses."""
+    n = U64(0)
+    st = pgz_stats() if stats else None
+    r = lib().pgz_decompress(ctx, gz_ptr, gz_len, out_ptr, out_cap, ctypes.byref(n),
+                             ctypes.byref(st) if st is not None else None)
+    return r, n.value, (st.as_dict() if st is not None else None)
+
+
+def pgz_decompress_host(ctx: int, gz, out: np.ndarray, stats: bool = False):
+    """(status, out_len, stats); gz: bytes/uint8 array in host memory, out: uint8 array."""
+    a = np.frombuffer(gz, dtype=np.uint8) if isinstance(gz, (bytes, bytearray)) else np.ascontiguousarray(gz)
+    n = U64(0)
+    st = pgz_stats() if stats else None
+    r = lib().pgz_decompress_host(ctx, a.ctypes.data, a.size, out.ctypes.data, out.size, ctypes.byref(n),
+                                  ctypes.byref(st) if st is not None else None)
+    return r, n.value, (st.as_dict() if st is not None else None)
+
+
+def pgz_decompress_at(ctx: int, gz_ptr: int, gz_len: int, start_bit: int, sym_ptr: int | None,
+                      byte_ptr: int | None, fill: int, out_cap: int):
+    """(status, out_len, block_bit, first_determined); device addresses."""
+    n, bb, fd = U64(0), U64(0), U64(0)
+    r = lib().pgz_decompress_at(ctx, gz_ptr, gz_len, start_bit, sym_ptr, byte_ptr, fill, out_cap,
+                                ctypes.byref(n), ctypes.byref(bb), ctypes.byref(fd))
+    return r, n.value, bb.value, fd.value
+
+
+def _jobs(jobs):
+    arr = (pgz_job * len(jobs))()
+    for k, (gz_ptr, gz_len, out_ptr, out_cap) in enumerate(jobs):
+        arr[k].gz, arr[k].gz_len, arr[k].out, arr[k].out_cap = gz_ptr, gz_len, out_ptr, out_cap
+    return arr
+
+
+def pgz_decompress_batch(ctx: int, jobs, stats: bool = False):
+    """jobs: list of (gz_ptr, gz_len, out_ptr, out_cap); returns (status, [(status, out_len)], stats)."""
+    arr = _jobs(jobs)
+    st = pgz_stats() if stats else None
+    r = lib().pgz_decompress_batch(ctx, len(jobs), arr, ctypes.byref(st) if st is not None else None)
+    return r, [(arr[k].status, arr[k].out_len) for k in range(len(jobs))], (st.as_dict() if st is not None else None)
+
+
+class Batch:
+    """pgz_batch_prepare / pgz_batch_run / pgz_batch_free."""
+
+    def __init__(self, ctx: int, jobs):
+        self.arr = _jobs(jobs)
+        h = VP()
+        r = lib().pgz_batch_prepare(ctx, len(jobs), self.arr, ctypes.byref(h))
+        if r:
+            raise PgzError(r, "pgz_batch_prepare")
+        self.h = h.value
+
+    def run(self, stats: bool = False):
+        st = pgz_stats() if stats else None
+        r = lib().pgz_batch_run(self.h, self.arr, ctypes.byref(st) if st is not None else None)
+        return r, [(self.arr[k].status, self.arr[k].out_len) for k in range(len(self.arr))], \
+            (st.as_dict() if st is not None else None)
+
+    def free(self):
+        if self.h:
+            lib().pgz_batch_free(self.h)
+            self.h = None
+
+
+def pgz_index_build(ctx: int, gz_ptr: int, gz_len: int) -> int:
+    h = VP()
+    r = lib().pgz_index_build(ctx, gz_ptr, gz_len, ctypes.byref(h))
+    if r:
+        raise PgzError(r, "pgz_index_build")
+    return h.value
+
+
+def pgz_index_info(idx: int):
+    t, n = U64(0), U64(0)
+    lib().pgz_index_info(idx, ctypes.byref(t), ctypes.byref(n))
+    return t.value, n.value
+
+
+def pgz_decompress_range(ctx: int, idx: int, d_off: int, length: int, out_ptr: int) -> int:
+    return lib().pgz_decompress_range(ctx, idx, d_off, length, out_ptr)
+
+
+def pgz_index_free(idx: int) -> None:
+    lib().pgz_index_free(idx)
+
+
+def pgz_inspect_parts(ctx: int):
+    n = ctypes.c_int(0)
+    lib().pgz_inspect_parts(ctx, 0, None, None, None, ctypes.byref(n))
+    sb = np.zeros(n.value, dtype=np.uint64)
+    ns = np.zeros(n.value, dtype=np.uint64)
+    nph = np.zeros(n.value, dtype=np.uint64)
+    r = lib().pgz_inspect_parts(ctx, n.value, sb.ctypes.data, ns.ctypes.data, nph.ctypes.data, ctypes.byref(n))
+    if r:
+        raise PgzError(r, "pgz_inspect_parts")
+    return sb, ns, nph
+
+
+def pgz_inspect_symbols(ctx: int, part: int) -> np.ndarray:
+    n = U64(0)
+    r = lib().pgz_inspect_symbols(ctx, part, None, 0, ctypes.byref(n))
+    if r:
+        raise PgzError(r, "pgz_inspect_symbols")
+    out = np.zeros(n.value, dtype=np.uint16)
+    if n.value:
+        r = lib().pgz_inspect_symbols(ctx, part, out.ctypes.data, n.value, ctypes.byref(n))
+        if r:
+            raise PgzError(r, "pgz_inspect_symbols")
+    return out
+
+
+def pgz_inspect_window(ctx: int, part: int) -> np.ndarray:
+    w = np.zeros(32768, dtype=np.uint8)
+    r = lib().pgz_inspect_window(ctx, part, w.ctypes.data)
+    if r:
+        raise PgzError(r, "pgz_inspect_window")
+    return w
+
+
+def pgz_kernel_launches(ctx: int) -> int:
+    return int(lib().pgz_kernel_launches(ctx))

@@ -1,0 +1,264 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Every comparison is exact (bytes, u16 symbols, bit offsets, counts): the
+method's arithmetic is integer-only.  Stage by stage:
+  part start bits       == oracle.two_pass part_bits (block-start search)
+  pass-1 symbols (u16)  == oracle.inflate_from(start, stop) of each part
+  placeholder counts    == the oracle's counts
+  windows w_i           == the 32 KiB of true output before part i
+  output bytes          == oracle.gunzip == the generator's text
+"""
+import zlib
+
+import numpy as np
+import pytest
+
+import oracle
+import deflate_writer as dw
+from gpu_util import Ctx, to_device, empty
+from paper_1905_07224_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    """1 MiB FASTQ, 100 bp, seed 0, level 6, 8 parts (the small workload)."""
+    data = synth.fastq(1 << 20, 100, 0.001, 0)
+    gz = synth.gzip_compress(data, 6)
+    return data, gz
+
+
+def _check_parts(ctx, data, gz, nparts):
+    ref = oracle.two_pass(gz, nparts)
+    assert ref["status"] == 0 and ref["out"] == data
+    pgz = ctx.pgz
+    sb, ns, nph = pgz.pgz_inspect_parts(ctx.h)
+    assert len(sb) == nparts
+    ob = ref["part_bits"].astype(np.uint64)
+    used = ob != np.uint64(oracle.NONE)
+    assert np.array_equal(sb[used], ob[used])
+    assert np.all(sb[~used] == np.uint64(pgz.NONE))
+    assert np.array_equal(ns, ref["part_len"])
+    assert np.array_equal(nph, ref["part_nph"])
+    end = (len(gz) - 8) * 8
+    starts = [int(b) for b in ob[used]]
+    idx = np.nonzero(used)[0]
+    off = 0
+    for k, i in enumerate(idx):
+        stop = starts[k + 1] if k + 1 < len(starts) else 0
+        r = oracle.inflate_from(gz, end, starts[k], stop, known=(i == 0))
+        assert r["status"] == 0
+        got = pgz.pgz_inspect_symbols(ctx.h, int(i))
+        assert np.array_equal(got, r["sym"]), f"part {i}"
+        w = pgz.pgz_inspect_window(ctx.h, int(i))
+        if i > 0:
+            lo = max(0, off - 32768)
+            truth_w = np.frombuffer(data[lo:off], dtype=np.uint8)
+            assert np.array_equal(w[32768 - truth_w.size:], truth_w), f"window {i}"
+        off += int(ns[i])
+
+
+def test_small_workload_parts_and_output(cfg1):
+    data, gz = cfg1
+    ctx = Ctx(n_chunks=8)
+    try:
+        st, out, n, s = ctx.decompress(gz, stats=True)
+        assert st == 0, ctx.pgz.pgz_strerror(st)
+        assert n == len(data) and out == data
+        _check_parts(ctx, data, gz, 8)
+        assert s["placeholders"] > 0 and s["chunks"] == 8
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("nparts", [1, 2, 3, 64, 300])
+def test_part_counts(cfg1, nparts):
+    data, gz = cfg1
+    ctx = Ctx(n_chunks=nparts)
+    try:
+        st, out, n, _ = ctx.decompress(gz)
+        assert st == 0 and out == data
+        _check_parts(ctx, data, gz, nparts)
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("level", [1, 6, 9])
+@pytest.mark.parametrize("kind", ["fastq", "markov"])
+def test_levels_and_kinds(level, kind):
+    data = synth.fastq(3 << 20, 150, 0.01, 5) if kind == "fastq" else synth.markov(3 << 20, 6)
+    gz = synth.gzip_compress(data, level)
+    ctx = Ctx(n_chunks=24)
+    try:
+        st, out, n, _ = ctx.decompress(gz)
+        assert st == 0, ctx.pgz.pgz_strerror(st)
+        assert out == data
+        _check_parts(ctx, data, gz, 24)
+    finally:
+        ctx.close()
+
+
+def _hand(blocks):
+    w = dw.BitWriter()
+    text = b""
+    for k, (kind, payload) in enumerate(blocks):
+        final = k == len(blocks) - 1
+        if kind == "stored":
+            dw.write_stored(w, payload, final)
+            text += payload
+        else:
+            seg = dw.expand(payload, text)
+            (dw.write_fixed if kind == "fixed" else dw.write_dynamic)(w, payload, final)
+            text += seg
+    return dw.gzip_wrap(w.tobytes(), text), text
+
+
+def test_edge_inputs():
+    big = synth.fastq(40000, 100, 0.0, 7)
+    cases = {
+        "empty": (synth.gzip_compress(b"", 6), b""),
+        "one": (synth.gzip_compress(b"A", 6), b"A"),
+        "run258": (synth.gzip_compress(b"z" * 300000, 9), b"z" * 300000),
+        "64k+1": (synth.gzip_compress(synth.fastq(65537, 100, 0.0, 1), 6), synth.fastq(65537, 100, 0.0, 1)),
+        "binary_stored": None,
+        "hand": _hand([("stored", b"head\n"), ("fixed", [("lit", c) for c in b"abcabc"] + [("match", 258, 3)]),
+                       ("dynamic", dw.tokens_from_text(big)), ("stored", b"tail\n")]),
+        "maxdist": _hand([("dynamic", [("lit", b) for b in big[:32768]] + [("match", 258, 32768)])]),
+        "header_flags": None,
+    }
+    binary = np.random.default_rng(1).integers(0, 256, 200000, dtype=np.uint8).tobytes()
+    cases["binary_stored"] = (synth.gzip_compress(binary, 0), binary)
+    raw = zlib.compressobj(6, zlib.DEFLATED, -15)
+    txt = synth.markov(100000, 2)
+    cases["header_flags"] = (dw.gzip_wrap(raw.compress(txt) + raw.flush(), txt, flags=2 | 4 | 8 | 16,
+                                          name=b"x" * 5000, extra=b"e" * 300, comment=b"c"), txt)
+    for nparts in [1, 4, 32]:
+        ctx = Ctx(n_chunks=nparts)
+        try:
+            for name, (gz, text) in cases.items():
+                st, out, n, _ = ctx.decompress(gz)
+                assert st == 0, (name, nparts, ctx.pgz.pgz_strerror(st))
+                assert out == text, (name, nparts)
+        finally:
+            ctx.close()
+
+
+def test_errors():
+    pgz_ok = synth.gzip_compress(synth.fastq(500000, 100, 0.0, 3), 6)
+    data = synth.fastq(500000, 100, 0.0, 3)
+    ctx = Ctx(n_chunks=8)
+    try:
+        P = ctx.pgz
+        bad_crc = pgz_ok[:-8] + bytes([pgz_ok[-8] ^ 1]) + pgz_ok[-7:]
+        assert ctx.decompress(bad_crc)[0] == P.PGZ_E_CRC
+        bad_isize = pgz_ok[:-4] + bytes([pgz_ok[-4] ^ 1]) + pgz_ok[-3:]
+        assert ctx.decompress(bad_isize)[0] == P.PGZ_E_ISIZE
+        assert ctx.decompress(b"\x1f\x8c" + pgz_ok[2:])[0] == P.PGZ_E_HEADER
+        assert ctx.decompress(pgz_ok[:len(pgz_ok) // 2] + pgz_ok[-8:])[0] in (P.PGZ_E_DATA, P.PGZ_E_CRC)
+        assert ctx.decompress(pgz_ok + synth.gzip_compress(b"second", 6))[0] == P.PGZ_E_UNSUPPORTED
+        st, _, n, _ = ctx.decompress(pgz_ok, out_cap=1000)
+        assert st == P.PGZ_E_CAPACITY and n == len(data)
+        # a distance before the member start
+        w = dw.BitWriter()
+        dw.write_fixed(w, [("lit", 65), ("match", 3, 2)], True)
+        assert ctx.decompress(dw.gzip_wrap(w.tobytes(), b"AAAA"))[0] == P.PGZ_E_DATA
+        # the context still works afterwards
+        st, out, _, _ = ctx.decompress(pgz_ok)
+        assert st == 0 and out == data
+    finally:
+        ctx.close()
+
+
+def test_decompress_at_matches_oracle(cfg1):
+    data, gz = cfg1
+    ctx = Ctx(n_chunks=8)
+    try:
+        P = ctx.pgz
+        d = to_device(gz)
+        for start in [0, 80, 1000, (len(gz) // 3) * 8 + 5, (len(gz) * 2 // 3) * 8]:
+            ref = oracle.decompress_at(gz, start, fill=ord("?"))
+            cap = len(data) + 65536
+            sym = empty(cap * 2)
+            byt = empty(cap)
+            st, n, bb, fd = P.pgz_decompress_at(ctx.h, d.data_ptr(), len(gz), start, sym.data_ptr(),
+                                                byt.data_ptr(), ord("?"), cap)
+            assert st == ref["status"] == 0
+            assert bb == ref["block_bit"] and n == ref["sym"].size and fd == ref["first_determined"]
+            s = sym.view(dtype=__import__("torch").int16)[:n].cpu().numpy().view(np.uint16)
+            assert np.array_equal(s, ref["sym"])
+            assert byt[:n].cpu().numpy().tobytes() == ref["bytes"]
+        st, n, bb, fd = P.pgz_decompress_at(ctx.h, d.data_ptr(), len(gz), (len(gz) - 9) * 8, None, None, 63, 1 << 20)
+        assert st == P.PGZ_E_NOSYNC
+    finally:
+        ctx.close()
+
+
+def test_batch_and_graph():
+    import torch
+    man = synth.batch_manifest(12, seed=9, lo=1 << 10, hi=4 << 20)
+    files = [synth.make_file(*e) for e in man]
+    ctx = Ctx(n_chunks=0, chunk_bytes=128 << 10)
+    try:
+        P = ctx.pgz
+        dev = [to_device(g) for _, g in files]
+        outs = [empty(len(r) + 4096) for r, _ in files]
+        jobs = [(dev[k].data_ptr(), len(files[k][1]), outs[k].data_ptr(), len(files[k][0]) + 4096)
+                for k in range(len(files))]
+        st, res, s = P.pgz_decompress_batch(ctx.h, jobs, stats=True)
+        assert st == 0, [P.pgz_strerror(r[0]) for r in res]
+        for k, (raw, _) in enumerate(files):
+            assert res[k] == (0, len(raw))
+            assert outs[k][:len(raw)].cpu().numpy().tobytes() == raw
+        b = P.Batch(ctx.h, jobs)
+        try:
+            for _ in range(2):
+                for o in outs:
+                    o.zero_()
+                torch.cuda.synchronize()
+                st, res, s = b.run(stats=True)
+                assert st == 0
+                for k, (raw, _) in enumerate(files):
+                    assert res[k] == (0, len(raw))
+                    assert outs[k][:len(raw)].cpu().numpy().tobytes() == raw
+        finally:
+            b.free()
+    finally:
+        ctx.close()
+
+
+def test_index_and_ranges(cfg1):
+    data, gz = cfg1
+    ctx = Ctx(n_chunks=16)
+    try:
+        P = ctx.pgz
+        d = to_device(gz)
+        idx = P.pgz_index_build(ctx.h, d.data_ptr(), len(gz))
+        try:
+            total, nparts = P.pgz_index_info(idx)
+            assert total == len(data) and nparts >= 2
+            rng = np.random.default_rng(4)
+            ranges = [(0, 10), (len(data) - 10, 10), (123456, 70000), (0, len(data))]
+            ranges += [(int(o), int(min(len(data) - o, l))) for o, l in
+                       zip(rng.integers(0, len(data), 8), rng.integers(1, 300000, 8))]
+            for off, ln in ranges:
+                out = empty(ln)
+                st = P.pgz_decompress_range(ctx.h, idx, off, ln, out.data_ptr())
+                assert st == 0, P.pgz_strerror(st)
+                assert out[:ln].cpu().numpy().tobytes() == data[off:off + ln], (off, ln)
+        finally:
+            P.pgz_index_free(idx)
+    finally:
+        ctx.close()
+
+
+def test_host_entry_point(cfg1):
+    data, gz = cfg1
+    ctx = Ctx(n_chunks=8)
+    try:
+        out = np.zeros(len(data) + 100, dtype=np.uint8)
+        st, n, s = ctx.pgz.pgz_decompress_host(ctx.h, gz, out, stats=True)
+        assert st == 0 and n == len(data) and out[:n].tobytes() == data
+        assert ctx.pgz.pgz_kernel_launches(ctx.h) > 0
+    finally:
+        ctx.close()
