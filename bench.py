@@ -1,0 +1,338 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 two-pass parallel gzip decompression (libpgz).
+
+Default workload (one GPU): two 256 MiB synthetic FASTQ files (150 bp reads,
+seed 1), gzip level 1 and level 9 via host zlib.  One step decompresses both
+files through the C ABI (pgz_decompress, device-resident input and output):
+block-start search, pass 1, window chain, translation, CRC-32/ISIZE check.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pgz|reference]
+                  [--workload fastq256|fastq1m|batched]
+
+Prints one JSON line.  --impl reference times the CPU oracle (the plain
+bit-at-a-time RFC 1951 inflater under oracle/) on the same files.  Under
+torchrun every rank decodes its own copy of the workload (independent files,
+no collective: weak scaling) and rank 0 prints the whole-job throughput.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_BYTES = 126 * (1 << 20)
+CHUNK_BYTES = 32 << 10        # compressed bytes per part (about one DEFLATE block of zlib output)
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+def _compress_job(args):
+    from paper_1905_07224_gb300 import synth
+    kind, n, level, seed, read_len, p_n = args
+    raw = synth.fastq(n, read_len, p_n, seed) if kind == "fastq" else synth.markov(n, seed)
+    return raw, synth.gzip_compress(raw, level)
+
+
+def make_workload(name: str):
+    """List of (label, raw, gz) and a description."""
+    import multiprocessing as mp
+    if name == "fastq256":
+        jobs = [("fastq", 256 << 20, 1, 1, 150, 0.001), ("fastq", 256 << 20, 9, 1, 150, 0.001)]
+        desc = "2 x 256 MiB synthetic FASTQ (150 bp, seed 1), gzip -1 and -9"
+    elif name == "fastq1m":
+        jobs = [("fastq", 1 << 20, 6, 0, 100, 0.001)]
+        desc = "1 MiB synthetic FASTQ (100 bp, seed 0), gzip -6"
+    else:
+        raise ValueError(name)
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        res = pool.map(_compress_job, jobs)
+    files = [(f"{j[0]}-L{j[2]}", raw, gz) for j, (raw, gz) in zip(jobs, res)]
+    return files, desc
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def run_pgz(args, rank, world):
+    import numpy as np
+    import torch
+    from paper_1905_07224_gb300 import build, pgz
+
+    build.build()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    files, desc = make_workload(args.workload)
+    stream = torch.cuda.current_stream()
+    cfg = pgz.pgz_config_init(device=dev, cuda_stream=stream.cuda_stream, n_chunks=0, chunk_bytes=args.chunk_bytes)
+    ctx = pgz.pgz_create(cfg)
+    gz_dev = [torch.from_numpy(np.frombuffer(g, dtype=np.uint8).copy()).cuda() for _, _, g in files]
+    outs = [torch.empty(len(r) + 4096, dtype=torch.uint8, device="cuda") for _, r, _ in files]
+    total_out = sum(len(r) for _, r, _ in files)
+    total_in = sum(len(g) for _, _, g in files)
+
+    def step(stats=False):
+        res = []
+        for k, (_, raw, g) in enumerate(files):
+            st, n, s = pgz.pgz_decompress(ctx, gz_dev[k].data_ptr(), len(g), outs[k].data_ptr(), outs[k].numel(),
+                                          stats)
+            if st != 0 or n != len(raw):
+                raise RuntimeError(f"pgz_decompress failed: {pgz.pgz_strerror(st)}")
+            res.append(s)
+        return res
+
+    # correctness of the timed configuration
+    step()
+    for k, (_, raw, _) in enumerate(files):
+        if outs[k][:len(raw)].cpu().numpy().tobytes() != raw:
+            raise RuntimeError("output mismatch")
+    for _ in range(args.warmup):
+        step()
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.barrier()
+    torch.cuda.synchronize()
+    l0 = pgz.pgz_kernel_launches(ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(dev) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        tdist.barrier()
+    launches = pgz.pgz_kernel_launches(ctx) - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    clocks = clk.summary()
+    # per-stage times of the same configuration (library CUDA events on the same stream)
+    stage = {k: 0.0 for k in ("ms_sync", "ms_inflate", "ms_chain", "ms_translate", "ms_crc", "ms_total")}
+    nst = 3
+    chunks, empties, ph, syms = [], 0, 0, 0
+    for _ in range(nst):
+        for s in step(stats=True):
+            for k in stage:
+                stage[k] += s[k] / nst
+    for s in step(stats=True):
+        chunks.append(s["chunks"])
+        empties += s["empty_chunks"]
+        ph += s["placeholders"]
+        syms += s["symbols"]
+    # end to end through the host entry point: pinned host input -> device -> pinned host output
+    pin_in = [torch.from_numpy(np.frombuffer(g, dtype=np.uint8).copy()).pin_memory() for _, _, g in files]
+    pin_out = [torch.empty(len(r) + 4096, dtype=torch.uint8).pin_memory() for _, r, _ in files]
+
+    def e2e_step():
+        for k, (_, raw, g) in enumerate(files):
+            st, n, _ = pgz.pgz_decompress_host(ctx, pin_in[k].numpy(), pin_out[k].numpy())
+            if st != 0 or n != len(raw):
+                raise RuntimeError(f"pgz_decompress_host failed: {pgz.pgz_strerror(st)}")
+
+    e2e_step()
+    if pin_out[0][:len(files[0][1])].numpy().tobytes() != files[0][1]:
+        raise RuntimeError("e2e output mismatch")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.steps)):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / max(1, args.steps)
+    # max over ranks
+    if dist:
+        t = torch.tensor([ms, e2e_ms], device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms, e2e_ms = float(t[0]), float(t[1])
+    pgz.pgz_destroy(ctx)
+    gbs = world * total_out / (ms * 1e-3) / 1e9
+    pk = _peaks()
+    hbm = pk.get("hbm_gbs")
+    pass1_ms = stage["ms_sync"] + stage["ms_inflate"]
+    alg1 = total_in + 2 * total_out                  # compressed bytes read + u16 symbols written
+    ach1 = alg1 / (pass1_ms * 1e-3) / 1e9
+    alg4 = 3 * total_out                             # u16 symbols read + bytes written
+    ach4 = alg4 / (stage["ms_translate"] * 1e-3) / 1e9 if stage["ms_translate"] > 0 else None
+    line = {
+        "metric": "decompressed GB/s on 1 GB300 (two-pass parallel gzip decompression, plain API)",
+        "value": round(gbs, 3),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": desc, "files": len(files), "out_bytes_per_step": total_out,
+                   "in_bytes_per_step": total_in, "chunk_bytes": args.chunk_bytes, "parts": chunks,
+                   "empty_parts": empties, "placeholder_fraction": round(ph / max(1, syms), 4),
+                   "l2": "inputs (%.0f MB) and outputs (%.0f MB) larger than L2" % (total_in / 1e6, total_out / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "compressed_MBps": round(world * total_in / (ms * 1e-3) / 1e6, 1),
+        "stages_ms": {k: round(v, 3) for k, v in stage.items()},
+        "roofline": {"bound": "hbm", "kernel": "pass 1 (k_sync + k_inflate)", "achieved": round(ach1, 2),
+                     "peak": hbm, "unit": "GB/s", "frac": round(ach1 / hbm, 5) if hbm else None,
+                     "traffic": None, "peak_source": "measured" if hbm else "fallback 6800"},
+        "roofline_translate": {"bound": "hbm", "kernel": "k_translate", "achieved": round(ach4, 1) if ach4 else None,
+                               "peak": hbm, "unit": "GB/s",
+                               "frac": round(ach4 / hbm, 4) if (ach4 and hbm) else None},
+        "e2e": {"value": round(world * total_out / (e2e_ms * 1e-3) / 1e9, 3), "unit": "GB/s",
+                "h2d_bytes_per_step": total_in, "d2h_bytes_per_step": total_out},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if rank == 0:
+        line["cpu_baseline"] = cpu_baseline(files)
+    return line
+
+
+def cpu_baseline(files, budget_s: float = 20.0):
+    """The oracle (plain bit-at-a-time inflater, one thread) on the same files."""
+    import oracle
+    oracle.build()
+    done_out, t_used, sample = 0, 0.0, []
+    for label, raw, gz in files:
+        if t_used > budget_s:
+            break
+        t0 = time.perf_counter()
+        e, out, _, _ = oracle.gunzip(gz, cap=len(raw) + 1024)
+        dt = time.perf_counter() - t0
+        if e != 0 or len(out) != len(raw):
+            raise RuntimeError("oracle failed")
+        t_used += dt
+        done_out += len(raw)
+        sample.append(label)
+    return {"value": round(done_out / t_used / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle.gunzip (one thread) over {', '.join(sample)} ({done_out >> 20} MiB out, {t_used:.1f} s)"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle, as it stands, on the same workload."""
+    import oracle
+    oracle.build()
+    files, desc = make_workload(args.workload)
+    total = sum(len(r) for _, r, _ in files)
+
+    def step():
+        for _, raw, gz in files:
+            e, out, _, _ = oracle.gunzip(gz, cap=len(raw) + 1024)
+            if e != 0 or len(out) != len(raw):
+                raise RuntimeError("oracle failed")
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    v = total / (ms * 1e-3) / 1e9
+    return {"impl": "reference", "metric": "decompressed GB/s on 1 GB300 (two-pass parallel gzip decompression, plain API)",
+            "value": round(v, 4), "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 1), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8", "data": "synthetic", "config": {"workload": desc, "out_bytes_per_step": total},
+            "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": f"oracle.gunzip (one thread), the whole workload per step"},
+            "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pgz", choices=["pgz", "reference"])
+    ap.add_argument("--workload", default="fastq256", choices=["fastq256", "fastq1m"])
+    ap.add_argument("--chunk-bytes", type=int, default=CHUNK_BYTES)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group("nccl")
+    line = run_pgz(args, rank, world)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -636,6 +636,10 @@ int pgz_decompress_at(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, uint64_t
     begin_plan(P);
     const uint64_t s0_bit = mi.s0 * 8, end_bit = (gz_len - 8) * 8;
     FileDesc F{};
+    if (!byte_out) {                                   // the translation still counts the placeholders
+        if (cuda_status(ctx->out_buf.ensure(out_cap))) return PGZ_E_NOMEM;
+        byte_out = ctx->out_buf.as<uint8_t>();
+    }
     F.gz = gz;
     F.gz_len = gz_len;
     F.out = byte_out;
@@ -660,7 +664,7 @@ int pgz_decompress_at(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, uint64_t
     P.chunks.push_back(C);
     P.chain = false;
     P.crc = false;
-    P.translate = byte_out != nullptr;
+    P.translate = true;
     if (cuda_status(ctx->fill_buf.ensure(kWin))) return PGZ_E_NOMEM;
     cudaMemsetAsync(ctx->fill_buf.p, fill, kWin, ctx->stream);
     P.fill = ctx->fill_buf.as<uint8_t>();

@@ -84,14 +84,16 @@ struct ChunkDesc {
     uint64_t sync;         // block start (bit), kNone if none
     uint64_t resume;       // bit after the first block
     uint64_t n;            // symbols produced
-    uint64_t nph;          // placeholder symbols produced
-    uint64_t last_ph;      // one past the last placeholder symbol
+    uint64_t nph;          // placeholder symbols produced (counted by the translation)
+    uint64_t last_ph;      // one past the last placeholder symbol (idem)
     uint64_t end;          // bit where pass 1 stopped
     uint64_t out_off;      // output offset of the part
     uint32_t state;
     uint32_t err;
     uint32_t blocks;
     uint32_t final;        // the part decoded the member's final block
+    uint32_t anyph;        // pass 1 produced at least one placeholder
+    uint32_t pad2;
 };
 
 // host-side launch wrappers (pgz_kernels.cu)
@@ -103,7 +105,7 @@ void launch_plan(FileDesc* files, ChunkDesc* chunks, int nfiles, cudaStream_t s)
 void launch_chain(const FileDesc* files, const ChunkDesc* chunks, int nfiles, int ngroups,
                   const int32_t* group_chunk0, const int32_t* group_n, const int32_t* group_file,
                   const uint16_t* sym, uint16_t* gmaps, uint8_t* wstart, uint8_t* windows, cudaStream_t s);
-void launch_translate(const FileDesc* files, const ChunkDesc* chunks, int nchunks, uint64_t max_cap,
+void launch_translate(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint64_t max_cap,
                       const uint16_t* sym, const uint8_t* windows, const uint8_t* fill_window, cudaStream_t s);
 void launch_crc(FileDesc* files, int nfiles, uint64_t total_seg, const uint64_t* seg0, cudaStream_t s);
 void launch_finalize(FileDesc* files, int nfiles, cudaStream_t s);

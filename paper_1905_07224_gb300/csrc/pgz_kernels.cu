@@ -68,9 +68,12 @@ __constant__ uint32_t c_crc_tab[256];   // register after one byte b from a zero
 __constant__ uint32_t c_x2k[64];        // x^(2^k) mod P
 __constant__ uint32_t c_lane_shift[32]; // x^(8*128*k) mod P
 
-// literal/length lookup entry: bits 0-3 code length, 4-7 extra bits,
-// 8-15 literal, 16-24 base length, 28-31 kind
-enum : uint32_t { EK_LIT = 0, EK_LEN = 1, EK_EOB = 2, EK_LONG = 3, EK_BAD = 4 };
+// literal/length lookup entry: bits 0-4 bits to drop, 8-16 value, 17-19
+// extra-bit count (K_LENX), 28-31 kind.  K_LEN carries the exact length
+// (code and extra bits both inside the lookup width), K_LENX the base.
+// K_LIT2: two literals whose codes both fit the lookup width: bits 8-15 and
+// 16-23 the bytes, 24-27 the first code's length, 0-4 both lengths.
+enum : uint32_t { K_LIT = 0, K_LIT2 = 1, K_LEN = 2, K_LENX = 3, K_EOB = 4, K_LONG = 5, K_BAD = 6 };
 // distance lookup entry: bits 0-3 code length, 4-7 extra bits, 8-9 kind, 16-31 base
 enum : uint32_t { DK_OK = 0, DK_LONG = 1, DK_BAD = 2 };
 
@@ -93,39 +96,25 @@ __device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
     return ((uint64_t)hi << 32) | lo;
 }
 
-__device__ __forceinline__ uint64_t warp_sum64(uint64_t v) {
-    for (int d = 16; d; d >>= 1) {
-        uint32_t lo = __shfl_xor_sync(FULL, (uint32_t)v, d), hi = __shfl_xor_sync(FULL, (uint32_t)(v >> 32), d);
-        v += ((uint64_t)hi << 32) | lo;
-    }
-    return v;
-}
-
-__device__ __forceinline__ uint64_t warp_max64(uint64_t v) {
-    for (int d = 16; d; d >>= 1) {
-        uint32_t lo = __shfl_xor_sync(FULL, (uint32_t)v, d), hi = __shfl_xor_sync(FULL, (uint32_t)(v >> 32), d);
-        uint64_t o = ((uint64_t)hi << 32) | lo;
-        v = o > v ? o : v;
-    }
-    return v;
-}
-
 // ---------------------------------------------------------------------------
-// bit input: RFC 1951 3.1.1, LSB first; 32-bit words, bounds-checked
+// bit input: RFC 1951 3.1.1, LSB first; 32-bit words, bounds-checked; the
+// next word is loaded one refill ahead
 // ---------------------------------------------------------------------------
 struct BitIn {
-    const uint32_t* w;
+    const uint32_t* w;   // the member's bytes as 32-bit words (4-byte aligned)
     const uint8_t* b;
-    uint64_t nbytes, nfull;
-    uint64_t buf;
-    uint32_t cnt;
-    uint64_t widx;
+    uint64_t nbytes;
+    uint32_t nfull;      // words wholly inside the member
+    uint32_t lo, hi;     // buffered bits [0, 32) and [32, 64); zero above cnt
+    uint32_t cnt;        // buffered bits
+    uint32_t nxt;        // word(wi), loaded one refill ahead
+    uint32_t wi;         // next word to merge into the buffer
 
     __device__ __forceinline__ void setup(const uint8_t* gz, uint64_t len) {
         w = reinterpret_cast<const uint32_t*>(gz);
         b = gz;
         nbytes = len;
-        nfull = len >> 2;
+        nfull = (uint32_t)((len >> 2) < 0xffffffffull ? (len >> 2) : 0xffffffffull);
     }
     __device__ __forceinline__ uint32_t word(uint64_t i) const {
         if (i < nfull) return __ldg(w + i);
@@ -137,25 +126,32 @@ struct BitIn {
         }
         return v;
     }
+    // SAFE: the caller has checked that word wi lies inside the member
+    template <bool SAFE = false>
     __device__ __forceinline__ void refill() {
         if (cnt <= 32) {
-            buf |= (uint64_t)word(widx) << cnt;
-            ++widx;
+            lo |= __funnelshift_lc(0u, nxt, cnt);    // nxt << cnt, 0 when cnt = 32
+            hi |= __funnelshift_lc(nxt, 0u, cnt);    // nxt >> (32 - cnt), nxt when cnt = 32
             cnt += 32;
+            ++wi;
+            nxt = SAFE ? __ldg(w + wi) : word(wi);
         }
     }
     __device__ __forceinline__ void seek(uint64_t bit) {
-        widx = bit >> 5;
+        wi = (uint32_t)(bit >> 5);
         const uint32_t s = (uint32_t)(bit & 31);
-        buf = (uint64_t)(word(widx) >> s);
+        lo = word(wi) >> s;
+        hi = 0;
         cnt = 32 - s;
-        ++widx;
+        ++wi;
+        nxt = word(wi);
         refill();
     }
-    __device__ __forceinline__ uint64_t pos() const { return widx * 32 - cnt; }
-    __device__ __forceinline__ uint32_t peek(uint32_t n) const { return (uint32_t)buf & ((1u << n) - 1u); }
-    __device__ __forceinline__ void drop(uint32_t n) {
-        buf >>= n;
+    __device__ __forceinline__ uint64_t pos() const { return (uint64_t)wi * 32 - cnt; }
+    __device__ __forceinline__ uint32_t peek(uint32_t n) const { return lo & ((1u << n) - 1u); }   // n < 32
+    __device__ __forceinline__ void drop(uint32_t n) {                                           // n < 32
+        lo = __funnelshift_r(lo, hi, n);
+        hi >>= n;
         cnt -= n;
     }
 };
@@ -216,22 +212,23 @@ __device__ CodeInfo build_code(WarpSmem& S, const uint8_t* lens, int n, uint16_t
     return ci;
 }
 
-// lut[stream bits] for every NB-bit pattern: the code of length <= NB that
-// prefixes it, else `miss` (a longer code, or no code)
+// lut[x] for every NB-bit stream pattern x: the code of length <= NB that
+// prefixes it (make(symbol, length, x)), else `miss` (a longer code, or none)
 template <int NB, typename Make>
 __device__ void fill_lut(uint32_t* lut, const uint16_t* first, const uint16_t* count, const uint16_t* off,
                          const uint16_t* sym, int maxlen, uint32_t miss, Make make, int lane) {
     const int top = maxlen < NB ? maxlen : NB;
     for (uint32_t v = lane; v < (1u << NB); v += 32) {      // v: NB code bits, first bit most significant
+        const uint32_t x = __brev(v) >> (32 - NB);
         uint32_t e = miss;
         for (int L = 1; L <= top; ++L) {
             const uint32_t d = (v >> (NB - L)) - first[L];
             if (d < count[L]) {
-                e = make(sym[off[L] + d], (uint32_t)L);
+                e = make(sym[off[L] + d], (uint32_t)L, x, v);
                 break;
             }
         }
-        lut[__brev(v) >> (32 - NB)] = e;
+        lut[x] = e;
     }
 }
 
@@ -250,14 +247,17 @@ __device__ __forceinline__ int decode_long(uint32_t bits15, int nb, const uint16
     return -1;
 }
 
-__device__ __forceinline__ uint32_t lit_entry(uint32_t s, uint32_t L) {
-    if (s < 256) return (EK_LIT << 28) | (s << 8) | L;
-    if (s == 256) return (EK_EOB << 28) | L;
+// x: the lookup index (stream bits), whose bits after the code are the
+// length's extra bits when they fit
+__device__ __forceinline__ uint32_t lit_entry(uint32_t s, uint32_t L, uint32_t x) {
+    if (s < 256) return (K_LIT << 28) | (s << 8) | L;
+    if (s == 256) return (K_EOB << 28) | L;
     if (s < 286) {
-        const uint32_t k = s - 257;
-        return (EK_LEN << 28) | ((uint32_t)c_lbase[k] << 16) | ((uint32_t)c_lext[k] << 4) | L;
+        const uint32_t k = s - 257, base = c_lbase[k], E = c_lext[k];
+        if (L + E <= (uint32_t)LB) return (K_LEN << 28) | ((base + ((x >> L) & ((1u << E) - 1u))) << 8) | (L + E);
+        return (K_LENX << 28) | (E << 17) | (base << 8) | L;
     }
-    return (EK_BAD << 28) | L;
+    return (K_BAD << 28) | L;
 }
 
 __device__ __forceinline__ uint32_t dist_entry(uint32_t s, uint32_t L) {
@@ -265,20 +265,37 @@ __device__ __forceinline__ uint32_t dist_entry(uint32_t s, uint32_t L) {
     return (DK_BAD << 8) | L;
 }
 
+// a literal followed, inside the lookup width, by a second literal: one entry
 struct LitMake {
-    __device__ uint32_t operator()(uint32_t s, uint32_t L) const { return lit_entry(s, L); }
+    const uint16_t *first, *count, *off, *sym;
+    __device__ uint32_t operator()(uint32_t s, uint32_t L, uint32_t x, uint32_t v) const {
+        const uint32_t e = lit_entry(s, L, x);
+        if (s >= 256 || L >= (uint32_t)LB - 1) return e;
+        const uint32_t rest = LB - L, v2 = v & ((1u << rest) - 1u);   // the next code bits, first bit most significant
+        for (uint32_t L2 = 1; L2 <= rest; ++L2) {
+            const uint32_t d = (v2 >> (rest - L2)) - first[L2];
+            if (d < count[L2]) {
+                const uint32_t s2 = sym[off[L2] + d];
+                if (s2 >= 256) return e;
+                return (K_LIT2 << 28) | (L << 24) | (s2 << 16) | (s << 8) | (L + L2);
+            }
+        }
+        return e;
+    }
 };
 struct DistMake {
-    __device__ uint32_t operator()(uint32_t s, uint32_t L) const { return dist_entry(s, L); }
+    __device__ uint32_t operator()(uint32_t s, uint32_t L, uint32_t, uint32_t) const { return dist_entry(s, L); }
 };
 struct ClMake {
-    __device__ uint32_t operator()(uint32_t s, uint32_t L) const { return s | (L << 8); }
+    __device__ uint32_t operator()(uint32_t s, uint32_t L, uint32_t, uint32_t) const { return s | (L << 8); }
 };
 
 // Reading of valid codes, as RFC 1951 3.2.7 and its producer zlib use them:
 // code-length code complete; literal/length code complete or one code of
 // length 1, with an end-of-block code; distance code complete, one code of
-// length 1, or empty.
+// length 1, or empty.  HDR_ONLY: stop after the checks (block-start search);
+// an over-subscribed length set ends the decoding early either way.
+template <bool HDR_ONLY>
 __device__ int read_dynamic(WarpSmem& S, BitIn& br, int lane) {
     if (lane == 0) S.table_kind = 0;
     br.refill();
@@ -292,14 +309,14 @@ __device__ int read_dynamic(WarpSmem& S, BitIn& br, int lane) {
     S.cllens[lane] = 0;
     __syncwarp();
     br.refill();
-    const uint32_t n1 = hclen < 11 ? hclen : 11;
-    if ((uint32_t)lane < n1) S.cllens[c_clorder[lane]] = (uint8_t)((br.buf >> (3 * lane)) & 7);
+    const uint32_t n1 = hclen < 10 ? hclen : 10;
+    if ((uint32_t)lane < n1) S.cllens[c_clorder[lane]] = (uint8_t)((br.lo >> (3 * lane)) & 7);
     br.drop(3 * n1);
     br.refill();
-    if (hclen > 11) {
-        if ((uint32_t)lane >= 11 && (uint32_t)lane < hclen)
-            S.cllens[c_clorder[lane]] = (uint8_t)((br.buf >> (3 * (lane - 11))) & 7);
-        br.drop(3 * (hclen - 11));
+    if (hclen > 10) {
+        if ((uint32_t)lane >= 10 && (uint32_t)lane < hclen)
+            S.cllens[c_clorder[lane]] = (uint8_t)((br.lo >> (3 * (lane - 10))) & 7);
+        br.drop(3 * (hclen - 10));
     }
     __syncwarp();
     CodeInfo ci = build_code(S, S.cllens, 19, S.dfirst, S.dcount, S.doff, S.dsym, lane);
@@ -309,46 +326,69 @@ __device__ int read_dynamic(WarpSmem& S, BitIn& br, int lane) {
     __syncwarp();
     const uint32_t total = hlit + hdist;
     uint32_t i = 0, prev = 0;
+    uint32_t kl = 0, kd = 0, nl = 0, nd = 0, ml = 0, md = 0;   // Kraft sums (units of 2^-15), counts, max lengths
+    bool eob = false;
     while (i < total) {
         br.refill();
         const uint32_t e = S.dist[br.peek(7)];
         const uint32_t s = e & 0xffu;
         br.drop(e >> 8);
+        uint32_t rep = 1, val;
         if (s < 16) {
-            if (lane == 0) S.lens[i] = (uint8_t)s;
+            val = s;
             prev = s;
-            ++i;
-            continue;
-        }
-        uint32_t rep, val = 0;
-        if (s == 16) {
+        } else if (s == 16) {
             if (i == 0) return CE_DATA;
             val = prev;
             rep = 3 + br.peek(2);
             br.drop(2);
         } else if (s == 17) {
+            val = 0;
             rep = 3 + br.peek(3);
             br.drop(3);
             prev = 0;
         } else {
+            val = 0;
             rep = 11 + br.peek(7);
             br.drop(7);
             prev = 0;
         }
         if (i + rep > total) return CE_DATA;
-        for (uint32_t j = lane; j < rep; j += 32) S.lens[i + j] = (uint8_t)val;
+        if (val) {
+            const uint32_t e2 = i + rep;
+            const uint32_t nlit = i < hlit ? ((e2 < hlit ? e2 : hlit) - i) : 0u;
+            const uint32_t ndst = rep - nlit;
+            kl += nlit * (32768u >> val);
+            kd += ndst * (32768u >> val);
+            nl += nlit;
+            nd += ndst;
+            if (nlit && val > ml) ml = val;
+            if (ndst && val > md) md = val;
+            if (i <= 256 && 256 < e2) eob = true;
+            if (kl > 32768u || kd > 32768u) return CE_DATA;       // over-subscribed
+        }
+        if (!HDR_ONLY) {
+            if (rep == 1) {
+                if (lane == 0) S.lens[i] = (uint8_t)val;
+            } else {
+                for (uint32_t j = lane; j < rep; j += 32) S.lens[i + j] = (uint8_t)val;
+            }
+        }
         i += rep;
     }
+    if (!eob) return CE_DATA;
+    if (!(kl == 32768u || (nl == 1 && ml == 1))) return CE_DATA;
+    if (!(kd == 32768u || nd == 0 || (nd == 1 && md == 1))) return CE_DATA;
+    if (HDR_ONLY) return CE_OK;
     __syncwarp();
-    if (S.lens[256] == 0) return CE_DATA;
     ci = build_code(S, S.lens, (int)hlit, S.lfirst, S.lcount, S.loff, S.lsym, lane);
-    if (ci.status < 0 || (ci.status > 0 && !(ci.ncodes == 1 && ci.maxlen == 1))) return CE_DATA;
+    if (ci.status < 0) return CE_DATA;
     __syncwarp();
-    fill_lut<LB>(S.lit, S.lfirst, S.lcount, S.loff, S.lsym, ci.maxlen, EK_LONG << 28, LitMake(), lane);
+    fill_lut<LB>(S.lit, S.lfirst, S.lcount, S.loff, S.lsym, ci.maxlen, K_LONG << 28,
+                 LitMake{S.lfirst, S.lcount, S.loff, S.lsym}, lane);
     if (lane == 0) S.lmax = (uint32_t)ci.maxlen;
     ci = build_code(S, S.lens + hlit, (int)hdist, S.dfirst, S.dcount, S.doff, S.dsym, lane);
-    if (ci.status < 0 || (ci.status > 0 && !(ci.ncodes == 0 || (ci.ncodes == 1 && ci.maxlen == 1))))
-        return CE_DATA;
+    if (ci.status < 0) return CE_DATA;
     __syncwarp();
     fill_lut<DB>(S.dist, S.dfirst, S.dcount, S.doff, S.dsym, ci.maxlen, DK_LONG << 8, DistMake(), lane);
     if (lane == 0) {
@@ -366,7 +406,8 @@ __device__ void build_fixed(WarpSmem& S, int lane) {
     __syncwarp();
     CodeInfo ci = build_code(S, S.lens, 288, S.lfirst, S.lcount, S.loff, S.lsym, lane);
     __syncwarp();
-    fill_lut<LB>(S.lit, S.lfirst, S.lcount, S.loff, S.lsym, ci.maxlen, EK_LONG << 28, LitMake(), lane);
+    fill_lut<LB>(S.lit, S.lfirst, S.lcount, S.loff, S.lsym, ci.maxlen, K_LONG << 28,
+                 LitMake{S.lfirst, S.lcount, S.loff, S.lsym}, lane);
     if (lane == 0) S.lmax = (uint32_t)ci.maxlen;
     ci = build_code(S, S.lens + 288, 32, S.dfirst, S.dcount, S.doff, S.dsym, lane);
     __syncwarp();
@@ -385,9 +426,8 @@ struct OutState {
     uint16_t* sym;     // the part's symbols; also its window
     uint64_t cap;
     uint64_t n;        // symbols so far (uniform)
-    uint64_t nph;      // this lane's placeholder count
-    uint64_t last_ph;  // this lane's largest (placeholder index + 1)
     bool known;        // the context before the part is empty (member start)
+    bool neg;          // this lane copied from before the part start (a placeholder source)
 };
 
 // the symbol at part position q: q < 0 lies in the symbolic context
@@ -395,32 +435,20 @@ __device__ __forceinline__ uint16_t sym_at(const uint16_t* out, int64_t q) {
     return q >= 0 ? out[q] : (uint16_t)(kPH | (uint32_t)(kWin + q));
 }
 
-__device__ __forceinline__ void note_ph(OutState& o, uint16_t v, uint64_t pos) {
-    if (v & kPH) {
-        o.nph++;
-        o.last_ph = pos + 1 > o.last_ph ? pos + 1 : o.last_ph;
-    }
-}
-
 // a copy whose source lies wholly before this batch: loads first, then stores
-__device__ __forceinline__ void copy_run(OutState& o, int64_t src, uint64_t dst, uint32_t len) {
-    uint16_t* out = o.sym;
+__device__ __forceinline__ void copy_run(uint16_t* out, int64_t src, uint64_t dst, uint32_t len) {
     for (uint32_t j0 = 0; j0 < len; j0 += 8) {
         uint16_t v[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) v[k] = (j0 + k < len) ? sym_at(out, src + j0 + k) : (uint16_t)0;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            if (j0 + k < len) {
-                out[dst + j0 + k] = v[k];
-                note_ph(o, v[k], dst + j0 + k);
-            }
-        }
+        for (int k = 0; k < 8; ++k)
+            if (j0 + k < len) out[dst + j0 + k] = v[k];
     }
 }
 
 // token: literal = (1 << 16) | byte; match = bit 31 | length << 16 | (distance - 1)
-__device__ int exec_batch(OutState& o, uint32_t tok, int ntok, int lane, uint64_t& block_n) {
+__device__ __forceinline__ int exec_batch(OutState& o, uint32_t tok, int ntok, int lane, uint64_t& block_n) {
     const bool valid = lane < ntok;
     const bool ism = valid && (tok >> 31);
     const uint32_t len = valid ? ((tok >> 16) & 0x1ffu) : 0u;
@@ -440,9 +468,14 @@ __device__ int exec_batch(OutState& o, uint32_t tok, int ntok, int lane, uint64_
     if (valid && !ism) out[start] = (uint16_t)(tok & 0xffu);
     if (ism) {
         const int64_t src = (int64_t)start - (int64_t)dist;
-        if (o.known && src < 0) bad = true;
-        else if (src + (int64_t)len <= (int64_t)base) copy_run(o, src, start, len);
-        else dep = true;
+        if (src < 0) {
+            if (o.known) bad = true;
+            o.neg = true;
+        }
+        if (!bad) {
+            if (src + (int64_t)len <= (int64_t)base) copy_run(out, src, start, len);
+            else dep = true;
+        }
     }
     if (__any_sync(FULL, bad)) return CE_DIST;
     __syncwarp();
@@ -455,9 +488,7 @@ __device__ int exec_batch(OutState& o, uint32_t tok, int ntok, int lane, uint64_
         const uint32_t kd = __shfl_sync(FULL, dist, k);
         for (uint32_t j = lane; j < kl; j += 32) {
             const uint32_t jj = kd >= kl ? j : j % kd;
-            const uint16_t v = sym_at(out, (int64_t)ks - (int64_t)kd + jj);
-            out[ks + j] = v;
-            note_ph(o, v, ks + j);
+            out[ks + j] = sym_at(out, (int64_t)ks - (int64_t)kd + jj);
         }
         __syncwarp();
     }
@@ -468,77 +499,95 @@ __device__ int exec_batch(OutState& o, uint32_t tok, int ntok, int lane, uint64_
 
 __device__ __forceinline__ bool allowed_has(const uint32_t* a, uint32_t b) { return (a[b >> 5] >> (b & 31)) & 1u; }
 
-__device__ int huff_block(WarpSmem& S, BitIn& br, OutState& o, bool check, uint64_t max_block, uint64_t end_bit,
+// Up to 32 tokens of a Huffman block; lane t keeps token t.  SAFE: every
+// word this batch can read lies inside the member (no bounds checks).
+template <bool SAFE, bool CHECK>
+__device__ __forceinline__ int decode_batch(WarpSmem& S, BitIn& br, int lane, uint32_t& mytok, int& ntok, bool& eob) {
+#pragma unroll 1
+    while (ntok < 32) {
+        br.refill<SAFE>();
+        uint32_t e = S.lit[br.lo & ((1u << LB) - 1u)];
+        uint32_t k = e >> 28;
+        if (k <= K_LIT2) {
+            const uint32_t b = (e >> 8) & 0xffu;
+            if (k == K_LIT2 && ntok < 31) {
+                const uint32_t b2 = (e >> 16) & 0xffu;
+                if (CHECK && !(allowed_has(S.allowed, b) && allowed_has(S.allowed, b2))) return CE_BYTE;
+                br.drop(e & 31u);
+                if (lane == ntok) mytok = 0x10000u | b;
+                if (lane == ntok + 1) mytok = 0x10000u | b2;
+                ntok += 2;
+                continue;
+            }
+            if (CHECK && !allowed_has(S.allowed, b)) return CE_BYTE;
+            br.drop(k == K_LIT ? (e & 31u) : ((e >> 24) & 15u));
+            if (lane == ntok) mytok = 0x10000u | b;
+            ++ntok;
+            continue;
+        }
+        if (k >= K_LONG) {
+            uint32_t L = 0;
+            const int s = k == K_LONG
+                              ? decode_long(br.peek(15), LB, S.lfirst, S.lcount, S.loff, S.lsym, (int)S.lmax, L)
+                              : -1;
+            if (s < 0) return CE_DATA;
+            e = lit_entry((uint32_t)s, L, 0);
+            k = e >> 28;
+            if (k == K_BAD) return CE_DATA;
+            if (k == K_LIT) {
+                const uint32_t b = (e >> 8) & 0xffu;
+                if (CHECK && !allowed_has(S.allowed, b)) return CE_BYTE;
+                br.drop(e & 31u);
+                if (lane == ntok) mytok = 0x10000u | b;
+                ++ntok;
+                continue;
+            }
+        }
+        if (k == K_EOB) {
+            br.drop(e & 31u);
+            eob = true;
+            return CE_OK;
+        }
+        uint32_t len = (e >> 8) & 0x1ffu, dn = e & 31u;
+        if (k == K_LENX) {
+            const uint32_t eb = (e >> 17) & 7u;
+            len += (br.lo >> dn) & ((1u << eb) - 1u);
+            dn += eb;
+        }
+        br.drop(dn);
+        br.refill<SAFE>();
+        uint32_t d = S.dist[br.lo & ((1u << DB) - 1u)];
+        if (d & 0x300u) {
+            if ((d & 0x300u) != (DK_LONG << 8)) return CE_DATA;
+            uint32_t L = 0;
+            const int s = decode_long(br.peek(15), DB, S.dfirst, S.dcount, S.doff, S.dsym, (int)S.dmax, L);
+            if (s < 0) return CE_DATA;
+            d = dist_entry((uint32_t)s, L);
+            if (d & 0x300u) return CE_DATA;
+        }
+        const uint32_t dl = d & 15u, de = (d >> 4) & 15u;
+        const uint32_t dist = (d >> 16) + ((br.lo >> dl) & ((1u << de) - 1u));
+        br.drop(dl + de);
+        if (lane == ntok) mytok = 0x80000000u | (len << 16) | (dist - 1u);
+        ++ntok;
+    }
+    return CE_OK;
+}
+
+template <bool CHECK>
+__device__ int huff_block(WarpSmem& S, BitIn& br, OutState& o, uint64_t max_block, uint64_t end_bit,
                           uint64_t& block_n, int lane) {
     for (;;) {
         uint32_t mytok = 0;
         int ntok = 0;
-        int st = CE_OK;
         bool eob = false;
-        while (ntok < 32) {
-            br.refill();
-            uint32_t e = S.lit[br.peek(LB)];
-            if ((e >> 28) == EK_LONG) {
-                uint32_t L = 0;
-                const int s = decode_long(br.peek(15), LB, S.lfirst, S.lcount, S.loff, S.lsym, (int)S.lmax, L);
-                if (s < 0) {
-                    st = CE_DATA;
-                    break;
-                }
-                e = lit_entry((uint32_t)s, L);
-            }
-            const uint32_t kind = e >> 28;
-            uint32_t tok;
-            if (kind == EK_LIT) {
-                const uint32_t b = (e >> 8) & 0xffu;
-                br.drop(e & 15u);
-                if (check && !allowed_has(S.allowed, b)) {
-                    st = CE_BYTE;
-                    break;
-                }
-                tok = (1u << 16) | b;
-            } else if (kind == EK_LEN) {
-                const uint32_t cl = e & 15u, eb = (e >> 4) & 15u;
-                const uint32_t len = ((e >> 16) & 0x1ffu) + ((uint32_t)(br.buf >> cl) & ((1u << eb) - 1u));
-                br.drop(cl + eb);
-                br.refill();
-                uint32_t d = S.dist[br.peek(DB)];
-                if ((d >> 8) & 3u) {
-                    if (((d >> 8) & 3u) != DK_LONG) {
-                        st = CE_DATA;
-                        break;
-                    }
-                    uint32_t L = 0;
-                    const int s = decode_long(br.peek(15), DB, S.dfirst, S.dcount, S.doff, S.dsym, (int)S.dmax, L);
-                    if (s < 0) {
-                        st = CE_DATA;
-                        break;
-                    }
-                    d = dist_entry((uint32_t)s, L);
-                    if ((d >> 8) & 3u) {
-                        st = CE_DATA;
-                        break;
-                    }
-                }
-                const uint32_t dl = d & 15u, de = (d >> 4) & 15u;
-                const uint32_t dist = (d >> 16) + ((uint32_t)(br.buf >> dl) & ((1u << de) - 1u));
-                br.drop(dl + de);
-                tok = 0x80000000u | (len << 16) | (dist - 1u);
-            } else if (kind == EK_EOB) {
-                br.drop(e & 15u);
-                eob = true;
-                break;
-            } else {
-                st = CE_DATA;
-                break;
-            }
-            if (lane == ntok) mytok = tok;
-            ++ntok;
-        }
+        // a batch reads at most 32 * 48 bits (48 words) plus one word ahead
+        const int st = (uint64_t)br.wi + 52 < br.nfull ? decode_batch<true, CHECK>(S, br, lane, mytok, ntok, eob)
+                                                       : decode_batch<false, CHECK>(S, br, lane, mytok, ntok, eob);
         if (st) return st;
         if (ntok) {
-            st = exec_batch(o, mytok, ntok, lane, block_n);
-            if (st) return st;
+            const int e = exec_batch(o, mytok, ntok, lane, block_n);
+            if (e) return e;
         }
         if (br.pos() > end_bit) return CE_TRUNC;
         if (max_block && block_n >= max_block) return CE_SIZE;
@@ -589,15 +638,19 @@ __device__ int one_block(WarpSmem& S, BitIn& br, OutState& o, bool check, uint64
     int st;
     if (type == 0) {
         st = stored_block(br, o, check, S.allowed, end_bit, block_n, lane);
-    } else if (type == 1) {
-        if (S.table_kind != 1) build_fixed(S, lane);
-        st = huff_block(S, br, o, check, max_block, end_bit, block_n, lane);
-    } else if (type == 2) {
-        st = read_dynamic(S, br, lane);
-        if (st == CE_OK && br.pos() > end_bit) st = CE_TRUNC;
-        if (st == CE_OK) st = huff_block(S, br, o, check, max_block, end_bit, block_n, lane);
-    } else {
+    } else if (type == 3) {
         st = CE_DATA;
+    } else {
+        if (type == 1) {
+            if (S.table_kind != 1) build_fixed(S, lane);
+            st = CE_OK;
+        } else {
+            st = read_dynamic<false>(S, br, lane);
+            if (st == CE_OK && br.pos() > end_bit) st = CE_TRUNC;
+        }
+        if (st == CE_OK)
+            st = check ? huff_block<true>(S, br, o, max_block, end_bit, block_n, lane)
+                       : huff_block<false>(S, br, o, max_block, end_bit, block_n, lane);
     }
     if (st == CE_OK && max_block && block_n >= max_block) st = CE_SIZE;
     if (st == CE_OK && block_n < min_block) st = CE_SIZE;
@@ -605,119 +658,47 @@ __device__ int one_block(WarpSmem& S, BitIn& br, OutState& o, bool check, uint64
 }
 
 // ---------------------------------------------------------------------------
-// block-start candidates: header checks of one bit offset, by one lane.
-// A necessary condition for the full checks (which one_block repeats
-// exactly): every offset that passes them passes here.
+// block-start candidates.  Per bit offset p, in order of cost:
+//  1. BFINAL = 0, BTYPE = 10, HLIT <= 29, HDIST <= 29: bit-parallel over the
+//     32 offsets of a lane;
+//  2. the code-length code is complete: sum of 2^-l over its lengths is 1,
+//     from a 512-entry table of three-field sums;
+//  3. the whole dynamic header is valid (read_dynamic<true>), one offset at a
+//     time by the whole warp, lowest offset first.
+// The full block decode then follows in k_sync.  Stages 1-3 are implied by
+// the complete checks, so no offset that passes those is dropped here.
 // ---------------------------------------------------------------------------
-__device__ bool header_ok(const FileDesc& F, uint64_t p) {
-    BitIn br;
-    br.setup(F.gz, F.gz_len);
-    br.seek(p + 3);
-    const uint32_t hlit = br.peek(5) + 257;
-    br.drop(5);
-    const uint32_t hdist = br.peek(5) + 1;
-    br.drop(5);
-    const uint32_t hclen = br.peek(4) + 4;
-    br.drop(4);
-    br.refill();
-    uint64_t clb = 0;
-    uint32_t kraft = 0;
-    for (uint32_t k = 0; k < hclen; ++k) {
-        if (k == 10) br.refill();
-        const uint32_t l = br.peek(3);
-        br.drop(3);
-        clb |= (uint64_t)l << (3 * c_clorder[k]);
-        if (l) kraft += 128u >> l;
-    }
-    if (kraft != 128u) return false;                 // code-length code must be complete
-    uint32_t cnt[8], first[8], off[8], nxt[8];
-    uint8_t sorted[19];
-    for (int L = 0; L < 8; ++L) cnt[L] = 0;
-    for (int s = 0; s < 19; ++s) cnt[(clb >> (3 * s)) & 7]++;
-    cnt[0] = 0;
-    uint32_t code = 0, o = 0;
-    first[0] = off[0] = 0;
-    for (int L = 1; L < 8; ++L) {
-        code = (code + cnt[L - 1]) << 1;
-        first[L] = code;
-        off[L] = o;
-        nxt[L] = o;
-        o += cnt[L];
-    }
-    for (int s = 0; s < 19; ++s) {
-        const uint32_t l = (clb >> (3 * s)) & 7;
-        if (l) sorted[nxt[l]++] = (uint8_t)s;
-    }
-    uint32_t kl = 0, kd = 0, nl = 0, nd = 0, ml = 0, md = 0, i = 0, prev = 0;
-    bool eob = false;
-    const uint32_t total = hlit + hdist;
-    while (i < total) {
-        br.refill();
-        const uint32_t v = __brev(br.peek(7)) >> 25;
-        int s = -1;
-        uint32_t L = 1;
-        for (; L < 8; ++L) {
-            const uint32_t d = (v >> (7 - L)) - first[L];
-            if (d < cnt[L]) {
-                s = sorted[off[L] + d];
-                break;
-            }
-        }
-        if (s < 0) return false;
-        br.drop(L);
-        uint32_t val, rep;
-        if (s < 16) {
-            val = (uint32_t)s;
-            rep = 1;
-            prev = val;
-        } else if (s == 16) {
-            if (i == 0) return false;
-            val = prev;
-            rep = 3 + br.peek(2);
-            br.drop(2);
-        } else if (s == 17) {
-            val = 0;
-            rep = 3 + br.peek(3);
-            br.drop(3);
-            prev = 0;
-        } else {
-            val = 0;
-            rep = 11 + br.peek(7);
-            br.drop(7);
-            prev = 0;
-        }
-        if (i + rep > total) return false;
-        if (val) {
-            const uint32_t e = i + rep;
-            const uint32_t nlit = i < hlit ? ((e < hlit ? e : hlit) - i) : 0u;
-            const uint32_t ndst = rep - nlit;
-            kl += nlit * (32768u >> val);
-            kd += ndst * (32768u >> val);
-            nl += nlit;
-            nd += ndst;
-            if (nlit && val > ml) ml = val;
-            if (ndst && val > md) md = val;
-            if (i <= 256 && 256 < e) eob = true;
-            if (kl > 32768u || kd > 32768u) return false;   // over-subscribed
-        }
-        i += rep;
-        if (br.pos() > F.end_bit) return false;
-    }
-    if (!eob) return false;
-    if (!(kl == 32768u || (nl == 1 && ml == 1))) return false;
-    if (!(kd == 32768u || nd == 0 || (nd == 1 && md == 1))) return false;
-    return true;
+__device__ __forceinline__ uint32_t fsr(uint32_t lo, uint32_t hi, uint32_t s) { return __funnelshift_r(lo, hi, s); }
+
+// 3-field Kraft sums in units of 2^-7: kraft3[a | b << 3 | c << 6]
+__device__ __forceinline__ uint32_t kraft1(uint32_t l) { return l ? (128u >> l) : 0u; }
+
+__device__ uint32_t cl_complete(const uint16_t* kraft3, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3, uint32_t k) {
+    // bits of the window from offset k + 13 (HCLEN) onward; k < 32
+    const uint32_t q = k + 13;                   // < 45
+    const uint32_t a0 = q < 32 ? fsr(w0, w1, q) : fsr(w1, w2, q - 32);
+    const uint32_t hclen = (a0 & 15u) + 4;
+    const uint32_t q1 = q + 4, q2 = q + 34;      // 10 fields, then 9 fields
+    const uint32_t f1 = q1 < 32 ? fsr(w0, w1, q1) : fsr(w1, w2, q1 - 32);
+    const uint32_t f2 = q2 < 64 ? fsr(w1, w2, q2 - 32) : fsr(w2, w3, q2 - 64);
+    const uint64_t fields = (uint64_t)(f1 & 0x3fffffffu) | ((uint64_t)(f2 & 0x7ffffffu) << 30);
+    const uint64_t x = fields & ((1ull << (3 * hclen)) - 1ull);
+    uint32_t kr = 0;
+#pragma unroll
+    for (int g = 0; g < 7; ++g) kr += kraft3[(x >> (9 * g)) & 511u];
+    return kr == 128u;
 }
 
-// least bit of [lo, hi) passing header_ok; the warp tests 1024 offsets per step
-__device__ uint64_t find_candidate(const FileDesc& F, uint64_t lo, uint64_t hi, int lane) {
+__device__ uint64_t find_candidate(WarpSmem& S, const uint16_t* kraft3, const FileDesc& F, uint64_t lo, uint64_t hi,
+                                   int lane) {
     BitIn w;
     w.setup(F.gz, F.gz_len);
     if (hi > F.end_bit) hi = F.end_bit;
     for (uint64_t T = lo & ~1023ull; T < hi; T += 1024) {
         const uint64_t base = T + 32ull * (uint64_t)lane;
         const uint64_t wi = base >> 5;
-        const uint64_t x = (uint64_t)w.word(wi) | ((uint64_t)w.word(wi + 1) << 32);
+        const uint32_t w0 = w.word(wi), w1 = w.word(wi + 1), w2 = w.word(wi + 2), w3 = w.word(wi + 3);
+        const uint64_t x = (uint64_t)w0 | ((uint64_t)w1 << 32);
         uint64_t y = ~x & ~(x >> 1) & (x >> 2);                // BFINAL = 0, BTYPE = 10
         y &= ~((x >> 4) & (x >> 5) & (x >> 6) & (x >> 7));     // HLIT <= 29
         y &= ~((x >> 9) & (x >> 10) & (x >> 11) & (x >> 12));  // HDIST <= 29
@@ -727,17 +708,23 @@ __device__ uint64_t find_candidate(const FileDesc& F, uint64_t lo, uint64_t hi, 
             m = d >= 32 ? 0u : (m & (~0u << d));
         }
         if (base + 32 > hi) m = base >= hi ? 0u : (m & ((1u << (uint32_t)(hi - base)) - 1u));
-        uint64_t found = kNone;
-        while (m) {
-            const int k = __ffs(m) - 1;
-            m &= m - 1;
-            if (header_ok(F, base + (uint64_t)k)) {
-                found = base + (uint64_t)k;
-                break;
-            }
+        uint32_t c = 0;
+        for (uint32_t mm = m; mm; mm &= mm - 1) {
+            const uint32_t k = __ffs(mm) - 1;
+            if (cl_complete(kraft3, w0, w1, w2, w3, k)) c |= 1u << k;
         }
-        const uint32_t b = __ballot_sync(FULL, found != kNone);
-        if (b) return shfl64(found, __ffs(b) - 1);
+        // lowest first: lanes cover increasing offsets
+        for (uint32_t b = __ballot_sync(FULL, c != 0); b; b = __ballot_sync(FULL, c != 0)) {
+            const int l = __ffs(b) - 1;
+            const uint32_t cl = __shfl_sync(FULL, c, l);
+            const uint32_t k = __ffs(cl) - 1;
+            if (lane == l) c &= c - 1;
+            const uint64_t p = T + 32ull * (uint64_t)l + k;
+            BitIn br;
+            br.setup(F.gz, F.gz_len);
+            br.seek(p + 3);
+            if (read_dynamic<true>(S, br, lane) == CE_OK && br.pos() <= F.end_bit) return p;
+        }
     }
     return kNone;
 }
@@ -753,11 +740,17 @@ __device__ __forceinline__ void init_smem(WarpSmem& S, const KParams& p, int lan
     __syncwarp();
 }
 
+constexpr int kWarpsPerBlock = 4;
+
 // ---------------------------------------------------------------------------
 // k_sync: block start of each part and its first block
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_sync(const FileDesc* __restrict__ files, ChunkDesc* chunks, int nchunks,
-                                              uint16_t* symbuf, KParams p) {
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, 8)
+    k_sync(const FileDesc* __restrict__ files, ChunkDesc* chunks, int nchunks, uint16_t* symbuf, KParams p) {
+    __shared__ uint16_t kraft3[512];
+    for (uint32_t v = threadIdx.x; v < 512; v += blockDim.x)
+        kraft3[v] = (uint16_t)(kraft1(v & 7) + kraft1((v >> 3) & 7) + kraft1(v >> 6));
+    __syncthreads();
     WarpSmem& S = warp_smem();
     const int lane = threadIdx.x & 31;
     const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -765,7 +758,7 @@ __global__ void __launch_bounds__(128) k_sync(const FileDesc* __restrict__ files
     ChunkDesc& C = chunks[c];
     const FileDesc& F = files[C.file];
     init_smem(S, p, lane);
-    OutState o{symbuf + C.sym_base, C.cap, 0, 0, 0, C.index == 0 && C.lo <= F.s0_bit};
+    OutState o{symbuf + C.sym_base, C.cap, 0, C.index == 0 && C.lo <= F.s0_bit, false};
     BitIn br;
     br.setup(F.gz, F.gz_len);
     uint32_t state = CS_EMPTY, err = CE_OK, final = 0;
@@ -786,12 +779,11 @@ __global__ void __launch_bounds__(128) k_sync(const FileDesc* __restrict__ files
     } else {
         uint64_t lo = C.lo;
         for (;;) {
-            const uint64_t cand = find_candidate(F, lo, C.hi, lane);
+            const uint64_t cand = find_candidate(S, kraft3, F, lo, C.hi, lane);
             if (cand == kNone) break;
             br.seek(cand);
             o.n = 0;
-            o.nph = 0;
-            o.last_ph = 0;
+            o.neg = false;
             const int st = one_block(S, br, o, true, p.min_block, p.max_block, true, F.end_bit, final, lane);
             if (st == CE_OK) {
                 state = CS_FOUND;
@@ -808,15 +800,16 @@ __global__ void __launch_bounds__(128) k_sync(const FileDesc* __restrict__ files
             lo = cand + 1;
         }
     }
-    const uint64_t nph = warp_sum64(o.nph), last_ph = warp_max64(o.last_ph);
+    const bool neg = __any_sync(FULL, o.neg);
     if (lane == 0) {
         C.state = state;
         C.err = err;
         C.sync = sync;
         C.resume = resume;
         C.n = state == CS_FOUND ? o.n : 0;
-        C.nph = nph;
-        C.last_ph = last_ph;
+        C.nph = 0;
+        C.last_ph = 0;
+        C.anyph = neg && state == CS_FOUND;
         C.blocks = state == CS_FOUND ? 1u : 0u;
         C.final = final && state == CS_FOUND;
         C.end = resume;
@@ -826,8 +819,8 @@ __global__ void __launch_bounds__(128) k_sync(const FileDesc* __restrict__ files
 // ---------------------------------------------------------------------------
 // k_inflate: pass 1 of each part up to the next part's block start
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_inflate(const FileDesc* __restrict__ files, ChunkDesc* chunks, int nchunks,
-                                                 uint16_t* symbuf, KParams p) {
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, 8)
+    k_inflate(const FileDesc* __restrict__ files, ChunkDesc* chunks, int nchunks, uint16_t* symbuf, KParams p) {
     WarpSmem& S = warp_smem();
     const int lane = threadIdx.x & 31;
     const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -835,28 +828,23 @@ __global__ void __launch_bounds__(128) k_inflate(const FileDesc* __restrict__ fi
     ChunkDesc& C = chunks[c];
     if (C.state != CS_FOUND) return;
     const FileDesc& F = files[C.file];
-    init_smem(S, p, lane);
-    // the next part that holds a block start; a part whose search failed
-    // stops this one at its nominal start (the run is repeated anyway)
+    // the next part that holds a block start.  `sync` is final after k_sync
+    // and never written here (other warps of this kernel rewrite `state`).
     uint64_t stop = C.stop_hint;
     for (int j = c + 1; j < F.chunk0 + F.nchunks; ++j) {
-        const uint32_t s = chunks[j].state;
-        if (s == CS_FOUND) {
-            stop = chunks[j].sync;
-            break;
-        }
-        if (s == CS_ERROR) {
-            stop = chunks[j].lo;
+        const uint64_t sj = chunks[j].sync;
+        if (sj != kNone) {
+            stop = sj;
             break;
         }
     }
-    OutState o{symbuf + C.sym_base, C.cap, C.n, lane == 0 ? C.nph : 0, lane == 0 ? C.last_ph : 0,
-               C.index == 0 && C.sync == F.s0_bit};
+    OutState o{symbuf + C.sym_base, C.cap, C.n, C.index == 0 && C.sync == F.s0_bit, false};
     uint32_t blocks = C.blocks, final = C.final, err = CE_OK;
     uint64_t end = C.resume;
     if (final) {
         if (stop != kNone) err = CE_CHAIN;
-    } else {
+    } else if (!(stop != kNone && C.resume == stop)) {
+        init_smem(S, p, lane);
         BitIn br;
         br.setup(F.gz, F.gz_len);
         br.seek(C.resume);
@@ -885,13 +873,12 @@ __global__ void __launch_bounds__(128) k_inflate(const FileDesc* __restrict__ fi
     if (err == CE_OK && final && F.mode != 2) {          // the trailer must follow the final block
         if (((end + 7) >> 3) + 8 != F.gz_len) err = CE_TRAIL;
     }
-    const uint64_t nph = warp_sum64(o.nph), last_ph = warp_max64(o.last_ph);
+    const bool neg = __any_sync(FULL, o.neg);
     if (lane == 0) {
         C.state = err ? CS_ERROR : CS_DONE;
         C.err = err;
         C.n = o.n;
-        C.nph = nph;
-        C.last_ph = last_ph;
+        C.anyph = C.anyph | (neg ? 1u : 0u);
         C.blocks = blocks;
         C.final = final;
         C.end = end;
@@ -1061,23 +1048,29 @@ __global__ void __launch_bounds__(1024) k_chain_expand(const FileDesc* __restric
 // ---------------------------------------------------------------------------
 constexpr uint32_t kTile = 65536;   // symbols per block
 
-__global__ void __launch_bounds__(1024) k_translate(const FileDesc* __restrict__ files,
-                                                    const ChunkDesc* __restrict__ chunks, uint32_t tiles_per_chunk,
-                                                    const uint16_t* __restrict__ sym, const uint8_t* __restrict__ windows,
+__global__ void __launch_bounds__(1024) k_translate(const FileDesc* __restrict__ files, ChunkDesc* chunks,
+                                                    uint32_t tiles_per_chunk, const uint16_t* __restrict__ sym,
+                                                    const uint8_t* __restrict__ windows,
                                                     const uint8_t* __restrict__ fillw) {
     __shared__ __align__(16) uint8_t W[kWin];
+    __shared__ unsigned long long s_nph, s_last;
     const uint32_t c = blockIdx.x / tiles_per_chunk, tile = blockIdx.x % tiles_per_chunk;
-    const ChunkDesc& C = chunks[c];
+    ChunkDesc& C = chunks[c];
     const FileDesc& F = files[C.file];
     if (F.status != PGZ_OK || C.state != CS_DONE) return;
     const uint64_t t0 = (uint64_t)tile * kTile;
     if (t0 >= C.n) return;
     const uint64_t t1 = t0 + kTile < C.n ? t0 + kTile : C.n;
-    if (t0 < C.last_ph) {
+    const bool ph = C.anyph != 0;
+    if (threadIdx.x == 0) {
+        s_nph = 0;
+        s_last = 0;
+    }
+    if (ph) {
         const uint4* src = reinterpret_cast<const uint4*>(fillw ? fillw : windows + (uint64_t)c * kWin);
         for (uint32_t k = threadIdx.x; k < kWin / 16; k += blockDim.x) reinterpret_cast<uint4*>(W)[k] = src[k];
-        __syncthreads();
     }
+    __syncthreads();
     const uint16_t* s = sym + C.sym_base;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     // output byte P of the member goes to out[P - out_lo] when out_lo <= P < out_hi
@@ -1085,6 +1078,8 @@ __global__ void __launch_bounds__(1024) k_translate(const FileDesc* __restrict__
     const uint64_t lo = F.out_lo, hi = F.out_hi;
     const bool vec = F.out_lo == 0 && F.out_hi == kNone && ((reinterpret_cast<uintptr_t>(out) & 7) == 0);
     const uint32_t m = (uint32_t)(C.out_off & 7);
+    uint32_t nph = 0;
+    uint64_t last = 0;
     for (uint64_t wb = t0 + 256ull * warp; wb < t1; wb += 256ull * nwarp) {
         const uint64_t i = wb + 8ull * lane;
         uint32_t nv = 0;
@@ -1096,8 +1091,15 @@ __global__ void __launch_bounds__(1024) k_translate(const FileDesc* __restrict__
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const uint32_t v = (w4[k >> 1] >> (16 * (k & 1))) & 0xffffu;
-                const uint32_t b = (v & kPH) ? W[v & (kWin - 1)] : (v & 0xffu);
-                if ((uint32_t)k < nv) val |= (uint64_t)b << (8 * k);
+                if ((uint32_t)k < nv) {
+                    uint32_t b = v & 0xffu;
+                    if (v & kPH) {
+                        b = W[v & (kWin - 1)];
+                        ++nph;
+                        last = i + k + 1;
+                    }
+                    val |= (uint64_t)b << (8 * k);
+                }
             }
         }
         const uint64_t P = C.out_off + i;
@@ -1124,6 +1126,22 @@ __global__ void __launch_bounds__(1024) k_translate(const FileDesc* __restrict__
         const bool tail_by_next = lane < 31 && nv == 8 && next_nv >= head;
         if (!tail_by_next)
             for (uint32_t k = head; k < nv; ++k) out[P + k] = (uint8_t)(val >> (8 * k));
+    }
+    if (ph) {                                         // placeholder count and extent of the part
+        for (int d = 16; d; d >>= 1) {
+            nph += __shfl_xor_sync(FULL, nph, d);
+            const uint64_t o = shfl64(last, lane ^ d);
+            last = o > last ? o : last;
+        }
+        if (lane == 0) {
+            atomicAdd(&s_nph, (unsigned long long)nph);
+            atomicMax(&s_last, (unsigned long long)last);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            atomicAdd(reinterpret_cast<unsigned long long*>(&C.nph), s_nph);
+            atomicMax(reinterpret_cast<unsigned long long*>(&C.last_ph), s_last);
+        }
     }
 }
 
@@ -1226,14 +1244,14 @@ static size_t warp_smem_bytes() { return sizeof(WarpSmem); }
 void launch_sync(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, const KParams& p,
                  cudaStream_t s) {
     if (nchunks <= 0) return;
-    const int wpb = 4;
+    const int wpb = kWarpsPerBlock;
     k_sync<<<(nchunks + wpb - 1) / wpb, 32 * wpb, wpb * warp_smem_bytes(), s>>>(files, chunks, nchunks, sym, p);
 }
 
 void launch_inflate(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, const KParams& p,
                     cudaStream_t s) {
     if (nchunks <= 0) return;
-    const int wpb = 4;
+    const int wpb = kWarpsPerBlock;
     k_inflate<<<(nchunks + wpb - 1) / wpb, 32 * wpb, wpb * warp_smem_bytes(), s>>>(files, chunks, nchunks, sym, p);
 }
 
@@ -1258,7 +1276,7 @@ void launch_chain(const FileDesc* files, const ChunkDesc* chunks, int nfiles, in
     k_chain_expand<<<ngroups, 1024, 2 * kWin, s>>>(files, chunks, g0, gn, gfile, sym, wstart, windows);
 }
 
-void launch_translate(const FileDesc* files, const ChunkDesc* chunks, int nchunks, uint64_t max_cap,
+void launch_translate(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint64_t max_cap,
                       const uint16_t* sym, const uint8_t* windows, const uint8_t* fillw, cudaStream_t s) {
     if (nchunks <= 0) return;
     const uint32_t tpc = (uint32_t)((max_cap + kTile - 1) / kTile);
