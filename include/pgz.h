@@ -176,6 +176,26 @@ int pgz_inspect_parts(pgz_ctx* ctx, int n, uint64_t* start_bit, uint64_t* nsym,
 int pgz_inspect_symbols(pgz_ctx* ctx, int part, uint16_t* host_dst, uint64_t cap, uint64_t* nsym);
 int pgz_inspect_window(pgz_ctx* ctx, int part, uint8_t* host_dst /* 32768 bytes */);
 
+/* Whole-member decompression that allocates nothing (the paper has no
+   counterpart; this is a deployment convenience).  For callers that cannot let
+   a library allocate device memory -- applications that give all GPU memory
+   to their own allocator at start-up, services with a fixed device-memory
+   budget, loops that cannot afford cudaFree's device-wide synchronisation --
+   it runs the same kernels as pgz_decompress with every scratch buffer inside
+   one fixed file-scope __device__ array of about 19 MiB, held on each GPU that
+   loads the library until the process exits.  No cudaMalloc, cudaFree or other
+   allocating routine is called.
+   gz [device, 4-byte aligned, gz_len bytes], out [device, out_cap bytes] on
+   the current device; cuda_stream: the cudaStream_t to use (NULL = default).
+   Limits: output (ISIZE) <= 4 MiB, gz_len <= 4 MiB + 64 KiB + 4 KiB, gzip
+   header <= 4 KiB; larger inputs return PGZ_E_ARG.  The first call on a device
+   sets up the array's address there; make it before any stream capture.
+   Calls share the array: calls that overlap on the GPU (other streams or
+   threads) race and must be serialised by the caller.  Default configuration
+   (pgz_config_init).  *out_len as for pgz_decompress. */
+int pgz_decompress_noalloc(const uint8_t* gz, uint64_t gz_len, uint8_t* out, uint64_t out_cap,
+                           uint64_t* out_len, void* cuda_stream);
+
 /* Number of kernels this library launched on ctx since it was created. */
 uint64_t pgz_kernel_launches(const pgz_ctx* ctx);
 

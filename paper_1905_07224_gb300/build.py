@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpgz.so")
-SOURCES = ["pgz_kernels.cu", "pgz_host.cu"]
+SOURCES = ["pgz_kernels.cu", "pgz_host.cu", "pgz_noalloc.cu"]
 HEADERS = ["pgz_internal.h", os.path.join("..", "..", "include", "pgz.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

@@ -76,6 +76,7 @@ def _load():
         "pgz_inspect_symbols": (ctypes.c_int, [VP, ctypes.c_int, VP, U64, P(U64)]),
         "pgz_inspect_window": (ctypes.c_int, [VP, ctypes.c_int, VP]),
         "pgz_kernel_launches": (U64, [VP]),
+        "pgz_decompress_noalloc": (ctypes.c_int, [VP, U64, VP, U64, P(U64), VP]),
         "pgz_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
@@ -98,7 +99,8 @@ def lib():
 EXPORTED = ["pgz_config_init", "pgz_create", "pgz_destroy", "pgz_decompress", "pgz_decompress_host",
             "pgz_decompress_at", "pgz_decompress_batch", "pgz_batch_prepare", "pgz_batch_run", "pgz_batch_free",
             "pgz_index_build", "pgz_index_info", "pgz_decompress_range", "pgz_index_free", "pgz_inspect_parts",
-            "pgz_inspect_symbols", "pgz_inspect_window", "pgz_kernel_launches", "pgz_strerror"]
+            "pgz_inspect_symbols", "pgz_inspect_window", "pgz_kernel_launches", "pgz_strerror",
+            "pgz_decompress_noalloc"]
 
 
 def pgz_strerror(status: int) -> str:
@@ -252,3 +254,10 @@ def pgz_inspect_window(ctx: int, part: int) -> np.ndarray:
 
 def pgz_kernel_launches(ctx: int) -> int:
     return int(lib().pgz_kernel_launches(ctx))
+
+
+def pgz_decompress_noalloc(gz_ptr: int, gz_len: int, out_ptr: int, out_cap: int, stream: int | None = None):
+    """(status, out_len): decompression with no device allocation (fixed scratch); device addresses."""
+    n = U64(0)
+    r = lib().pgz_decompress_noalloc(gz_ptr, gz_len, out_ptr, out_cap, ctypes.byref(n), stream)
+    return r, n.value
