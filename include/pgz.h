@@ -182,7 +182,7 @@ int pgz_inspect_window(pgz_ctx* ctx, int part, uint8_t* host_dst /* 32768 bytes 
    to their own allocator at start-up, services with a fixed device-memory
    budget, loops that cannot afford cudaFree's device-wide synchronisation --
    it runs the same kernels as pgz_decompress with every scratch buffer inside
-   one fixed file-scope __device__ array of about 19 MiB, held on each GPU that
+   one fixed file-scope __device__ array of about 23 MiB, held on each GPU that
    loads the library until the process exits.  No cudaMalloc, cudaFree or other
    allocating routine is called.
    gz [device, 4-byte aligned, gz_len bytes], out [device, out_cap bytes] on

@@ -19,6 +19,7 @@ using namespace pgz;
 namespace {
 
 constexpr uint64_t kSegBytes = 4096;
+constexpr uint64_t kMaxPartSymbols = (1ull << 31) - 256;   // part positions are 32-bit in the kernels
 constexpr int kMaxRetries = 32;
 
 struct DBuf {
@@ -124,7 +125,7 @@ struct Plan {
     bool chain = true, translate = true, crc = true;
     bool results_valid = false;   // the device chunk array holds the last run's results
     const uint8_t* fill = nullptr;   // device window of fill bytes (mode 1)
-    DBuf d_files, d_chunks, d_g0, d_gn, d_gfile, d_seg0, d_sym, d_windows, d_gmaps, d_wstart;
+    DBuf d_files, d_chunks, d_g0, d_gn, d_gfile, d_seg0, d_sym, d_windows, d_gmaps, d_wstart, d_tok;
     PBuf h_files, h_chunks;
     cudaGraphExec_t graph = nullptr;
     void release() {
@@ -138,6 +139,7 @@ struct Plan {
         d_windows.release();
         d_gmaps.release();
         d_wstart.release();
+        d_tok.release();
         h_files.release();
         h_chunks.release();
         if (graph) cudaGraphExecDestroy(graph);
@@ -228,7 +230,7 @@ void plan_member(pgz_ctx* ctx, Plan& P, const uint8_t* gz, uint64_t gz_len, uint
     const uint64_t per = (csize + n - 1) / n;
     // symbols expected per part: ISIZE is exact below 4 GiB; 2x the compressed size bounds text otherwise
     const uint64_t d_est = std::max<uint64_t>(mi.isize, 2 * csize);
-    const uint64_t cap = round_up(2 * d_est / n + 65536, 8);
+    const uint64_t cap = std::min<uint64_t>(round_up(2 * d_est / n + 65536, 8), kMaxPartSymbols);
     F.chunk0 = (int32_t)P.chunks.size();
     F.nchunks = (int32_t)n;
     for (uint64_t i = 0; i < n; ++i) {
@@ -288,6 +290,7 @@ int layout(Plan& P) {
     if (!e) e = P.d_gfile.ensure(ng * sizeof(int32_t));
     if (!e) e = P.d_seg0.ensure(nf * sizeof(uint64_t));
     if (!e) e = P.d_sym.ensure(P.sym_total * sizeof(uint16_t));
+    if (!e) e = P.d_tok.ensure(nc * token_words_per_part() * sizeof(uint32_t));
     if (!e && P.chain) e = P.d_windows.ensure(nc * (size_t)kWin);
     if (!e && P.chain) e = P.d_gmaps.ensure(ng * (size_t)kWin * sizeof(uint16_t));
     if (!e && P.chain) e = P.d_wstart.ensure(ng * (size_t)kWin);
@@ -317,9 +320,11 @@ int enqueue(pgz_ctx* ctx, Plan& P, cudaStream_t s, bool timed) {
     uint16_t* sym = P.d_sym.as<uint16_t>();
     int k = 0;
     if (timed) cudaEventRecord(ctx->ev[0], s);
-    launch_sync(df, dc, (int)nc, sym, ctx->kp, s);
+    launch_sync(df, dc, (int)nc, sym, P.d_tok.as<uint32_t>(), ctx->kp, s);
+    if (cudaPeekAtLastError() != cudaSuccess) return PGZ_E_CUDA;
     if (timed) cudaEventRecord(ctx->ev[1], s);
-    launch_inflate(df, dc, (int)nc, sym, ctx->kp, s);
+    launch_inflate(df, dc, (int)nc, sym, P.d_tok.as<uint32_t>(), ctx->kp, s);
+    if (cudaPeekAtLastError() != cudaSuccess) return PGZ_E_CUDA;
     launch_plan(df, dc, (int)nf, s);
     k += 3;
     if (timed) cudaEventRecord(ctx->ev[2], s);
@@ -366,7 +371,8 @@ bool recover(Plan& P, int f, const ChunkDesc* res, uint64_t* false_syncs) {
         if (R.state != CS_ERROR) continue;
         ChunkDesc& C = P.chunks[c];
         if (R.err == CE_OVERFLOW) {
-            C.cap *= 2;
+            if (C.cap >= kMaxPartSymbols) return false;
+            C.cap = std::min<uint64_t>(C.cap * 2, kMaxPartSymbols);
             return true;
         }
         if (R.err == CE_TRAIL) return false;
@@ -374,7 +380,8 @@ bool recover(Plan& P, int f, const ChunkDesc* res, uint64_t* false_syncs) {
             for (int j = c + 1; j < F.chunk0 + F.nchunks; ++j) {
                 if (res[j].state == CS_EMPTY || P.chunks[j].disabled) continue;
                 if (res[j].state == CS_ERROR && res[j].err == CE_OVERFLOW) {
-                    P.chunks[j].cap *= 2;
+                    if (P.chunks[j].cap >= kMaxPartSymbols) return false;
+                    P.chunks[j].cap = std::min<uint64_t>(P.chunks[j].cap * 2, kMaxPartSymbols);
                     return true;
                 }
                 P.chunks[j].disabled = 1;
@@ -660,7 +667,7 @@ int pgz_decompress_at(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, uint64_t
     C.index = at_start ? 0 : 1;
     C.stop_hint = kNone;
     C.sync = kNone;
-    C.cap = round_up(std::max<uint64_t>(out_cap, 65536), 8);
+    C.cap = std::min<uint64_t>(round_up(std::max<uint64_t>(out_cap, 65536), 8), kMaxPartSymbols);
     P.chunks.push_back(C);
     P.chain = false;
     P.crc = false;

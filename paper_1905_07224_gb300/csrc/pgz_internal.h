@@ -97,10 +97,12 @@ struct ChunkDesc {
 };
 
 // host-side launch wrappers (pgz_kernels.cu)
-void launch_sync(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, const KParams& p,
-                 cudaStream_t s);
-void launch_inflate(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, const KParams& p,
-                    cudaStream_t s);
+// tok: per part, token_words_per_part() u32 of scratch for the parallel block decoder
+void launch_sync(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, uint32_t* tok,
+                 const KParams& p, cudaStream_t s);
+void launch_inflate(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, uint32_t* tok,
+                    const KParams& p, cudaStream_t s);
+uint64_t token_words_per_part();
 void launch_plan(FileDesc* files, ChunkDesc* chunks, int nfiles, cudaStream_t s);
 void launch_chain(const FileDesc* files, const ChunkDesc* chunks, int nfiles, int ngroups,
                   const int32_t* group_chunk0, const int32_t* group_n, const int32_t* group_file,

@@ -89,6 +89,9 @@ struct WarpSmem {
     uint32_t lmax, dmax, table_kind, pad;
     uint8_t lens[320];
     uint8_t cllens[32];
+    uint32_t masks[32 * 32];   // parallel decoding: token starts in the first 1024 bits of each lane's segment;
+                               // reused by exec_range: words 0-511 a position -> token map (1024 entries),
+                               // 512-767 the batch's tokens, 768-1023 their output offsets
 };
 
 __device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
@@ -430,27 +433,23 @@ struct OutState {
     bool neg;          // this lane copied from before the part start (a placeholder source)
 };
 
-// the symbol at part position q: q < 0 lies in the symbolic context
-__device__ __forceinline__ uint16_t sym_at(const uint16_t* out, int64_t q) {
-    return q >= 0 ? out[q] : (uint16_t)(kPH | (uint32_t)(kWin + q));
+// the symbol at part position q: q < 0 lies in the symbolic context.  Part
+// positions are 32-bit (a part holds fewer than 2^31 symbols).
+__device__ __forceinline__ uint16_t sym_at(const uint16_t* out, int32_t q) {
+    return q >= 0 ? out[(uint32_t)q] : (uint16_t)(kPH | (uint32_t)((int32_t)kWin + q));
 }
 
-// a copy whose source lies wholly before this batch: loads first, then stores
-__device__ __forceinline__ void copy_run(uint16_t* out, int64_t src, uint64_t dst, uint32_t len) {
-    for (uint32_t j0 = 0; j0 < len; j0 += 8) {
-        uint16_t v[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = (j0 + k < len) ? sym_at(out, src + j0 + k) : (uint16_t)0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-            if (j0 + k < len) out[dst + j0 + k] = v[k];
-    }
-}
-
-// token: literal = (1 << 16) | byte; match = bit 31 | length << 16 | (distance - 1)
+// Writes the symbols of a batch of tokens (lane t holds token t < ntok):
+// token = (1 << 16) | byte for a literal, bit 31 | length << 16 | (distance-1)
+// for a match.  Output-parallel: lane j produces output positions j, j + 32,
+// ... of the batch.  A position inside a match follows the copy to its source;
+// a source inside the batch is resolved in registers (the covering token is
+// found by binary search over the tokens' starts, an overlapping copy folds
+// back by the distance), so only sources before the batch are loaded from the
+// part's output (or are placeholders U_j before the part start).  All loads of
+// up to 256 positions are issued before their stores.
 __device__ __forceinline__ int exec_batch(OutState& o, uint32_t tok, int ntok, int lane, uint64_t& block_n) {
     const bool valid = lane < ntok;
-    const bool ism = valid && (tok >> 31);
     const uint32_t len = valid ? ((tok >> 16) & 0x1ffu) : 0u;
     uint32_t incl = len;
 #pragma unroll
@@ -459,39 +458,64 @@ __device__ __forceinline__ int exec_batch(OutState& o, uint32_t tok, int ntok, i
         if (lane >= d) incl += t;
     }
     const uint32_t total = __shfl_sync(FULL, incl, 31);
-    const uint64_t base = o.n;
-    if (base + total > o.cap) return CE_OVERFLOW;
-    const uint64_t start = base + incl - len;
+    const uint32_t base = (uint32_t)o.n;
+    if ((uint64_t)base + total > o.cap) return CE_OVERFLOW;
+    const uint32_t st = incl - len;          // start of my token, relative to the batch
     uint16_t* out = o.sym;
-    const uint32_t dist = (tok & 0xffffu) + 1u;
-    bool dep = false, bad = false;
-    if (valid && !ism) out[start] = (uint16_t)(tok & 0xffu);
-    if (ism) {
-        const int64_t src = (int64_t)start - (int64_t)dist;
-        if (src < 0) {
-            if (o.known) bad = true;
-            o.neg = true;
+    bool bad = false;
+    for (uint32_t r0 = 0; r0 < total; r0 += 256) {
+        uint32_t val[8];
+        int32_t src[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            uint32_t rel = r0 + 32u * r + (uint32_t)lane;
+            bool need = rel < total;
+            val[r] = 0;
+            src[r] = INT32_MIN;
+            while (__any_sync(FULL, need)) {
+                int t = 0;
+#pragma unroll
+                for (int sft = 16; sft; sft >>= 1) {
+                    const uint32_t x = __shfl_sync(FULL, st, (t + sft) & 31);
+                    if (t + sft < ntok && x <= rel) t += sft;
+                }
+                const uint32_t tk = __shfl_sync(FULL, tok, t), sk = __shfl_sync(FULL, st, t);
+                if (need) {
+                    if (!(tk >> 31)) {
+                        val[r] = tk & 0xffu;
+                        need = false;
+                    } else {
+                        const uint32_t dk = (tk & 0xffffu) + 1u;
+                        int32_t q = (int32_t)rel - (int32_t)dk;
+                        if (q >= (int32_t)sk) q = (int32_t)sk - (int32_t)dk + (int32_t)((rel - sk) % dk);
+                        if (q < 0) {
+                            src[r] = (int32_t)base + q;     // before the batch: final, or a placeholder
+                            need = false;
+                        } else {
+                            rel = (uint32_t)q;
+                        }
+                    }
+                }
+            }
         }
-        if (!bad) {
-            if (src + (int64_t)len <= (int64_t)base) copy_run(out, src, start, len);
-            else dep = true;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            if (src[r] != INT32_MIN) {
+                if (src[r] < 0) {
+                    if (o.known) bad = true;
+                    o.neg = true;
+                }
+                val[r] = sym_at(out, src[r]);
+            }
+        }
+        if (__any_sync(FULL, bad)) return CE_DIST;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const uint32_t rel = r0 + 32u * r + (uint32_t)lane;
+            if (rel < total) out[base + rel] = (uint16_t)val[r];
         }
     }
-    if (__any_sync(FULL, bad)) return CE_DIST;
     __syncwarp();
-    uint32_t dm = __ballot_sync(FULL, dep);
-    while (dm) {                                    // copies that read this batch, in order
-        const int k = __ffs(dm) - 1;
-        dm &= dm - 1;
-        const uint64_t ks = shfl64(start, k);
-        const uint32_t kl = __shfl_sync(FULL, len, k);
-        const uint32_t kd = __shfl_sync(FULL, dist, k);
-        for (uint32_t j = lane; j < kl; j += 32) {
-            const uint32_t jj = kd >= kl ? j : j % kd;
-            out[ks + j] = sym_at(out, (int64_t)ks - (int64_t)kd + jj);
-        }
-        __syncwarp();
-    }
     o.n = base + total;
     block_n += total;
     return CE_OK;
@@ -574,16 +598,17 @@ __device__ __forceinline__ int decode_batch(WarpSmem& S, BitIn& br, int lane, ui
     return CE_OK;
 }
 
-template <bool CHECK>
-__device__ int huff_block(WarpSmem& S, BitIn& br, OutState& o, uint64_t max_block, uint64_t end_bit,
-                          uint64_t& block_n, int lane) {
+constexpr int CE_MORE = 100;   // internal: the token limit was reached inside the block
+
+__device__ int huff_block(WarpSmem& S, BitIn& br, OutState& o, bool check, uint64_t max_block, uint64_t end_bit,
+                          uint64_t& block_n, int lane, uint32_t tok_limit = 0) {
+    uint32_t done = 0;
     for (;;) {
         uint32_t mytok = 0;
         int ntok = 0;
         bool eob = false;
-        // a batch reads at most 32 * 48 bits (48 words) plus one word ahead
-        const int st = (uint64_t)br.wi + 52 < br.nfull ? decode_batch<true, CHECK>(S, br, lane, mytok, ntok, eob)
-                                                       : decode_batch<false, CHECK>(S, br, lane, mytok, ntok, eob);
+        const int st = check ? decode_batch<false, true>(S, br, lane, mytok, ntok, eob)
+                             : decode_batch<false, false>(S, br, lane, mytok, ntok, eob);
         if (st) return st;
         if (ntok) {
             const int e = exec_batch(o, mytok, ntok, lane, block_n);
@@ -592,6 +617,391 @@ __device__ int huff_block(WarpSmem& S, BitIn& br, OutState& o, uint64_t max_bloc
         if (br.pos() > end_bit) return CE_TRUNC;
         if (max_block && block_n >= max_block) return CE_SIZE;
         if (eob) return CE_OK;
+        done += (uint32_t)ntok;
+        if (tok_limit && done >= tok_limit) return CE_MORE;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// parallel decoding of one Huffman block by the 32 lanes of a warp.
+// Round: lane k decodes its own kSeg-bit segment from bit start + k*kSeg with
+// the block's codes (a guess: it may begin inside a code), storing its tokens
+// and marking its token starts among the first kSyncW bits.  Lane k then
+// continues into segment k+1 until its parse meets a token start of lane
+// k+1's parse: from there the two parses are identical (Huffman codes
+// resynchronise), so lane k+1's tokens from that bit on are the block's.
+// Lane 0 starts at a known token start, so the chain of meeting points gives
+// the true token sequence; the warp then writes those tokens in order.  A
+// lane that does not meet its successor within kSyncW bits ends the round
+// there; the next round starts at that known position.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kSeg = 2048;      // bits per lane per round
+constexpr uint32_t kSyncW = 1024;    // bits at the head of a segment where meeting points are looked for
+constexpr uint32_t kTokCap = 512;    // tokens a lane may keep per round (own segment + continuation)
+constexpr uint64_t kTokPerPart = 32ull * kTokCap;   // token buffer of one part (one warp)
+
+enum : int { LT_ONE = 0, LT_TWO = 1, LT_EOB = 2, LT_ERR = 3 };
+
+// one token by one lane: t0 (and t1 for two literals, the first l1 bits long)
+template <bool SAFE>
+__device__ __forceinline__ int lane_token(const WarpSmem& S, BitIn& b, uint32_t& t0, uint32_t& t1, uint32_t& l1) {
+    b.refill<SAFE>();
+    uint32_t e = S.lit[b.lo & ((1u << LB) - 1u)];
+    uint32_t k = e >> 28;
+    if (k == K_LIT2) {
+        t0 = 0x10000u | ((e >> 8) & 0xffu);
+        t1 = 0x10000u | ((e >> 16) & 0xffu);
+        l1 = (e >> 24) & 15u;
+        b.drop(e & 31u);
+        return LT_TWO;
+    }
+    if (k >= K_LONG) {
+        uint32_t L = 0;
+        const int s = k == K_LONG ? decode_long(b.peek(15), LB, S.lfirst, S.lcount, S.loff, S.lsym, (int)S.lmax, L) : -1;
+        if (s < 0) return LT_ERR;
+        e = lit_entry((uint32_t)s, L, 0);
+        k = e >> 28;
+        if (k == K_BAD) return LT_ERR;
+    }
+    if (k == K_LIT) {
+        t0 = 0x10000u | ((e >> 8) & 0xffu);
+        b.drop(e & 31u);
+        return LT_ONE;
+    }
+    if (k == K_EOB) {
+        b.drop(e & 31u);
+        return LT_EOB;
+    }
+    uint32_t len = (e >> 8) & 0x1ffu, dn = e & 31u;
+    if (k == K_LENX) {
+        const uint32_t eb = (e >> 17) & 7u;
+        len += (b.lo >> dn) & ((1u << eb) - 1u);
+        dn += eb;
+    }
+    b.drop(dn);
+    b.refill<SAFE>();
+    uint32_t d = S.dist[b.lo & ((1u << DB) - 1u)];
+    if (d & 0x300u) {
+        if ((d & 0x300u) != (DK_LONG << 8)) return LT_ERR;
+        uint32_t L = 0;
+        const int s = decode_long(b.peek(15), DB, S.dfirst, S.dcount, S.doff, S.dsym, (int)S.dmax, L);
+        if (s < 0) return LT_ERR;
+        d = dist_entry((uint32_t)s, L);
+        if (d & 0x300u) return LT_ERR;
+    }
+    const uint32_t dl = d & 15u, de = (d >> 4) & 15u;
+    const uint32_t dist = (d >> 16) + ((b.lo >> dl) & ((1u << de) - 1u));
+    b.drop(dl + de);
+    t0 = 0x80000000u | (len << 16) | (dist - 1u);
+    return LT_ONE;
+}
+
+enum : uint32_t { PS_OK = 0, PS_EOB = 1, PS_ERR = 2, PS_CAP = 3, PS_SYNC = 4, PS_NOSYNC = 5 };
+
+__device__ __forceinline__ void mark(uint32_t& mw, uint32_t& mwi, uint32_t* m, uint32_t rel) {
+    const uint32_t wi = rel >> 5;
+    if (wi != mwi) {
+        m[mwi] = mw;
+        mw = 0;
+        mwi = wi;
+    }
+    mw |= 1u << (rel & 31);
+}
+
+// own segment: tokens from `my0` while the token start lies before my0 + kSeg.
+// The loop runs in lock step over the warp (one token per lane per step).
+__device__ uint32_t seg_own(const WarpSmem& S, BitIn& b, uint64_t my0, uint32_t* m, uint32_t* tb, uint32_t& n,
+                            uint64_t& stop, uint32_t& ev) {
+    uint32_t mw = 0, mwi = 0;
+    uint32_t st = PS_OK;
+    const uint32_t p0 = (uint32_t)my0;
+    bool go = true;
+    while (__any_sync(FULL, go)) {
+        if (!go) continue;
+        const uint32_t rel = (uint32_t)(b.wi * 32u - b.cnt) - p0;
+        if (rel >= kSeg) {
+            go = false;
+            continue;
+        }
+        if (rel < kSyncW) mark(mw, mwi, m, rel);
+        if (n + 2 > kTokCap) {
+            st = PS_CAP;
+            go = false;
+            continue;
+        }
+        uint32_t t0, t1, l1;
+        const int r = lane_token<false>(S, b, t0, t1, l1);
+        if (r <= LT_TWO) {
+            tb[n++] = t0;
+            if (r == LT_TWO) {
+                if (rel + l1 < kSyncW) mark(mw, mwi, m, rel + l1);
+                tb[n++] = t1;
+            }
+        } else {
+            st = r == LT_EOB ? PS_EOB : PS_ERR;
+            ev = n;
+            go = false;
+        }
+    }
+    m[mwi] = mw;
+    stop = b.pos();
+    return st;
+}
+
+// continuation into the next segment until the parse meets one of its token
+// starts (lock step; lanes with nothing to do idle)
+__device__ uint32_t seg_next(const WarpSmem& S, BitIn& b, bool active, uint64_t nx0, const uint32_t* nm, uint32_t* tb,
+                             uint32_t n, uint32_t& n2, uint64_t& q, uint32_t& ev) {
+    const uint32_t p0 = (uint32_t)nx0;
+    uint32_t st = PS_NOSYNC;
+    bool go = active;
+    while (__any_sync(FULL, go)) {
+        if (!go) continue;
+        const uint32_t rel = (uint32_t)(b.wi * 32u - b.cnt) - p0;
+        if (rel >= kSyncW || n + n2 + 2 > kTokCap) {
+            st = PS_NOSYNC;
+            go = false;
+            continue;
+        }
+        if ((nm[rel >> 5] >> (rel & 31)) & 1u) {
+            st = PS_SYNC;
+            go = false;
+            continue;
+        }
+        uint32_t t0, t1, l1;
+        const int r = lane_token<false>(S, b, t0, t1, l1);
+        if (r <= LT_TWO) {
+            tb[n + n2++] = t0;
+            if (r == LT_TWO) tb[n + n2++] = t1;
+        } else {
+            ev = n2;
+            st = r == LT_EOB ? PS_EOB : PS_ERR;
+            go = false;
+        }
+    }
+    q = b.pos();
+    return st;
+}
+
+// Writes up to 256 consecutive tokens of the block (lane j loads tokens
+// 8j..8j+7).  Output positions are spread over the lanes; a position inside a
+// match follows the copy to its source, resolved through the batch's tokens
+// in shared memory (a position -> token map for the first 1024 positions,
+// binary search beyond) until it reaches a literal or a position before the
+// batch (already final in the part's output, or a placeholder before the part
+// start).  Loads of four positions per lane are in flight together.
+__device__ __forceinline__ int exec_range(WarpSmem& S, OutState& o, const uint32_t* tks, uint32_t ntok, bool check,
+                                          uint64_t& block_n, int lane) {
+    uint32_t t[8], L[8], sum = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const uint32_t idx = 8u * lane + i;
+        t[i] = idx < ntok ? tks[idx] : 0u;
+        L[i] = idx < ntok ? ((t[i] >> 16) & 0x1ffu) : 0u;
+        sum += L[i];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t x = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += x;
+    }
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    const uint32_t base = (uint32_t)o.n;
+    if ((uint64_t)base + total > o.cap) return CE_OVERFLOW;
+    if (check) {
+        bool bad = false;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (L[i] && !(t[i] >> 31) && !allowed_has(S.allowed, t[i] & 0xffu)) bad = true;
+        if (__any_sync(FULL, bad)) return CE_BYTE;
+    }
+    uint16_t* map = reinterpret_cast<uint16_t*>(S.masks);
+    uint32_t* tokS = S.masks + 512;
+    uint32_t* stS = S.masks + 768;
+    uint32_t s0 = incl - sum;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const uint32_t idx = 8u * lane + i;
+        if (idx < ntok) {
+            tokS[idx] = t[i];
+            stS[idx] = s0;
+            const uint32_t e = s0 + L[i] < 1024u ? s0 + L[i] : 1024u;
+            for (uint32_t x = s0; x < e; ++x) map[x] = (uint16_t)idx;
+        }
+        s0 += L[i];
+    }
+    __syncwarp();
+    uint16_t* out = o.sym;
+    bool bad = false;
+    constexpr int U = 8;                                   // positions per lane in flight
+    for (uint32_t r0 = 0; r0 < total; r0 += 32u * U) {
+        uint32_t rel[U], val[U];
+        int32_t src[U];
+        uint32_t need = 0;                                 // bit u: position u not resolved yet
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            rel[u] = r0 + 32u * u + (uint32_t)lane;
+            src[u] = INT32_MIN;
+            val[u] = 0;
+            if (rel[u] < total) need |= 1u << u;
+        }
+        // one hop per pass for every unresolved position: a literal ends the chain,
+        // a source before the batch ends it with a load, else continue at the
+        // source (strictly earlier in the batch, so every chain ends)
+        while (need) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (!((need >> u) & 1u)) continue;
+                uint32_t ti;
+                if (rel[u] < 1024u) {
+                    ti = map[rel[u]];
+                } else {                                   // binary search over the starts
+                    uint32_t lo = 0, hi = ntok - 1;
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi + 1) >> 1;
+                        if (stS[mid] <= rel[u]) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    ti = lo;
+                }
+                const uint32_t tk = tokS[ti];
+                if (!(tk >> 31)) {
+                    val[u] = tk & 0xffu;
+                    need &= ~(1u << u);
+                    continue;
+                }
+                const uint32_t sk = stS[ti], dk = (tk & 0xffffu) + 1u;
+                int32_t q = (int32_t)rel[u] - (int32_t)dk;
+                if (q >= (int32_t)sk) q = (int32_t)sk - (int32_t)dk + (int32_t)((rel[u] - sk) % dk);
+                if (q < 0) {
+                    src[u] = (int32_t)base + q;
+                    need &= ~(1u << u);
+                } else {
+                    rel[u] = (uint32_t)q;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (src[u] != INT32_MIN) {
+                if (src[u] < 0) {
+                    if (o.known) bad = true;
+                    o.neg = true;
+                }
+                val[u] = sym_at(out, src[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t p = r0 + 32u * u + (uint32_t)lane;
+            if (p < total) out[base + p] = (uint16_t)val[u];
+        }
+    }
+    if (__any_sync(FULL, bad)) return CE_DIST;
+    __syncwarp();
+    o.n = base + total;
+    block_n += total;
+    return CE_OK;
+}
+
+__device__ int par_block(WarpSmem& S, uint32_t* tokbuf, BitIn& br, OutState& o, bool check, uint64_t max_block,
+                         uint64_t end_bit, uint64_t& block_n, int lane) {
+    uint32_t* tb = tokbuf + (uint64_t)lane * kTokCap;
+    uint32_t* mymask = S.masks + 32 * lane;
+    for (;;) {
+        const uint64_t start = br.pos();
+        const uint64_t my0 = start + (uint64_t)lane * kSeg;
+#pragma unroll
+        for (int w = 0; w < 32; ++w) mymask[w] = 0;
+        {   // bring the lane's segment (and the continuation window) into L1
+            const uint64_t b0 = my0 >> 3, b1 = (my0 + kSeg + kSyncW + 128) >> 3;
+            for (uint64_t a = b0 & ~127ull; a < b1; a += 128)
+                if (a < br.nbytes) asm volatile("prefetch.global.L1 [%0];" ::"l"(br.b + a));
+        }
+        BitIn b = br;
+        b.seek(my0);
+        uint32_t n = 0, ev1 = 0, ev2 = 0, n2 = 0;
+        uint64_t stop = 0, q = 0;
+        const uint32_t st1 = seg_own(S, b, my0, mymask, tb, n, stop, ev1);
+        __syncwarp();
+        const uint32_t st2 = seg_next(S, b, st1 == PS_OK && lane < 31, my0 + kSeg, S.masks + 32 * ((lane + 1) & 31), tb,
+                                      n, n2, q, ev2);
+        __syncwarp();
+        // the chain of meeting points, lane by lane (uniform)
+        uint32_t skip = 0, my_vs = 0, my_ve = 0;
+        int last = -1;
+        bool block_end = false;
+        int err = CE_OK;
+        uint64_t round_end = 0;
+        for (int k = 0; k < 32; ++k) {
+            const uint32_t s1 = __shfl_sync(FULL, st1, k), nk = __shfl_sync(FULL, n, k);
+            uint32_t ve;
+            bool stop_here = true;
+            if (s1 == PS_EOB) {
+                ve = __shfl_sync(FULL, ev1, k);
+                block_end = true;
+                round_end = shfl64(stop, k);
+            } else if (s1 == PS_ERR) {
+                err = CE_DATA;
+                ve = skip;
+            } else if (s1 == PS_CAP || k == 31) {
+                ve = nk;
+                round_end = shfl64(stop, k);
+            } else {
+                const uint32_t s2 = __shfl_sync(FULL, st2, k), n2k = __shfl_sync(FULL, n2, k);
+                const uint64_t qk = shfl64(q, k);
+                if (s2 == PS_EOB) {
+                    ve = nk + __shfl_sync(FULL, ev2, k);
+                    block_end = true;
+                    round_end = qk;
+                } else if (s2 == PS_ERR) {
+                    err = CE_DATA;
+                    ve = skip;
+                } else if (s2 == PS_NOSYNC) {
+                    ve = nk + n2k;
+                    round_end = qk;
+                } else {                                   // met lane k+1 at qk
+                    ve = nk + n2k;
+                    stop_here = false;
+                }
+                if (!stop_here) {
+                    // lane k+1's tokens that start before qk are not the block's
+                    const uint32_t rel = (uint32_t)(qk - (start + (uint64_t)(k + 1) * kSeg));
+                    const uint32_t w = S.masks[32 * (k + 1) + lane];
+                    const uint32_t below = (uint32_t)lane < (rel >> 5) ? __popc(w)
+                                         : ((uint32_t)lane == (rel >> 5) ? __popc(w & ((1u << (rel & 31)) - 1u)) : 0u);
+                    const uint32_t nskip = __reduce_add_sync(FULL, below);
+                    if (lane == k) {
+                        my_vs = skip;
+                        my_ve = ve;
+                    }
+                    skip = nskip;
+                    continue;
+                }
+            }
+            if (lane == k) {
+                my_vs = skip;
+                my_ve = ve;
+            }
+            last = k;
+            break;
+        }
+        if (err) return err;
+        // the block's tokens of this round, in order: lane ranges one after another
+        for (int k = 0; k <= last; ++k) {
+            const uint32_t vs = __shfl_sync(FULL, my_vs, k), ve = __shfl_sync(FULL, my_ve, k);
+            const uint32_t* rng = tokbuf + (uint64_t)k * kTokCap;
+            for (uint32_t x = vs; x < ve; x += 256) {
+                const int e = exec_range(S, o, rng + x, ve - x < 256 ? ve - x : 256, check, block_n, lane);
+                if (e) return e;
+                if (max_block && block_n >= max_block) return CE_SIZE;
+            }
+        }
+        __syncwarp();
+        if (round_end > end_bit) return CE_TRUNC;
+        br.seek(round_end);
+        if (block_end) return CE_OK;
     }
 }
 
@@ -622,9 +1032,11 @@ __device__ int stored_block(BitIn& br, OutState& o, bool check, const uint32_t* 
 
 // one block.  candidate: the block must be a non-final dynamic block (the
 // block-start checks); min/max_block bound its size; check: its literals must
-// be allowed bytes.
-__device__ int one_block(WarpSmem& S, BitIn& br, OutState& o, bool check, uint64_t min_block, uint64_t max_block,
-                         bool candidate, uint64_t end_bit, uint32_t& final, int lane) {
+// be allowed bytes.  Huffman blocks are decoded by the whole warp in parallel
+// (par_block); a candidate block start first runs a short serial prefix, so
+// that false candidates fail after a few tokens.
+__device__ int one_block(WarpSmem& S, uint32_t* tokbuf, BitIn& br, OutState& o, bool check, uint64_t min_block,
+                         uint64_t max_block, bool candidate, uint64_t end_bit, uint32_t& final, int lane) {
     br.refill();
     final = br.peek(1);
     const uint32_t type = br.peek(3) >> 1;
@@ -648,9 +1060,14 @@ __device__ int one_block(WarpSmem& S, BitIn& br, OutState& o, bool check, uint64
             st = read_dynamic<false>(S, br, lane);
             if (st == CE_OK && br.pos() > end_bit) st = CE_TRUNC;
         }
-        if (st == CE_OK)
-            st = check ? huff_block<true>(S, br, o, max_block, end_bit, block_n, lane)
-                       : huff_block<false>(S, br, o, max_block, end_bit, block_n, lane);
+        if (st == CE_OK && candidate) {
+            st = huff_block(S, br, o, check, max_block, end_bit, block_n, lane, 64);
+            st = st == CE_MORE ? CE_MORE : (st == CE_OK ? CE_OK + 1000 : st);
+        }
+        if (st == CE_OK || st == CE_MORE)
+            st = par_block(S, tokbuf, br, o, check, max_block, end_bit, block_n, lane);
+        else if (st == CE_OK + 1000)
+            st = CE_OK;
     }
     if (st == CE_OK && max_block && block_n >= max_block) st = CE_SIZE;
     if (st == CE_OK && block_n < min_block) st = CE_SIZE;
@@ -745,8 +1162,9 @@ constexpr int kWarpsPerBlock = 4;
 // ---------------------------------------------------------------------------
 // k_sync: block start of each part and its first block
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, 8)
-    k_sync(const FileDesc* __restrict__ files, ChunkDesc* chunks, int nchunks, uint16_t* symbuf, KParams p) {
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, 5)
+    k_sync(const FileDesc* __restrict__ files, ChunkDesc* chunks, int nchunks, uint16_t* symbuf, uint32_t* tokbuf,
+           KParams p) {
     __shared__ uint16_t kraft3[512];
     for (uint32_t v = threadIdx.x; v < 512; v += blockDim.x)
         kraft3[v] = (uint16_t)(kraft1(v & 7) + kraft1((v >> 3) & 7) + kraft1(v >> 6));
@@ -758,6 +1176,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 8)
     ChunkDesc& C = chunks[c];
     const FileDesc& F = files[C.file];
     init_smem(S, p, lane);
+    uint32_t* tok = tokbuf + (uint64_t)c * kTokPerPart;
     OutState o{symbuf + C.sym_base, C.cap, 0, C.index == 0 && C.lo <= F.s0_bit, false};
     BitIn br;
     br.setup(F.gz, F.gz_len);
@@ -767,7 +1186,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 8)
         state = CS_EMPTY;
     } else if (o.known || C.given) {          // the member start (empty context) or a known block start
         br.seek(C.lo);
-        const int st = one_block(S, br, o, false, 0, 0, false, F.end_bit, final, lane);
+        const int st = one_block(S, tok, br, o, false, 0, 0, false, F.end_bit, final, lane);
         sync = C.lo;
         resume = br.pos();
         if (st) {
@@ -784,7 +1203,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 8)
             br.seek(cand);
             o.n = 0;
             o.neg = false;
-            const int st = one_block(S, br, o, true, p.min_block, p.max_block, true, F.end_bit, final, lane);
+            const int st = one_block(S, tok, br, o, true, p.min_block, p.max_block, true, F.end_bit, final, lane);
             if (st == CE_OK) {
                 state = CS_FOUND;
                 sync = cand;
@@ -819,8 +1238,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 8)
 // ---------------------------------------------------------------------------
 // k_inflate: pass 1 of each part up to the next part's block start
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, 8)
-    k_inflate(const FileDesc* __restrict__ files, ChunkDesc* chunks, int nchunks, uint16_t* symbuf, KParams p) {
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, 5)
+    k_inflate(const FileDesc* __restrict__ files, ChunkDesc* chunks, int nchunks, uint16_t* symbuf, uint32_t* tokbuf,
+              KParams p) {
     WarpSmem& S = warp_smem();
     const int lane = threadIdx.x & 31;
     const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -856,7 +1276,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 8)
             }
             const bool check = !o.known && blocks <= (uint32_t)p.confirm_blocks;
             uint32_t fin = 0;
-            const int st = one_block(S, br, o, check, 0, 0, false, F.end_bit, fin, lane);
+            const int st = one_block(S, tokbuf + (uint64_t)c * kTokPerPart, br, o, check, 0, 0, false, F.end_bit, fin,
+                                     lane);
             if (st) {
                 err = (check && st != CE_OVERFLOW) ? (uint32_t)CE_CONFIRM : (uint32_t)st;
                 break;
@@ -1166,7 +1587,7 @@ __device__ uint32_t xpow8(uint64_t n) {       // x^(8n) mod P
     return r;
 }
 
-constexpr uint32_t kSeg = 4096;    // bytes per warp
+constexpr uint32_t kCrcSeg = 4096;    // bytes per warp
 constexpr uint32_t kPiece = 128;   // bytes per lane
 
 __global__ void __launch_bounds__(256) k_crc(FileDesc* files, int nfiles, uint64_t total_seg, const uint64_t* seg0) {
@@ -1187,9 +1608,9 @@ __global__ void __launch_bounds__(256) k_crc(FileDesc* files, int nfiles, uint64
         FileDesc& F = files[lo];
         if (F.status != PGZ_OK || F.mode != 0) continue;
         const uint64_t D = F.total;
-        const uint64_t a = (sg - seg0[lo]) * kSeg;
+        const uint64_t a = (sg - seg0[lo]) * kCrcSeg;
         if (a >= D) continue;
-        const uint64_t se = a + kSeg < D ? a + kSeg : D;
+        const uint64_t se = a + kCrcSeg < D ? a + kCrcSeg : D;
         const uint64_t pa = a + (uint64_t)kPiece * lane;
         const uint64_t pb = pa + kPiece < se ? pa + kPiece : se;
         uint32_t r = 0;
@@ -1215,7 +1636,7 @@ __global__ void __launch_bounds__(256) k_crc(FileDesc* files, int nfiles, uint64
                 for (uint64_t x = pa; x < pb; ++x) r = T[(r ^ out[x]) & 0xffu] ^ (r >> 8);
             }
             // shift to the end of the segment
-            if (se - a == kSeg) r = gf2_mul(r, LS[31 - lane]);
+            if (se - a == kCrcSeg) r = gf2_mul(r, LS[31 - lane]);
             else r = gf2_mul(r, xpow8(se - pb));
         }
         for (int d = 16; d; d >>= 1) r ^= __shfl_xor_sync(FULL, r, d);
@@ -1240,20 +1661,24 @@ __global__ void k_finalize(FileDesc* files, int nfiles) {
 // host wrappers
 // ---------------------------------------------------------------------------
 static size_t warp_smem_bytes() { return sizeof(WarpSmem); }
+static_assert(kWarpsPerBlock * sizeof(WarpSmem) <= 48 * 1024, "per-block shared memory above the default limit");
 
-void launch_sync(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, const KParams& p,
-                 cudaStream_t s) {
+void launch_sync(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, uint32_t* tok,
+                 const KParams& p, cudaStream_t s) {
     if (nchunks <= 0) return;
     const int wpb = kWarpsPerBlock;
-    k_sync<<<(nchunks + wpb - 1) / wpb, 32 * wpb, wpb * warp_smem_bytes(), s>>>(files, chunks, nchunks, sym, p);
+    k_sync<<<(nchunks + wpb - 1) / wpb, 32 * wpb, wpb * warp_smem_bytes(), s>>>(files, chunks, nchunks, sym, tok, p);
 }
 
-void launch_inflate(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, const KParams& p,
-                    cudaStream_t s) {
+void launch_inflate(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, uint32_t* tok,
+                    const KParams& p, cudaStream_t s) {
     if (nchunks <= 0) return;
     const int wpb = kWarpsPerBlock;
-    k_inflate<<<(nchunks + wpb - 1) / wpb, 32 * wpb, wpb * warp_smem_bytes(), s>>>(files, chunks, nchunks, sym, p);
+    k_inflate<<<(nchunks + wpb - 1) / wpb, 32 * wpb, wpb * warp_smem_bytes(), s>>>(files, chunks, nchunks, sym, tok,
+                                                                                   p);
 }
+
+uint64_t token_words_per_part() { return kTokPerPart; }
 
 void launch_plan(FileDesc* files, ChunkDesc* chunks, int nfiles, cudaStream_t s) {
     if (nfiles <= 0) return;
