@@ -29,7 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 L2_BYTES = 126 * (1 << 20)
-CHUNK_BYTES = 32 << 10        # compressed bytes per part (about one DEFLATE block of zlib output)
+CHUNK_BYTES = 64 << 10        # compressed bytes per part (about two DEFLATE blocks of zlib output)
 
 
 def _peaks():

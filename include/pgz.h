@@ -62,7 +62,7 @@ typedef struct pgz_ctx pgz_ctx;
 typedef struct pgz_config {
     int device;                 /* CUDA device ordinal */
     void* cuda_stream;          /* cudaStream_t to issue work on; NULL = default stream */
-    uint64_t chunk_bytes;       /* compressed bytes per part; 0 = default (see pgz_config_init) */
+    uint64_t chunk_bytes;       /* compressed bytes per part (used when n_chunks is 0) */
     int n_chunks;               /* > 0: exactly this many parts per file (overrides chunk_bytes) */
     int threads_per_chunk;      /* threads decoding one part: 32 (one warp) is the only value */
     uint8_t allowed[32];        /* literal bytes accepted at a block start, bit b of byte b/8 */
@@ -98,9 +98,10 @@ typedef struct pgz_job {
 typedef struct pgz_index pgz_index;
 typedef struct pgz_batch pgz_batch;
 
-/* Defaults: device 0, default stream, 1024 parts of the member's compressed
-   data (the part count of the paper's setting is a free parameter, Section
-   "Full file decompression in two passes"), ASCII bytes 9, 10, 13, 32..126
+/* Defaults: device 0, default stream, parts of 64 KiB of compressed data
+   (about two DEFLATE blocks of zlib output; the part count of the paper's
+   setting is a free parameter, Section "Full file decompression in two
+   passes"), ASCII bytes 9, 10, 13, 32..126
    (reading of the Appendix's "valid ASCII characters"), confirm_blocks 5
    (Section "Detection of DEFLATE block start positions"), block bounds
    1 KiB .. 4 MiB (Appendix "DEFLATE block decompression checks"). */

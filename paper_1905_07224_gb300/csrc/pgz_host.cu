@@ -532,8 +532,8 @@ void pgz_config_init(pgz_config* cfg) {
     memset(cfg, 0, sizeof *cfg);
     cfg->device = 0;
     cfg->cuda_stream = nullptr;
-    cfg->chunk_bytes = 0;
-    cfg->n_chunks = 1024;
+    cfg->chunk_bytes = 64 << 10;
+    cfg->n_chunks = 0;
     cfg->threads_per_chunk = 32;
     for (int b = 0; b < 256; ++b)
         if (b == 9 || b == 10 || b == 13 || (b >= 32 && b <= 126)) cfg->allowed[b >> 3] |= (uint8_t)(1u << (b & 7));

@@ -67,6 +67,7 @@ __constant__ uint8_t c_clorder[19] = {16, 17, 18, 0, 8, 7, 9, 6, 10, 5, 11, 4, 1
 __constant__ uint32_t c_crc_tab[256];   // register after one byte b from a zero register
 __constant__ uint32_t c_x2k[64];        // x^(2^k) mod P
 __constant__ uint32_t c_lane_shift[32]; // x^(8*128*k) mod P
+__constant__ uint32_t c_x4096;          // x^(8*4096) mod P
 
 // literal/length lookup entry: bits 0-4 bits to drop, 8-16 value, 17-19
 // extra-bit count (K_LENX), 28-31 kind.  K_LEN carries the exact length
@@ -1377,6 +1378,7 @@ __device__ __forceinline__ uint16_t map_entry(const uint16_t* d, uint64_t n, uin
     return t >= 0 ? d[t] : (uint16_t)(kPH | (uint32_t)(k + n));
 }
 
+// Every thread handles entries tid + 1024*j; eight loads are in flight at once.
 __global__ void __launch_bounds__(1024) k_chain_compose(const FileDesc* __restrict__ files,
                                                         const ChunkDesc* __restrict__ chunks, const int32_t* g0,
                                                         const int32_t* gn, const int32_t* gfile,
@@ -1386,15 +1388,23 @@ __global__ void __launch_bounds__(1024) k_chain_compose(const FileDesc* __restri
     uint16_t* tmp = acc + kWin;
     const int g = blockIdx.x;
     if (files[gfile[g]].status != PGZ_OK) return;
+    const uint32_t tid = threadIdx.x;
     bool have = false;
     for (int c = g0[g]; c < g0[g] + gn[g]; ++c) {
         const ChunkDesc& C = chunks[c];
         if (C.state != CS_DONE || C.n == 0) continue;
         const uint16_t* d = sym + C.sym_base;
-        for (uint32_t k = threadIdx.x; k < kWin; k += blockDim.x) {
-            uint16_t m = map_entry(d, C.n, k);
-            if (have && (m & kPH)) m = acc[m & (kWin - 1)];
-            tmp[k] = m;
+        const uint64_t n = C.n;
+        for (uint32_t j0 = 0; j0 < kWin / 1024; j0 += 8) {
+            uint16_t m[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) m[u] = map_entry(d, n, tid + 1024u * (j0 + u));
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                uint16_t e = m[u];
+                if (have && (e & kPH)) e = acc[e & (kWin - 1)];
+                tmp[tid + 1024u * (j0 + u)] = e;
+            }
         }
         __syncthreads();
         uint16_t* x = acc;
@@ -1403,7 +1413,7 @@ __global__ void __launch_bounds__(1024) k_chain_compose(const FileDesc* __restri
         have = true;
     }
     uint16_t* dst = gmaps + (uint64_t)g * kWin;
-    for (uint32_t k = threadIdx.x; k < kWin; k += blockDim.x) dst[k] = have ? acc[k] : (uint16_t)(kPH | k);
+    for (uint32_t k = tid; k < kWin; k += 1024) dst[k] = have ? acc[k] : (uint16_t)(kPH | k);
 }
 
 __global__ void __launch_bounds__(1024) k_chain_walk(const FileDesc* __restrict__ files, const uint16_t* __restrict__ gmaps,
@@ -1413,15 +1423,22 @@ __global__ void __launch_bounds__(1024) k_chain_walk(const FileDesc* __restrict_
     uint8_t* W2 = smem_raw + kWin;
     const FileDesc& F = files[blockIdx.x];
     if (F.status != PGZ_OK) return;
-    for (uint32_t k = threadIdx.x; k < kWin; k += blockDim.x) W[k] = 0;   // before the member: never referenced
+    const uint32_t tid = threadIdx.x;
+    for (uint32_t k = tid; k < kWin; k += 1024) W[k] = 0;   // before the member: never referenced
     __syncthreads();
     for (int g = F.group0; g < F.group0 + F.ngroups; ++g) {
         uint8_t* ws = wstart + (uint64_t)g * kWin;
         const uint16_t* m = gmaps + (uint64_t)g * kWin;
-        for (uint32_t k = threadIdx.x; k < kWin; k += blockDim.x) {
-            ws[k] = W[k];
-            const uint16_t e = m[k];
-            W2[k] = (e & kPH) ? W[e & (kWin - 1)] : (uint8_t)e;
+        for (uint32_t j0 = 0; j0 < kWin / 1024; j0 += 8) {
+            uint16_t e[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) e[u] = m[tid + 1024u * (j0 + u)];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t k = tid + 1024u * (j0 + u);
+                ws[k] = W[k];
+                W2[k] = (e[u] & kPH) ? W[e[u] & (kWin - 1)] : (uint8_t)e[u];
+            }
         }
         __syncthreads();
         uint8_t* x = W;
@@ -1440,27 +1457,32 @@ __global__ void __launch_bounds__(1024) k_chain_expand(const FileDesc* __restric
     uint8_t* W2 = smem_raw + kWin;
     const int g = blockIdx.x;
     if (files[gfile[g]].status != PGZ_OK) return;
+    const uint32_t tid = threadIdx.x;
     const uint8_t* ws = wstart + (uint64_t)g * kWin;
-    for (uint32_t k = threadIdx.x; k < kWin; k += blockDim.x) W[k] = ws[k];
+    for (uint32_t k = tid; k < kWin / 16; k += 1024)
+        reinterpret_cast<uint4*>(W)[k] = reinterpret_cast<const uint4*>(ws)[k];
     __syncthreads();
     for (int c = g0[g]; c < g0[g] + gn[g]; ++c) {
         const ChunkDesc& C = chunks[c];
-        uint8_t* wc = windows + (uint64_t)c * kWin;
-        const bool apply = C.state == CS_DONE && C.n > 0;
+        uint4* wc = reinterpret_cast<uint4*>(windows + (uint64_t)c * kWin);
+        for (uint32_t k = tid; k < kWin / 16; k += 1024) wc[k] = reinterpret_cast<const uint4*>(W)[k];
+        if (C.state != CS_DONE || C.n == 0) continue;
         const uint16_t* d = sym + C.sym_base;
-        for (uint32_t k = threadIdx.x; k < kWin; k += blockDim.x) {
-            wc[k] = W[k];
-            if (apply) {
-                const uint16_t e = map_entry(d, C.n, k);
-                W2[k] = (e & kPH) ? W[e & (kWin - 1)] : (uint8_t)e;
+        const uint64_t n = C.n;
+        for (uint32_t j0 = 0; j0 < kWin / 1024; j0 += 8) {
+            uint16_t m[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) m[u] = map_entry(d, n, tid + 1024u * (j0 + u));
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint16_t e = m[u];
+                W2[tid + 1024u * (j0 + u)] = (e & kPH) ? W[e & (kWin - 1)] : (uint8_t)e;
             }
         }
         __syncthreads();
-        if (apply) {
-            uint8_t* x = W;
-            W = W2;
-            W2 = x;
-        }
+        uint8_t* x = W;
+        W = W2;
+        W2 = x;
     }
 }
 
@@ -1501,52 +1523,62 @@ __global__ void __launch_bounds__(1024) k_translate(const FileDesc* __restrict__
     const uint32_t m = (uint32_t)(C.out_off & 7);
     uint32_t nph = 0;
     uint64_t last = 0;
-    for (uint64_t wb = t0 + 256ull * warp; wb < t1; wb += 256ull * nwarp) {
-        const uint64_t i = wb + 8ull * lane;
-        uint32_t nv = 0;
-        uint64_t val = 0;
-        if (i < t1) {
-            nv = t1 - i >= 8 ? 8u : (uint32_t)(t1 - i);
-            const uint4 q = *reinterpret_cast<const uint4*>(s + i);   // symbols past n lie within the capacity
-            const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+    constexpr int U = 4;                                 // 16-byte loads in flight per thread
+    const uint64_t stride = 256ull * nwarp;
+    for (uint64_t wb = t0 + 256ull * warp; wb < t1; wb += stride * U) {
+        uint4 qv[U];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const uint32_t v = (w4[k >> 1] >> (16 * (k & 1))) & 0xffffu;
-                if ((uint32_t)k < nv) {
-                    uint32_t b = v & 0xffu;
-                    if (v & kPH) {
-                        b = W[v & (kWin - 1)];
-                        ++nph;
-                        last = i + k + 1;
+        for (int u = 0; u < U; ++u) {
+            const uint64_t i = wb + stride * u + 8ull * lane;
+            qv[u] = i < t1 ? *reinterpret_cast<const uint4*>(s + i) : make_uint4(0, 0, 0, 0);   // within the capacity
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t i = wb + stride * u + 8ull * lane;
+            uint32_t nv = 0;
+            uint64_t val = 0;
+            if (i < t1) {
+                nv = t1 - i >= 8 ? 8u : (uint32_t)(t1 - i);
+                const uint32_t w4[4] = {qv[u].x, qv[u].y, qv[u].z, qv[u].w};
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const uint32_t v = (w4[k >> 1] >> (16 * (k & 1))) & 0xffffu;
+                    if ((uint32_t)k < nv) {
+                        uint32_t bt = v & 0xffu;
+                        if (v & kPH) {
+                            bt = W[v & (kWin - 1)];
+                            ++nph;
+                            last = i + k + 1;
+                        }
+                        val |= (uint64_t)bt << (8 * k);
                     }
-                    val |= (uint64_t)b << (8 * k);
                 }
             }
+            const uint64_t P = C.out_off + i;
+            if (!vec) {                                   // byte stores, clipped to [lo, hi)
+                for (uint32_t k = 0; k < nv; ++k)
+                    if (P + k >= lo && P + k < hi) out[P + k - lo] = (uint8_t)(val >> (8 * k));
+                continue;
+            }
+            if (m == 0) {
+                if (nv == 8) *reinterpret_cast<uint64_t*>(out + P) = val;
+                else
+                    for (uint32_t k = 0; k < nv; ++k) out[P + k] = (uint8_t)(val >> (8 * k));
+                continue;
+            }
+            const uint64_t prev = __shfl_up_sync(FULL, val, 1);
+            const uint32_t prev_nv = __shfl_up_sync(FULL, nv, 1);
+            const uint32_t next_nv = __shfl_down_sync(FULL, nv, 1);
+            const uint32_t head = 8 - m;                  // my bytes in the aligned word at P - m
+            if (lane > 0 && prev_nv == 8 && nv >= head) {
+                *reinterpret_cast<uint64_t*>(out + P - m) = (val << (8 * m)) | (prev >> (64 - 8 * m));
+            } else {
+                for (uint32_t k = 0; k < nv && k < head; ++k) out[P + k] = (uint8_t)(val >> (8 * k));
+            }
+            const bool tail_by_next = lane < 31 && nv == 8 && next_nv >= head;
+            if (!tail_by_next)
+                for (uint32_t k = head; k < nv; ++k) out[P + k] = (uint8_t)(val >> (8 * k));
         }
-        const uint64_t P = C.out_off + i;
-        if (!vec) {                                   // byte stores, clipped to [lo, hi)
-            for (uint32_t k = 0; k < nv; ++k)
-                if (P + k >= lo && P + k < hi) out[P + k - lo] = (uint8_t)(val >> (8 * k));
-            continue;
-        }
-        if (m == 0) {
-            if (nv == 8) *reinterpret_cast<uint64_t*>(out + P) = val;
-            else
-                for (uint32_t k = 0; k < nv; ++k) out[P + k] = (uint8_t)(val >> (8 * k));
-            continue;
-        }
-        const uint64_t prev = __shfl_up_sync(FULL, val, 1);
-        const uint32_t prev_nv = __shfl_up_sync(FULL, nv, 1);
-        const uint32_t next_nv = __shfl_down_sync(FULL, nv, 1);
-        const uint32_t head = 8 - m;                  // my bytes in the aligned word at P - m
-        if (lane > 0 && prev_nv == 8 && nv >= head) {
-            *reinterpret_cast<uint64_t*>(out + P - m) = (val << (8 * m)) | (prev >> (64 - 8 * m));
-        } else {
-            for (uint32_t k = 0; k < nv && k < head; ++k) out[P + k] = (uint8_t)(val >> (8 * k));
-        }
-        const bool tail_by_next = lane < 31 && nv == 8 && next_nv >= head;
-        if (!tail_by_next)
-            for (uint32_t k = head; k < nv; ++k) out[P + k] = (uint8_t)(val >> (8 * k));
     }
     if (ph) {                                         // placeholder count and extent of the part
         for (int d = 16; d; d >>= 1) {
@@ -1587,61 +1619,91 @@ __device__ uint32_t xpow8(uint64_t n) {       // x^(8n) mod P
     return r;
 }
 
-constexpr uint32_t kCrcSeg = 4096;    // bytes per warp
-constexpr uint32_t kPiece = 128;   // bytes per lane
+constexpr uint32_t kCrcSeg = 4096;    // bytes per warp step
+constexpr uint32_t kPiece = 128;      // bytes per lane
 
-__global__ void __launch_bounds__(256) k_crc(FileDesc* files, int nfiles, uint64_t total_seg, const uint64_t* seg0) {
-    __shared__ uint32_t T[256];
+// raw CRC register (zero start) of one 128-byte piece, four bytes per step:
+// T[j][b] is the register after byte b followed by j zero bytes
+__device__ __forceinline__ uint32_t crc_piece(const uint32_t (*T)[256], const uint8_t* p, uint64_t n) {
+    uint32_t r = 0;
+    if (n == kPiece && ((reinterpret_cast<uintptr_t>(p) & 15) == 0)) {
+        const uint4* v = reinterpret_cast<const uint4*>(p);
+#pragma unroll 2
+        for (int q = 0; q < 8; ++q) {
+            const uint4 x = v[q];
+            const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                r ^= w4[j];
+                r = T[3][r & 0xffu] ^ T[2][(r >> 8) & 0xffu] ^ T[1][(r >> 16) & 0xffu] ^ T[0][r >> 24];
+            }
+        }
+    } else {
+        for (uint64_t i = 0; i < n; ++i) r = T[0][(r ^ p[i]) & 0xffu] ^ (r >> 8);
+    }
+    return r;
+}
+
+// Each warp takes a contiguous run of 4 KiB segments: the 32 lanes' pieces
+// of a segment are combined by their shift to the segment end, segments are
+// folded in order (R(A||B) = R(A) x^(8|B|) + R(B)), and a run is shifted to
+// the end of its member once and XOR-accumulated there.
+__global__ void __launch_bounds__(256) k_crc(FileDesc* files, int nfiles, uint64_t total_seg, const uint64_t* seg0,
+                                             uint64_t segs_per_warp) {
+    __shared__ uint32_t T[4][256];
     __shared__ uint32_t LS[32];
-    for (int k = threadIdx.x; k < 256; k += blockDim.x) T[k] = c_crc_tab[k];
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) {
+        uint32_t r = c_crc_tab[k];
+        T[0][k] = r;
+        for (int j = 1; j < 4; ++j) {
+            r = c_crc_tab[r & 0xffu] ^ (r >> 8);
+            T[j][k] = r;
+        }
+    }
     if (threadIdx.x < 32) LS[threadIdx.x] = c_lane_shift[threadIdx.x];
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    for (uint64_t sg = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); sg < total_seg; sg += nw) {
-        int lo = 0, hi = nfiles - 1;                  // member holding segment sg
+    const uint64_t w = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const uint64_t s_begin = w * segs_per_warp;
+    if (s_begin >= total_seg) return;
+    const uint64_t s_end = s_begin + segs_per_warp < total_seg ? s_begin + segs_per_warp : total_seg;
+    int f = -1;
+    uint32_t acc = 0;
+    uint64_t run_end = 0;
+    auto flush = [&]() {
+        if (f >= 0 && lane == 0 && run_end > 0) atomicXor(&files[f].crc_acc, gf2_mul(acc, xpow8(files[f].total - run_end)));
+    };
+    for (uint64_t sg = s_begin; sg < s_end; ++sg) {
+        int lo = 0, hi = nfiles - 1;                      // member holding segment sg
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (seg0[mid] <= sg) lo = mid;
             else hi = mid - 1;
         }
-        FileDesc& F = files[lo];
+        if (lo != f) {
+            flush();
+            f = lo;
+            acc = 0;
+            run_end = 0;
+        }
+        FileDesc& F = files[f];
         if (F.status != PGZ_OK || F.mode != 0) continue;
         const uint64_t D = F.total;
-        const uint64_t a = (sg - seg0[lo]) * kCrcSeg;
+        const uint64_t a = (sg - seg0[f]) * kCrcSeg;
         if (a >= D) continue;
         const uint64_t se = a + kCrcSeg < D ? a + kCrcSeg : D;
         const uint64_t pa = a + (uint64_t)kPiece * lane;
         const uint64_t pb = pa + kPiece < se ? pa + kPiece : se;
         uint32_t r = 0;
-        const uint8_t* out = F.out;
         if (pa < pb) {
-            if (pb - pa == kPiece && ((reinterpret_cast<uintptr_t>(out + pa) & 15) == 0)) {
-                const uint4* v = reinterpret_cast<const uint4*>(out + pa);
-#pragma unroll 2
-                for (int q = 0; q < 8; ++q) {
-                    const uint4 x = v[q];
-                    const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        uint32_t wv = w4[j];
-#pragma unroll
-                        for (int b = 0; b < 4; ++b) {
-                            r = T[(r ^ wv) & 0xffu] ^ (r >> 8);
-                            wv >>= 8;
-                        }
-                    }
-                }
-            } else {
-                for (uint64_t x = pa; x < pb; ++x) r = T[(r ^ out[x]) & 0xffu] ^ (r >> 8);
-            }
-            // shift to the end of the segment
-            if (se - a == kCrcSeg) r = gf2_mul(r, LS[31 - lane]);
-            else r = gf2_mul(r, xpow8(se - pb));
+            r = crc_piece(T, F.out + pa, pb - pa);
+            r = (se - a == kCrcSeg) ? gf2_mul(r, LS[31 - lane]) : gf2_mul(r, xpow8(se - pb));
         }
         for (int d = 16; d; d >>= 1) r ^= __shfl_xor_sync(FULL, r, d);
-        if (lane == 0) atomicXor(&F.crc_acc, gf2_mul(r, xpow8(D - se)));
+        acc = (run_end == 0 ? 0u : gf2_mul(acc, se - a == kCrcSeg ? c_x4096 : xpow8(se - a))) ^ r;
+        run_end = se;
     }
+    flush();
 }
 
 __global__ void k_finalize(FileDesc* files, int nfiles) {
@@ -1710,8 +1772,10 @@ void launch_translate(const FileDesc* files, ChunkDesc* chunks, int nchunks, uin
 
 void launch_crc(FileDesc* files, int nfiles, uint64_t total_seg, const uint64_t* seg0, cudaStream_t s) {
     if (nfiles <= 0 || total_seg == 0) return;
-    const uint64_t warps = total_seg < 152ull * 64 ? total_seg : 152ull * 64;
-    k_crc<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(files, nfiles, total_seg, seg0);
+    const uint64_t target = 152ull * 48;                  // warps
+    const uint64_t spw = (total_seg + target - 1) / target;
+    const uint64_t warps = (total_seg + spw - 1) / spw;
+    k_crc<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(files, nfiles, total_seg, seg0, spw);
 }
 
 void launch_finalize(FileDesc* files, int nfiles, cudaStream_t s) {
@@ -1747,9 +1811,16 @@ void upload_crc_tables() {
             if (e & 1) r = h_mul(r, x2k[k]);
         ls[l] = r;
     }
+    uint32_t x4096 = 0x80000000u;
+    {
+        uint64_t e = 8ull * 4096;
+        for (int k = 0; e; ++k, e >>= 1)
+            if (e & 1) x4096 = h_mul(x4096, x2k[k]);
+    }
     cudaMemcpyToSymbol(c_crc_tab, tab, sizeof tab);
     cudaMemcpyToSymbol(c_x2k, x2k, sizeof x2k);
     cudaMemcpyToSymbol(c_lane_shift, ls, sizeof ls);
+    cudaMemcpyToSymbol(c_x4096, &x4096, sizeof x4096);
 }
 
 }  // namespace pgz

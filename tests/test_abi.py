@@ -38,7 +38,7 @@ def test_every_declared_symbol_is_exported(pgz):
 
 def test_host_only_calls(pgz):
     cfg = pgz.pgz_config_init()
-    assert cfg.n_chunks == 1024 and cfg.confirm_blocks == 5 and cfg.threads_per_chunk == 32
+    assert cfg.n_chunks == 0 and cfg.chunk_bytes == 64 << 10 and cfg.confirm_blocks == 5 and cfg.threads_per_chunk == 32
     assert cfg.min_block == 1024 and cfg.max_block == 4 << 20
     allowed = {b for b in range(256) if (cfg.allowed[b >> 3] >> (b & 7)) & 1}
     assert allowed == {9, 10, 13} | set(range(32, 127))
