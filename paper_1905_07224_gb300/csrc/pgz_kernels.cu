@@ -1489,111 +1489,152 @@ __global__ void __launch_bounds__(1024) k_chain_expand(const FileDesc* __restric
 // ---------------------------------------------------------------------------
 // pass 2b: translation U_j -> w_i[j], 8 symbols per thread per step
 // ---------------------------------------------------------------------------
-constexpr uint32_t kTile = 65536;   // symbols per block
 
-__global__ void __launch_bounds__(1024) k_translate(const FileDesc* __restrict__ files, ChunkDesc* chunks,
-                                                    uint32_t tiles_per_chunk, const uint16_t* __restrict__ sym,
-                                                    const uint8_t* __restrict__ windows,
-                                                    const uint8_t* __restrict__ fillw) {
+// Persistent: block b translates parts b, b + gridDim.x, ...; the part's
+// window w_i is loaded once into shared memory (only if the part produced a
+// placeholder).  A thread turns 8 symbols (one 16-byte load) into 8 bytes:
+// without a placeholder two byte permutations pack them, otherwise each
+// placeholder is looked up in the window.  Four loads per thread in flight.
+constexpr int kTransThreads = 512;
+
+__global__ void __launch_bounds__(kTransThreads) k_translate(const FileDesc* __restrict__ files, ChunkDesc* chunks,
+                                                             int nchunks, const uint16_t* __restrict__ sym,
+                                                             const uint8_t* __restrict__ windows,
+                                                             const uint8_t* __restrict__ fillw) {
     __shared__ __align__(16) uint8_t W[kWin];
     __shared__ unsigned long long s_nph, s_last;
-    const uint32_t c = blockIdx.x / tiles_per_chunk, tile = blockIdx.x % tiles_per_chunk;
-    ChunkDesc& C = chunks[c];
-    const FileDesc& F = files[C.file];
-    if (F.status != PGZ_OK || C.state != CS_DONE) return;
-    const uint64_t t0 = (uint64_t)tile * kTile;
-    if (t0 >= C.n) return;
-    const uint64_t t1 = t0 + kTile < C.n ? t0 + kTile : C.n;
-    const bool ph = C.anyph != 0;
-    if (threadIdx.x == 0) {
-        s_nph = 0;
-        s_last = 0;
-    }
-    if (ph) {
-        const uint4* src = reinterpret_cast<const uint4*>(fillw ? fillw : windows + (uint64_t)c * kWin);
-        for (uint32_t k = threadIdx.x; k < kWin / 16; k += blockDim.x) reinterpret_cast<uint4*>(W)[k] = src[k];
-    }
-    __syncthreads();
-    const uint16_t* s = sym + C.sym_base;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    // output byte P of the member goes to out[P - out_lo] when out_lo <= P < out_hi
-    uint8_t* out = F.out;
-    const uint64_t lo = F.out_lo, hi = F.out_hi;
-    const bool vec = F.out_lo == 0 && F.out_hi == kNone && ((reinterpret_cast<uintptr_t>(out) & 7) == 0);
-    const uint32_t m = (uint32_t)(C.out_off & 7);
-    uint32_t nph = 0;
-    uint64_t last = 0;
-    constexpr int U = 4;                                 // 16-byte loads in flight per thread
-    const uint64_t stride = 256ull * nwarp;
-    for (uint64_t wb = t0 + 256ull * warp; wb < t1; wb += stride * U) {
-        uint4 qv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const uint64_t i = wb + stride * u + 8ull * lane;
-            qv[u] = i < t1 ? *reinterpret_cast<const uint4*>(s + i) : make_uint4(0, 0, 0, 0);   // within the capacity
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        ChunkDesc& C = chunks[c];
+        const FileDesc& F = files[C.file];
+        if (F.status != PGZ_OK || C.state != CS_DONE || C.n == 0) continue;   // uniform per block
+        const uint64_t t1 = C.n;
+        const bool ph = C.anyph != 0;
+        __syncthreads();                                  // the previous part's window is no longer read
+        if (threadIdx.x == 0) {
+            s_nph = 0;
+            s_last = 0;
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const uint64_t i = wb + stride * u + 8ull * lane;
-            uint32_t nv = 0;
-            uint64_t val = 0;
-            if (i < t1) {
-                nv = t1 - i >= 8 ? 8u : (uint32_t)(t1 - i);
-                const uint32_t w4[4] = {qv[u].x, qv[u].y, qv[u].z, qv[u].w};
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const uint32_t v = (w4[k >> 1] >> (16 * (k & 1))) & 0xffffu;
-                    if ((uint32_t)k < nv) {
-                        uint32_t bt = v & 0xffu;
-                        if (v & kPH) {
-                            bt = W[v & (kWin - 1)];
-                            ++nph;
-                            last = i + k + 1;
-                        }
-                        val |= (uint64_t)bt << (8 * k);
-                    }
-                }
-            }
-            const uint64_t P = C.out_off + i;
-            if (!vec) {                                   // byte stores, clipped to [lo, hi)
-                for (uint32_t k = 0; k < nv; ++k)
-                    if (P + k >= lo && P + k < hi) out[P + k - lo] = (uint8_t)(val >> (8 * k));
-                continue;
-            }
-            if (m == 0) {
-                if (nv == 8) *reinterpret_cast<uint64_t*>(out + P) = val;
-                else
-                    for (uint32_t k = 0; k < nv; ++k) out[P + k] = (uint8_t)(val >> (8 * k));
-                continue;
-            }
-            const uint64_t prev = __shfl_up_sync(FULL, val, 1);
-            const uint32_t prev_nv = __shfl_up_sync(FULL, nv, 1);
-            const uint32_t next_nv = __shfl_down_sync(FULL, nv, 1);
-            const uint32_t head = 8 - m;                  // my bytes in the aligned word at P - m
-            if (lane > 0 && prev_nv == 8 && nv >= head) {
-                *reinterpret_cast<uint64_t*>(out + P - m) = (val << (8 * m)) | (prev >> (64 - 8 * m));
-            } else {
-                for (uint32_t k = 0; k < nv && k < head; ++k) out[P + k] = (uint8_t)(val >> (8 * k));
-            }
-            const bool tail_by_next = lane < 31 && nv == 8 && next_nv >= head;
-            if (!tail_by_next)
-                for (uint32_t k = head; k < nv; ++k) out[P + k] = (uint8_t)(val >> (8 * k));
-        }
-    }
-    if (ph) {                                         // placeholder count and extent of the part
-        for (int d = 16; d; d >>= 1) {
-            nph += __shfl_xor_sync(FULL, nph, d);
-            const uint64_t o = shfl64(last, lane ^ d);
-            last = o > last ? o : last;
-        }
-        if (lane == 0) {
-            atomicAdd(&s_nph, (unsigned long long)nph);
-            atomicMax(&s_last, (unsigned long long)last);
+        if (ph) {
+            const uint4* src = reinterpret_cast<const uint4*>(fillw ? fillw : windows + (uint64_t)c * kWin);
+            for (uint32_t k = threadIdx.x; k < kWin / 16; k += blockDim.x) reinterpret_cast<uint4*>(W)[k] = src[k];
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            atomicAdd(reinterpret_cast<unsigned long long*>(&C.nph), s_nph);
-            atomicMax(reinterpret_cast<unsigned long long*>(&C.last_ph), s_last);
+        const uint16_t* s = sym + C.sym_base;
+        // output byte P of the member goes to out[P - out_lo] when out_lo <= P < out_hi
+        uint8_t* out = F.out;
+        const uint64_t lo = F.out_lo, hi = F.out_hi;
+        const bool vec = F.out_lo == 0 && F.out_hi == kNone && ((reinterpret_cast<uintptr_t>(out) & 7) == 0);
+        const uint32_t m = (uint32_t)(C.out_off & 7);
+        uint32_t nph = 0, last = 0, last_i = 0xffffffffu, last_w[4] = {0, 0, 0, 0};
+        constexpr int U = 4;
+        // warp `warp` writes the contiguous slices [ws, we) of 256 symbols; lane 31's bytes of a
+        // slice are carried to lane 0 of the next, so every word inside the range is one 8-byte store
+        const uint32_t n32 = (uint32_t)t1;
+        const uint32_t nsl = (n32 + 255) / 256, per = (nsl + nwarp - 1) / nwarp;
+        const uint32_t ws = min(nsl, per * (uint32_t)warp) * 256u, we = min(nsl, per * (uint32_t)(warp + 1)) * 256u;
+        uint64_t carry = 0;
+        uint32_t carry_nv = 0;                            // valid symbols of the carried lane (0: none)
+        for (uint32_t wb = ws; wb < we; wb += 256u * U) {
+            uint4 qv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t i = wb + 256u * u + 8u * (uint32_t)lane;
+                qv[u] = (i < n32 && i < we) ? *reinterpret_cast<const uint4*>(s + i) : make_uint4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t sb = wb + 256u * u;
+                if (sb >= we) break;                      // uniform
+                const uint32_t i = sb + 8u * (uint32_t)lane;
+                const uint32_t nv = i < n32 ? min(n32 - i, 8u) : 0u;
+                uint32_t w4[4] = {qv[u].x, qv[u].y, qv[u].z, qv[u].w};
+                if (nv < 8) {                                 // symbols past the part's end are bytes 0
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (2u * k >= nv) w4[k] = 0;
+                        else if (2u * k + 1 >= nv) w4[k] &= 0xffffu;
+                    }
+                }
+                const uint32_t anyp = (w4[0] | w4[1] | w4[2] | w4[3]) & 0x80008000u;
+                uint32_t b0, b1;
+                if (!anyp) {
+                    b0 = __byte_perm(w4[0], w4[1], 0x6420);
+                    b1 = __byte_perm(w4[2], w4[3], 0x6420);
+                } else {
+                    uint32_t pr[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint32_t w = w4[k];
+                        const uint32_t lo = (w & 0x8000u) ? (uint32_t)W[w & 0x7fffu] : (w & 0xffu);
+                        const uint32_t hi = (w & 0x80000000u) ? (uint32_t)W[(w >> 16) & 0x7fffu] : ((w >> 16) & 0xffu);
+                        pr[k] = lo | (hi << 8);
+                        nph += __popc(w & 0x80008000u);
+                    }
+                    b0 = __byte_perm(pr[0], pr[1], 0x5410);
+                    b1 = __byte_perm(pr[2], pr[3], 0x5410);
+                    last_i = i;                               // the exact position is worked out once, at the end
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) last_w[k] = w4[k];
+                }
+                const uint64_t val = (uint64_t)b0 | ((uint64_t)b1 << 32);
+                const uint64_t P = C.out_off + i;
+                if (!vec) {                               // byte stores, clipped to [lo, hi)
+                    for (uint32_t k = 0; k < nv; ++k)
+                        if (P + k >= lo && P + k < hi) out[P + k - lo] = (uint8_t)(val >> (8 * k));
+                    continue;
+                }
+                if (m == 0) {
+                    if (nv == 8) *reinterpret_cast<uint64_t*>(out + P) = val;
+                    else
+                        for (uint32_t k = 0; k < nv; ++k) out[P + k] = (uint8_t)(val >> (8 * k));
+                    continue;
+                }
+                // the previous lane holds 8 symbols whenever this one holds any; lane 0's
+                // predecessor is the previous slice's lane 31 (carried)
+                uint64_t prev = __shfl_up_sync(FULL, val, 1);
+                uint32_t prev_nv = 8;
+                if (lane == 0) {
+                    prev = carry;
+                    prev_nv = carry_nv;
+                }
+                carry = shfl64(val, 31);
+                carry_nv = sb + 248u < n32 ? min(n32 - (sb + 248u), 8u) : 0u;
+                const uint32_t next_nv = i + 8u < n32 ? min(n32 - (i + 8u), 8u) : 0u;
+                const uint32_t head = 8 - m;              // my bytes in the aligned word at P - m
+                if (prev_nv == 8 && nv >= head) {
+                    *reinterpret_cast<uint64_t*>(out + P - m) = (val << (8 * m)) | (prev >> (64 - 8 * m));
+                } else {
+                    for (uint32_t k = 0; k < nv && k < head; ++k) out[P + k] = (uint8_t)(val >> (8 * k));
+                }
+                // lane 31: the next slice's lane 0 takes the tail only inside this warp's range
+                const uint32_t nx = sb + 256u;
+                const uint32_t next0_nv = (nx < we && nx < n32) ? min(n32 - nx, 8u) : 0u;
+                const bool tail_by_next = nv == 8 && (lane < 31 ? next_nv >= head : next0_nv >= head);
+                if (!tail_by_next)
+                    for (uint32_t k = head; k < nv; ++k) out[P + k] = (uint8_t)(val >> (8 * k));
+            }
+        }
+        if (ph) {                                         // placeholder count and extent of the part
+            if (last_i != 0xffffffffu) {                  // one past the last placeholder of the last slice that had one
+                const uint32_t fl = ((last_w[0] >> 15) & 1u) | ((last_w[0] >> 30) & 2u) | ((last_w[1] >> 13) & 4u) |
+                                    ((last_w[1] >> 28) & 8u) | ((last_w[2] >> 11) & 16u) | ((last_w[2] >> 26) & 32u) |
+                                    ((last_w[3] >> 9) & 64u) | ((last_w[3] >> 24) & 128u);
+                last = last_i + (32u - __clz(fl));
+            }
+            for (int d = 16; d; d >>= 1) {
+                nph += __shfl_xor_sync(FULL, nph, d);
+                last = max(last, __shfl_xor_sync(FULL, last, d));
+            }
+            if (lane == 0) {
+                atomicAdd(&s_nph, (unsigned long long)nph);
+                atomicMax(&s_last, (unsigned long long)last);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                C.nph = s_nph;
+                C.last_ph = s_last;
+            }
         }
     }
 }
@@ -1622,24 +1663,31 @@ __device__ uint32_t xpow8(uint64_t n) {       // x^(8n) mod P
 constexpr uint32_t kCrcSeg = 4096;    // bytes per warp step
 constexpr uint32_t kPiece = 128;      // bytes per lane
 
-// raw CRC register (zero start) of one 128-byte piece, four bytes per step:
-// T[j][b] is the register after byte b followed by j zero bytes
-__device__ __forceinline__ uint32_t crc_piece(const uint32_t (*T)[256], const uint8_t* p, uint64_t n) {
+// raw CRC register (zero start) of a 128-byte piece, a byte per step, from a
+// table replicated once per lane (entry b of lane l at word 32*b + l: every
+// lane reads its own bank)
+__device__ __forceinline__ uint32_t crc_bytes(const uint32_t* T, int lane, const uint8_t* p, uint64_t n) {
     uint32_t r = 0;
     if (n == kPiece && ((reinterpret_cast<uintptr_t>(p) & 15) == 0)) {
         const uint4* v = reinterpret_cast<const uint4*>(p);
-#pragma unroll 2
+        uint4 x[8];                                       // the whole piece in flight first
+#pragma unroll
+        for (int q = 0; q < 8; ++q) x[q] = v[q];
+#pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const uint4 x = v[q];
-            const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
+            const uint32_t w4[4] = {x[q].x, x[q].y, x[q].z, x[q].w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                r ^= w4[j];
-                r = T[3][r & 0xffu] ^ T[2][(r >> 8) & 0xffu] ^ T[1][(r >> 16) & 0xffu] ^ T[0][r >> 24];
+                uint32_t wv = w4[j];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    r = T[32u * ((r ^ wv) & 0xffu) + lane] ^ (r >> 8);
+                    wv >>= 8;
+                }
             }
         }
     } else {
-        for (uint64_t i = 0; i < n; ++i) r = T[0][(r ^ p[i]) & 0xffu] ^ (r >> 8);
+        for (uint64_t i = 0; i < n; ++i) r = T[32u * ((r ^ p[i]) & 0xffu) + lane] ^ (r >> 8);
     }
     return r;
 }
@@ -1650,16 +1698,9 @@ __device__ __forceinline__ uint32_t crc_piece(const uint32_t (*T)[256], const ui
 // the end of its member once and XOR-accumulated there.
 __global__ void __launch_bounds__(256) k_crc(FileDesc* files, int nfiles, uint64_t total_seg, const uint64_t* seg0,
                                              uint64_t segs_per_warp) {
-    __shared__ uint32_t T[4][256];
+    __shared__ uint32_t T[256 * 32];
     __shared__ uint32_t LS[32];
-    for (int k = threadIdx.x; k < 256; k += blockDim.x) {
-        uint32_t r = c_crc_tab[k];
-        T[0][k] = r;
-        for (int j = 1; j < 4; ++j) {
-            r = c_crc_tab[r & 0xffu] ^ (r >> 8);
-            T[j][k] = r;
-        }
-    }
+    for (int k = threadIdx.x; k < 256 * 32; k += blockDim.x) T[k] = c_crc_tab[k >> 5];
     if (threadIdx.x < 32) LS[threadIdx.x] = c_lane_shift[threadIdx.x];
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -1696,7 +1737,7 @@ __global__ void __launch_bounds__(256) k_crc(FileDesc* files, int nfiles, uint64
         const uint64_t pb = pa + kPiece < se ? pa + kPiece : se;
         uint32_t r = 0;
         if (pa < pb) {
-            r = crc_piece(T, F.out + pa, pb - pa);
+            r = crc_bytes(T, lane, F.out + pa, pb - pa);
             r = (se - a == kCrcSeg) ? gf2_mul(r, LS[31 - lane]) : gf2_mul(r, xpow8(se - pb));
         }
         for (int d = 16; d; d >>= 1) r ^= __shfl_xor_sync(FULL, r, d);
@@ -1766,13 +1807,14 @@ void launch_chain(const FileDesc* files, const ChunkDesc* chunks, int nfiles, in
 void launch_translate(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint64_t max_cap,
                       const uint16_t* sym, const uint8_t* windows, const uint8_t* fillw, cudaStream_t s) {
     if (nchunks <= 0) return;
-    const uint32_t tpc = (uint32_t)((max_cap + kTile - 1) / kTile);
-    k_translate<<<(unsigned)(tpc * (uint64_t)nchunks), 1024, 0, s>>>(files, chunks, tpc, sym, windows, fillw);
+    (void)max_cap;
+    const int grid = nchunks < 152 * 4 ? nchunks : 152 * 4;
+    k_translate<<<grid, kTransThreads, 0, s>>>(files, chunks, nchunks, sym, windows, fillw);
 }
 
 void launch_crc(FileDesc* files, int nfiles, uint64_t total_seg, const uint64_t* seg0, cudaStream_t s) {
     if (nfiles <= 0 || total_seg == 0) return;
-    const uint64_t target = 152ull * 48;                  // warps
+    const uint64_t target = 152ull * 56;                  // warps (7 blocks of 8 warps per SM)
     const uint64_t spw = (total_seg + target - 1) / target;
     const uint64_t warps = (total_seg + spw - 1) / spw;
     k_crc<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(files, nfiles, total_seg, seg0, spw);
