@@ -3,11 +3,18 @@
 
 Default workload (one GPU): two 256 MiB synthetic FASTQ files (150 bp reads,
 seed 1), gzip level 1 and level 9 via host zlib.  One step decompresses both
-files through the C ABI (pgz_decompress, device-resident input and output):
-block-start search, pass 1, window chain, translation, CRC-32/ISIZE check.
+files (block-start search, pass 1, window chain, translation, CRC-32/ISIZE
+check) with inputs and outputs resident in device memory, in two forms:
+
+  batched (the reported value): both files in one run of the pass kernels,
+      parts of --chunk-bytes compressed bytes taken from a device work queue,
+      captured once in a CUDA graph (pgz_batch_prepare / pgz_batch_run);
+  plain: one file at a time through pgz_decompress with 1024 equal parts per
+      file, with sync-failure and placeholder statistics per level.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pgz|reference]
-                  [--workload fastq256|fastq1m|batched]
+                  [--workload fastq256|fastq1m] [--chunk-bytes B]
+                  [--profile-case MIB:LEVEL:CALLS]
 
 Prints one JSON line.  --impl reference times the CPU oracle (the plain
 bit-at-a-time RFC 1951 inflater under oracle/) on the same files.  Under
@@ -30,6 +37,11 @@ sys.path.insert(0, ROOT)
 
 L2_BYTES = 126 * (1 << 20)
 CHUNK_BYTES = 64 << 10        # compressed bytes per part (about two DEFLATE blocks of zlib output)
+PLAIN_PARTS = 1024            # parts per file of the plain one-file-at-a-time form
+METRIC = "decompressed GB/s on 1 GB300 (batched vs plain), %HBM roofline"
+# DRAM bytes (read + write) of pass 1 per decompressed byte: ncu capture of k_sync and k_inflate on one
+# 256 MiB FASTQ gzip -1 file (profiles/pass1_fastq256_l1.md); None while the kernels differ from the capture
+PASS1_TRAFFIC_PER_OUT_BYTE = None
 
 
 def _peaks():
@@ -123,6 +135,7 @@ class Clocks:
 # the GPU arm
 # ---------------------------------------------------------------------------
 def run_pgz(args, rank, world):
+    """Both files of the workload, batched (headline) and plain (one file at a time, fixed part count)."""
     import numpy as np
     import torch
     from paper_1905_07224_gb300 import build, pgz
@@ -132,96 +145,137 @@ def run_pgz(args, rank, world):
     torch.cuda.set_device(dev)
     files, desc = make_workload(args.workload)
     stream = torch.cuda.current_stream()
-    cfg = pgz.pgz_config_init(device=dev, cuda_stream=stream.cuda_stream, n_chunks=0, chunk_bytes=args.chunk_bytes)
-    ctx = pgz.pgz_create(cfg)
     gz_dev = [torch.from_numpy(np.frombuffer(g, dtype=np.uint8).copy()).cuda() for _, _, g in files]
     outs = [torch.empty(len(r) + 4096, dtype=torch.uint8, device="cuda") for _, r, _ in files]
     total_out = sum(len(r) for _, r, _ in files)
     total_in = sum(len(g) for _, _, g in files)
-
-    def step(stats=False):
-        res = []
-        for k, (_, raw, g) in enumerate(files):
-            st, n, s = pgz.pgz_decompress(ctx, gz_dev[k].data_ptr(), len(g), outs[k].data_ptr(), outs[k].numel(),
-                                          stats)
-            if st != 0 or n != len(raw):
-                raise RuntimeError(f"pgz_decompress failed: {pgz.pgz_strerror(st)}")
-            res.append(s)
-        return res
-
-    # correctness of the timed configuration
-    step()
-    for k, (_, raw, _) in enumerate(files):
-        if outs[k][:len(raw)].cpu().numpy().tobytes() != raw:
-            raise RuntimeError("output mismatch")
-    for _ in range(args.warmup):
-        step()
+    jobs = [(gz_dev[k].data_ptr(), len(g), outs[k].data_ptr(), outs[k].numel()) for k, (_, _, g) in enumerate(files)]
     dist = world > 1
     if dist:
         import torch.distributed as tdist
-        tdist.barrier()
-    torch.cuda.synchronize()
-    l0 = pgz.pgz_kernel_launches(ctx)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with Clocks(dev) as clk:
+
+    def check(what):
+        torch.cuda.synchronize()
+        for k, (_, raw, _) in enumerate(files):
+            if outs[k][:len(raw)].cpu().numpy().tobytes() != raw:
+                raise RuntimeError(f"output mismatch ({what}, file {k})")
+        for o in outs:
+            o.fill_(0)
+
+    def timed(step, ctx):
+        """W untimed steps, then K steps between barriers, CUDA events on the launching stream."""
+        for _ in range(args.warmup):
+            step()
+        if dist:
+            tdist.barrier()
+        torch.cuda.synchronize()
+        l0 = pgz.pgz_kernel_launches(ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
             step()
         e1.record(stream)
         torch.cuda.synchronize()
-    if dist:
-        tdist.barrier()
-    launches = pgz.pgz_kernel_launches(ctx) - l0
-    ms = e0.elapsed_time(e1) / args.steps
+        if dist:
+            tdist.barrier()
+        return e0.elapsed_time(e1) / args.steps, pgz.pgz_kernel_launches(ctx) - l0
+
+    # ---- batched: every file of the step in one graph-captured run of the pass kernels
+    ctx_b = pgz.pgz_create(pgz.pgz_config_init(device=dev, cuda_stream=stream.cuda_stream, n_chunks=0,
+                                               chunk_bytes=args.chunk_bytes))
+    batch = pgz.Batch(ctx_b, jobs)
+
+    def step_batched():
+        r, res, _ = batch.run()
+        if r != 0 or any(st != 0 or n != len(files[k][1]) for k, (st, n) in enumerate(res)):
+            raise RuntimeError(f"pgz_batch_run failed: {pgz.pgz_strerror(r)}")
+
+    step_batched()
+    check("batched")
+    with Clocks(dev) as clk:
+        ms, launches = timed(step_batched, ctx_b)
     clocks = clk.summary()
-    # per-stage times of the same configuration (library CUDA events on the same stream)
+    # per-stage times of the same batch (the library's CUDA events on the same stream, graph-free run)
     stage = {k: 0.0 for k in ("ms_sync", "ms_inflate", "ms_chain", "ms_translate", "ms_crc", "ms_total")}
     nst = 3
-    chunks, empties, ph, syms = [], 0, 0, 0
     for _ in range(nst):
-        for s in step(stats=True):
-            for k in stage:
-                stage[k] += s[k] / nst
-    for s in step(stats=True):
-        chunks.append(s["chunks"])
-        empties += s["empty_chunks"]
-        ph += s["placeholders"]
-        syms += s["symbols"]
-    # end to end through the host entry point: pinned host input -> device -> pinned host output
+        r, _, s = pgz.pgz_decompress_batch(ctx_b, jobs, stats=True)
+        if r != 0:
+            raise RuntimeError(f"pgz_decompress_batch failed: {pgz.pgz_strerror(r)}")
+        for k in stage:
+            stage[k] += s[k] / nst
+    batch_parts = s["chunks"]
+
+    # ---- plain: one file at a time through pgz_decompress, PLAIN_PARTS equal parts per file
+    ctx_p = pgz.pgz_create(pgz.pgz_config_init(device=dev, cuda_stream=stream.cuda_stream, n_chunks=PLAIN_PARTS))
+
+    def step_plain(stats=False):
+        res = []
+        for k, (_, raw, g) in enumerate(files):
+            st, n, s = pgz.pgz_decompress(ctx_p, jobs[k][0], jobs[k][1], jobs[k][2], jobs[k][3], stats)
+            if st != 0 or n != len(raw):
+                raise RuntimeError(f"pgz_decompress failed: {pgz.pgz_strerror(st)}")
+            res.append(s)
+        return res
+
+    step_plain()
+    check("plain")
+    ms_plain, _ = timed(step_plain, ctx_p)
+    per_level = {}
+    for (label, raw, g), s in zip(files, step_plain(stats=True)):
+        per_level[label] = {"parts": s["chunks"], "empty_parts": s["empty_chunks"], "false_syncs": s["false_syncs"],
+                            "retries": s["retries"], "placeholder_fraction": round(s["placeholders"] / max(1, s["symbols"]), 4),
+                            "in_bytes": len(g), "ms": round(s["ms_total"], 3)}
+    pgz.pgz_destroy(ctx_p)
+
+    # ---- end to end: pinned host input -> device, the batched run, device -> pinned host output
     pin_in = [torch.from_numpy(np.frombuffer(g, dtype=np.uint8).copy()).pin_memory() for _, _, g in files]
     pin_out = [torch.empty(len(r) + 4096, dtype=torch.uint8).pin_memory() for _, r, _ in files]
 
     def e2e_step():
-        for k, (_, raw, g) in enumerate(files):
-            st, n, _ = pgz.pgz_decompress_host(ctx, pin_in[k].numpy(), pin_out[k].numpy())
-            if st != 0 or n != len(raw):
-                raise RuntimeError(f"pgz_decompress_host failed: {pgz.pgz_strerror(st)}")
+        for k in range(len(files)):
+            gz_dev[k].copy_(pin_in[k], non_blocking=True)
+        step_batched()
+        for k, (_, raw, _) in enumerate(files):
+            pin_out[k][:len(raw)].copy_(outs[k][:len(raw)], non_blocking=True)
+        torch.cuda.synchronize()
 
     e2e_step()
-    if pin_out[0][:len(files[0][1])].numpy().tobytes() != files[0][1]:
-        raise RuntimeError("e2e output mismatch")
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    for k, (_, raw, _) in enumerate(files):
+        if pin_out[k][:len(raw)].numpy().tobytes() != raw:
+            raise RuntimeError("e2e output mismatch")
+    # each step timed on the host clock (it includes the copies and the host side of the call); the
+    # median step is reported so that one host stall does not stand for the whole run
+    e2e_steps = []
     for _ in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         e2e_step()
-    torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / max(1, args.steps)
-    # max over ranks
+        e2e_steps.append((time.perf_counter() - t0) * 1e3)
+    e2e_ms = statistics.median(e2e_steps)
+    e2e_mean = sum(e2e_steps) / len(e2e_steps)
+    batch.free()
+    pgz.pgz_destroy(ctx_b)
     if dist:
-        t = torch.tensor([ms, e2e_ms], device="cuda")
+        t = torch.tensor([ms, e2e_ms, ms_plain], device="cuda")
         tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms, e2e_ms = float(t[0]), float(t[1])
-    pgz.pgz_destroy(ctx)
+        ms, e2e_ms, ms_plain = float(t[0]), float(t[1]), float(t[2])
+
     gbs = world * total_out / (ms * 1e-3) / 1e9
     pk = _peaks()
     hbm = pk.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
     pass1_ms = stage["ms_sync"] + stage["ms_inflate"]
     alg1 = total_in + 2 * total_out                  # compressed bytes read + u16 symbols written
     ach1 = alg1 / (pass1_ms * 1e-3) / 1e9
     alg4 = 3 * total_out                             # u16 symbols read + bytes written
     ach4 = alg4 / (stage["ms_translate"] * 1e-3) / 1e9 if stage["ms_translate"] > 0 else None
+    alg5 = total_out                                 # bytes read by the CRC
+    ach5 = alg5 / (stage["ms_crc"] * 1e-3) / 1e9 if stage["ms_crc"] > 0 else None
+    traffic1 = PASS1_TRAFFIC_PER_OUT_BYTE * total_out if PASS1_TRAFFIC_PER_OUT_BYTE else None
     line = {
-        "metric": "decompressed GB/s on 1 GB300 (two-pass parallel gzip decompression, plain API)",
+        "metric": METRIC,
         "value": round(gbs, 3),
         "unit": "GB/s",
         "n_gpus": world,
@@ -233,21 +287,27 @@ def run_pgz(args, rank, world):
         "vs_baseline": None,
         "dtype": "u8",
         "data": "synthetic",
-        "config": {"workload": desc, "files": len(files), "out_bytes_per_step": total_out,
-                   "in_bytes_per_step": total_in, "chunk_bytes": args.chunk_bytes, "parts": chunks,
-                   "empty_parts": empties, "placeholder_fraction": round(ph / max(1, syms), 4),
+        "config": {"workload": desc, "form": "batched (all files of the step in one graph-captured run)",
+                   "files": len(files), "out_bytes_per_step": total_out, "in_bytes_per_step": total_in,
+                   "chunk_bytes": args.chunk_bytes, "parts": batch_parts,
                    "l2": "inputs (%.0f MB) and outputs (%.0f MB) larger than L2" % (total_in / 1e6, total_out / 1e6),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "compressed_MBps": round(world * total_in / (ms * 1e-3) / 1e6, 1),
+        "plain": {"value": round(world * total_out / (ms_plain * 1e-3) / 1e9, 3), "unit": "GB/s",
+                  "ms_per_step": round(ms_plain, 3), "parts_per_file": PLAIN_PARTS,
+                  "form": "one file at a time through pgz_decompress", "per_level": per_level},
         "stages_ms": {k: round(v, 3) for k, v in stage.items()},
         "roofline": {"bound": "hbm", "kernel": "pass 1 (k_sync + k_inflate)", "achieved": round(ach1, 2),
-                     "peak": hbm, "unit": "GB/s", "frac": round(ach1 / hbm, 5) if hbm else None,
-                     "traffic": None, "peak_source": "measured" if hbm else "fallback 6800"},
+                     "peak": hbm, "unit": "GB/s", "frac": round(ach1 / hbm, 5),
+                     "traffic": round(traffic1) if traffic1 else None, "peak_source": peak_src},
         "roofline_translate": {"bound": "hbm", "kernel": "k_translate", "achieved": round(ach4, 1) if ach4 else None,
-                               "peak": hbm, "unit": "GB/s",
-                               "frac": round(ach4 / hbm, 4) if (ach4 and hbm) else None},
+                               "peak": hbm, "unit": "GB/s", "frac": round(ach4 / hbm, 4) if ach4 else None},
+        "roofline_crc": {"bound": "hbm", "kernel": "k_crc", "achieved": round(ach5, 1) if ach5 else None,
+                         "peak": hbm, "unit": "GB/s", "frac": round(ach5 / hbm, 4) if ach5 else None},
         "e2e": {"value": round(world * total_out / (e2e_ms * 1e-3) / 1e9, 3), "unit": "GB/s",
-                "h2d_bytes_per_step": total_in, "d2h_bytes_per_step": total_out},
+                "h2d_bytes_per_step": total_in, "d2h_bytes_per_step": total_out,
+                "ms_per_step_median": round(e2e_ms, 3), "ms_per_step_mean": round(e2e_mean, 3),
+                "path": "pinned host -> device copies, pgz_batch_run, device -> pinned host copies"},
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
@@ -296,13 +356,41 @@ def run_reference(args):
         step()
     ms = (time.perf_counter() - t0) * 1e3 / args.steps
     v = total / (ms * 1e-3) / 1e9
-    return {"impl": "reference", "metric": "decompressed GB/s on 1 GB300 (two-pass parallel gzip decompression, plain API)",
+    return {"impl": "reference", "metric": METRIC,
             "value": round(v, 4), "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(ms, 1), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u8", "data": "synthetic", "config": {"workload": desc, "out_bytes_per_step": total},
             "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
                              "sample": f"oracle.gunzip (one thread), the whole workload per step"},
             "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_profile_case(spec: str, chunk_bytes: int):
+    """--profile-case MIB:LEVEL:CALLS -- a small fixed case for ncu captures: one synthetic FASTQ file
+    (150 bp, seed 1) of MIB MiB at gzip LEVEL, decompressed CALLS times through pgz_decompress on device
+    buffers; the output of the last call is checked byte for byte and its stage times printed."""
+    import numpy as np
+    import torch
+    from paper_1905_07224_gb300 import build, pgz, synth
+    mib, level, calls = (int(x) for x in spec.split(":"))
+    build.build()
+    raw = synth.fastq(mib << 20, 150, 0.001, 1)
+    gz = synth.gzip_compress(raw, level)
+    stream = torch.cuda.current_stream()
+    ctx = pgz.pgz_create(pgz.pgz_config_init(device=0, cuda_stream=stream.cuda_stream, n_chunks=0,
+                                             chunk_bytes=chunk_bytes))
+    d_in = torch.from_numpy(np.frombuffer(gz, dtype=np.uint8).copy()).cuda()
+    d_out = torch.empty(len(raw) + 4096, dtype=torch.uint8, device="cuda")
+    for _ in range(calls):
+        st, n, s = pgz.pgz_decompress(ctx, d_in.data_ptr(), len(gz), d_out.data_ptr(), d_out.numel(), True)
+        if st != 0 or n != len(raw):
+            raise RuntimeError(f"pgz_decompress failed: {pgz.pgz_strerror(st)}")
+    torch.cuda.synchronize()
+    if d_out[:len(raw)].cpu().numpy().tobytes() != raw:
+        raise RuntimeError("output mismatch")
+    pgz.pgz_destroy(ctx)
+    return {"case": f"{mib} MiB FASTQ gzip -{level}", "in_bytes": len(gz), "out_bytes": len(raw),
+            **{k: (round(v, 3) if isinstance(v, float) else v) for k, v in s.items()}}
 
 
 def main():
@@ -313,7 +401,12 @@ def main():
     ap.add_argument("--impl", default="pgz", choices=["pgz", "reference"])
     ap.add_argument("--workload", default="fastq256", choices=["fastq256", "fastq1m"])
     ap.add_argument("--chunk-bytes", type=int, default=CHUNK_BYTES)
+    ap.add_argument("--profile-case", default=None, metavar="MIB:LEVEL:CALLS",
+                    help="run one small checked case for an ncu capture and print its stage times")
     args = ap.parse_args()
+    if args.profile_case:
+        print(json.dumps(run_profile_case(args.profile_case, args.chunk_bytes)), flush=True)
+        return
     args.warmup = max(3, args.warmup)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

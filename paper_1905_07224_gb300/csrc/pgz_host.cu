@@ -125,7 +125,7 @@ struct Plan {
     bool chain = true, translate = true, crc = true;
     bool results_valid = false;   // the device chunk array holds the last run's results
     const uint8_t* fill = nullptr;   // device window of fill bytes (mode 1)
-    DBuf d_files, d_chunks, d_g0, d_gn, d_gfile, d_seg0, d_sym, d_windows, d_gmaps, d_wstart, d_tok;
+    DBuf d_files, d_chunks, d_g0, d_gn, d_gfile, d_seg0, d_sym, d_windows, d_gmaps, d_wstart, d_tok, d_queue;
     PBuf h_files, h_chunks;
     cudaGraphExec_t graph = nullptr;
     void release() {
@@ -140,6 +140,7 @@ struct Plan {
         d_gmaps.release();
         d_wstart.release();
         d_tok.release();
+        d_queue.release();
         h_files.release();
         h_chunks.release();
         if (graph) cudaGraphExecDestroy(graph);
@@ -290,7 +291,8 @@ int layout(Plan& P) {
     if (!e) e = P.d_gfile.ensure(ng * sizeof(int32_t));
     if (!e) e = P.d_seg0.ensure(nf * sizeof(uint64_t));
     if (!e) e = P.d_sym.ensure(P.sym_total * sizeof(uint16_t));
-    if (!e) e = P.d_tok.ensure(nc * token_words_per_part() * sizeof(uint32_t));
+    if (!e) e = P.d_tok.ensure((size_t)pass1_warps((int)nc) * token_words_per_part() * sizeof(uint32_t));
+    if (!e) e = P.d_queue.ensure(2 * sizeof(uint32_t));
     if (!e && P.chain) e = P.d_windows.ensure(nc * (size_t)kWin);
     if (!e && P.chain) e = P.d_gmaps.ensure(ng * (size_t)kWin * sizeof(uint16_t));
     if (!e && P.chain) e = P.d_wstart.ensure(ng * (size_t)kWin);
@@ -320,10 +322,10 @@ int enqueue(pgz_ctx* ctx, Plan& P, cudaStream_t s, bool timed) {
     uint16_t* sym = P.d_sym.as<uint16_t>();
     int k = 0;
     if (timed) cudaEventRecord(ctx->ev[0], s);
-    launch_sync(df, dc, (int)nc, sym, P.d_tok.as<uint32_t>(), ctx->kp, s);
+    launch_sync(df, dc, (int)nc, sym, P.d_tok.as<uint32_t>(), P.d_queue.as<uint32_t>(), ctx->kp, s);
     if (cudaPeekAtLastError() != cudaSuccess) return PGZ_E_CUDA;
     if (timed) cudaEventRecord(ctx->ev[1], s);
-    launch_inflate(df, dc, (int)nc, sym, P.d_tok.as<uint32_t>(), ctx->kp, s);
+    launch_inflate(df, dc, (int)nc, sym, P.d_tok.as<uint32_t>(), P.d_queue.as<uint32_t>() + 1, ctx->kp, s);
     if (cudaPeekAtLastError() != cudaSuccess) return PGZ_E_CUDA;
     launch_plan(df, dc, (int)nf, s);
     k += 3;

@@ -97,12 +97,15 @@ struct ChunkDesc {
 };
 
 // host-side launch wrappers (pgz_kernels.cu)
-// tok: per part, token_words_per_part() u32 of scratch for the parallel block decoder
+// tok: token_words_per_part() u32 of parallel-block-decoder scratch for each of
+//      pass1_warps(nchunks) warps (at most nchunks rounded up to 4);
+// queue: one u32 work counter per kernel (zeroed by the launcher on the stream).
 void launch_sync(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, uint32_t* tok,
-                 const KParams& p, cudaStream_t s);
+                 uint32_t* queue, const KParams& p, cudaStream_t s);
 void launch_inflate(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, uint32_t* tok,
-                    const KParams& p, cudaStream_t s);
+                    uint32_t* queue, const KParams& p, cudaStream_t s);
 uint64_t token_words_per_part();
+int pass1_warps(int nchunks);
 void launch_plan(FileDesc* files, ChunkDesc* chunks, int nfiles, cudaStream_t s);
 void launch_chain(const FileDesc* files, const ChunkDesc* chunks, int nfiles, int ngroups,
                   const int32_t* group_chunk0, const int32_t* group_n, const int32_t* group_file,

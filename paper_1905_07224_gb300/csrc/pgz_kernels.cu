@@ -37,6 +37,7 @@
 //
 // No kernel waits on another block or warp; every read of the compressed
 // data, the symbol scratch and the output is bounds-checked.
+#include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -1160,24 +1161,35 @@ __device__ __forceinline__ void init_smem(WarpSmem& S, const KParams& p, int lan
 
 constexpr int kWarpsPerBlock = 4;
 
+// Work queue of the pass-1 kernels: each resident warp takes the next part
+// index until the parts run out, so parts of uneven work (many members of
+// different sizes in one launch) balance over the warps.  Parts are taken in
+// increasing order.  The counter is zeroed on the stream before each launch.
+__device__ __forceinline__ int next_part(uint32_t* queue, int lane) {
+    uint32_t c = 0;
+    if (lane == 0) c = atomicAdd(queue, 1u);
+    return (int)min(__shfl_sync(FULL, c, 0), 0x7fffffffu);
+}
+
 // ---------------------------------------------------------------------------
 // k_sync: block start of each part and its first block
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, 5)
     k_sync(const FileDesc* __restrict__ files, ChunkDesc* chunks, int nchunks, uint16_t* symbuf, uint32_t* tokbuf,
-           KParams p) {
+           uint32_t* queue, KParams p) {
     __shared__ uint16_t kraft3[512];
     for (uint32_t v = threadIdx.x; v < 512; v += blockDim.x)
         kraft3[v] = (uint16_t)(kraft1(v & 7) + kraft1((v >> 3) & 7) + kraft1(v >> 6));
     __syncthreads();
     WarpSmem& S = warp_smem();
     const int lane = threadIdx.x & 31;
-    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    uint32_t* tok = tokbuf + (uint64_t)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kTokPerPart;
+    for (;;) {
+    const int c = next_part(queue, lane);
     if (c >= nchunks) return;
     ChunkDesc& C = chunks[c];
     const FileDesc& F = files[C.file];
     init_smem(S, p, lane);
-    uint32_t* tok = tokbuf + (uint64_t)c * kTokPerPart;
     OutState o{symbuf + C.sym_base, C.cap, 0, C.index == 0 && C.lo <= F.s0_bit, false};
     BitIn br;
     br.setup(F.gz, F.gz_len);
@@ -1234,6 +1246,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 5)
         C.final = final && state == CS_FOUND;
         C.end = resume;
     }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1241,13 +1254,15 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 5)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, 5)
     k_inflate(const FileDesc* __restrict__ files, ChunkDesc* chunks, int nchunks, uint16_t* symbuf, uint32_t* tokbuf,
-              KParams p) {
+              uint32_t* queue, KParams p) {
     WarpSmem& S = warp_smem();
     const int lane = threadIdx.x & 31;
-    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    uint32_t* tok = tokbuf + (uint64_t)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kTokPerPart;
+    for (;;) {
+    const int c = next_part(queue, lane);
     if (c >= nchunks) return;
     ChunkDesc& C = chunks[c];
-    if (C.state != CS_FOUND) return;
+    if (C.state != CS_FOUND) continue;
     const FileDesc& F = files[C.file];
     // the next part that holds a block start.  `sync` is final after k_sync
     // and never written here (other warps of this kernel rewrite `state`).
@@ -1277,8 +1292,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 5)
             }
             const bool check = !o.known && blocks <= (uint32_t)p.confirm_blocks;
             uint32_t fin = 0;
-            const int st = one_block(S, tokbuf + (uint64_t)c * kTokPerPart, br, o, check, 0, 0, false, F.end_bit, fin,
-                                     lane);
+            const int st = one_block(S, tok, br, o, check, 0, 0, false, F.end_bit, fin, lane);
             if (st) {
                 err = (check && st != CE_OVERFLOW) ? (uint32_t)CE_CONFIRM : (uint32_t)st;
                 break;
@@ -1304,6 +1318,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 5)
         C.blocks = blocks;
         C.final = final;
         C.end = end;
+    }
     }
 }
 
@@ -1766,19 +1781,53 @@ __global__ void k_finalize(FileDesc* files, int nfiles) {
 static size_t warp_smem_bytes() { return sizeof(WarpSmem); }
 static_assert(kWarpsPerBlock * sizeof(WarpSmem) <= 48 * 1024, "per-block shared memory above the default limit");
 
+// resident blocks of the pass-1 kernels on the current device (both kernels
+// have the same launch bounds and shared memory)
+static int pass1_resident_blocks() {
+    static int cached[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int slot = dev >= 0 && dev < 64 ? dev : 0;
+    if (!cached[slot]) {
+        int sms = 0, per_sm_sync = 0, per_sm_inflate = 0;
+        const bool ok =
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_sync, k_sync, 32 * kWarpsPerBlock,
+                                                          kWarpsPerBlock * warp_smem_bytes()) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_inflate, k_inflate, 32 * kWarpsPerBlock,
+                                                          kWarpsPerBlock * warp_smem_bytes()) == cudaSuccess;
+        const int v = std::max(1, sms) * std::max(1, std::min(per_sm_sync, per_sm_inflate));
+        if (!ok) {
+            cudaGetLastError();
+            return v;                            // not cached: asked again once a device answers
+        }
+        cached[slot] = v;
+    }
+    return cached[slot];
+}
+
+int pass1_warps(int nchunks) {
+    if (nchunks <= 0) return 0;
+    const int blocks = std::min((nchunks + kWarpsPerBlock - 1) / kWarpsPerBlock, pass1_resident_blocks());
+    return blocks * kWarpsPerBlock;
+}
+
 void launch_sync(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, uint32_t* tok,
-                 const KParams& p, cudaStream_t s) {
+                 uint32_t* queue, const KParams& p, cudaStream_t s) {
     if (nchunks <= 0) return;
     const int wpb = kWarpsPerBlock;
-    k_sync<<<(nchunks + wpb - 1) / wpb, 32 * wpb, wpb * warp_smem_bytes(), s>>>(files, chunks, nchunks, sym, tok, p);
+    cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
+    k_sync<<<pass1_warps(nchunks) / wpb, 32 * wpb, wpb * warp_smem_bytes(), s>>>(files, chunks, nchunks, sym, tok,
+                                                                                 queue, p);
 }
 
 void launch_inflate(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, uint32_t* tok,
-                    const KParams& p, cudaStream_t s) {
+                    uint32_t* queue, const KParams& p, cudaStream_t s) {
     if (nchunks <= 0) return;
     const int wpb = kWarpsPerBlock;
-    k_inflate<<<(nchunks + wpb - 1) / wpb, 32 * wpb, wpb * warp_smem_bytes(), s>>>(files, chunks, nchunks, sym, tok,
-                                                                                   p);
+    cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
+    k_inflate<<<pass1_warps(nchunks) / wpb, 32 * wpb, wpb * warp_smem_bytes(), s>>>(files, chunks, nchunks, sym,
+                                                                                    tok, queue, p);
 }
 
 uint64_t token_words_per_part() { return kTokPerPart; }

@@ -56,7 +56,8 @@ constexpr size_t kOffWstart = a256(kOffGmaps + (size_t)kNaMaxGroups * kWin * siz
 constexpr size_t kOffSym = a256(kOffWstart + (size_t)kNaMaxGroups * kWin);
 constexpr size_t kTokWords = 32 * 512;                // token buffer of one part (parallel block decoder)
 constexpr size_t kOffTok = a256(kOffSym + kNaSymbols * sizeof(uint16_t));
-constexpr size_t kScratchBytes = a256(kOffTok + (size_t)kNaMaxParts * kTokWords * sizeof(uint32_t));   // about 23 MiB
+constexpr size_t kOffQueue = a256(kOffTok + (size_t)kNaMaxParts * kTokWords * sizeof(uint32_t));
+constexpr size_t kScratchBytes = a256(kOffQueue + 2 * sizeof(uint32_t));   // about 23 MiB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -156,7 +157,8 @@ extern "C" int pgz_decompress_noalloc(const uint8_t* gz, uint64_t gz_len, uint8_
     uint8_t* d_wstart = base + kOffWstart;
     uint16_t* d_sym = reinterpret_cast<uint16_t*>(base + kOffSym);
     uint32_t* d_tok = reinterpret_cast<uint32_t*>(base + kOffTok);
-    if (token_words_per_part() != kTokWords) return PGZ_E_ARG;
+    uint32_t* d_queue = reinterpret_cast<uint32_t*>(base + kOffQueue);
+    if (token_words_per_part() != kTokWords || pass1_warps(kNaMaxParts) > kNaMaxParts) return PGZ_E_ARG;
 
     KParams kp{};
     pgz_config cfg;
@@ -224,8 +226,8 @@ extern "C" int pgz_decompress_noalloc(const uint8_t* gz, uint64_t gz_len, uint8_
         cudaMemcpyAsync(d_gn, gn, ng * sizeof(int32_t), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(d_gfile, gfile, ng * sizeof(int32_t), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(d_seg0, &seg0, sizeof seg0, cudaMemcpyHostToDevice, s);
-        launch_sync(d_files, d_chunks, (int)n, d_sym, d_tok, kp, s);
-        launch_inflate(d_files, d_chunks, (int)n, d_sym, d_tok, kp, s);
+        launch_sync(d_files, d_chunks, (int)n, d_sym, d_tok, d_queue, kp, s);
+        launch_inflate(d_files, d_chunks, (int)n, d_sym, d_tok, d_queue + 1, kp, s);
         launch_plan(d_files, d_chunks, 1, s);
         launch_chain(d_files, d_chunks, 1, ng, d_g0, d_gn, d_gfile, d_sym, d_gmaps, d_wstart, d_windows, s);
         launch_translate(d_files, d_chunks, (int)n, plan[0].cap, d_sym, d_windows, nullptr, s);
