@@ -205,6 +205,9 @@ def run_pgz(args, rank, world):
         for k in stage:
             stage[k] += s[k] / nst
     batch_parts = s["chunks"]
+    # the translation reads the 32 KiB window of every part that holds a placeholder
+    _, _, nph_parts = pgz.pgz_inspect_parts(ctx_b)
+    window_bytes = int((nph_parts > 0).sum()) * 32768
 
     # ---- plain: one file at a time through pgz_decompress, PLAIN_PARTS equal parts per file
     ctx_p = pgz.pgz_create(pgz.pgz_config_init(device=dev, cuda_stream=stream.cuda_stream, n_chunks=PLAIN_PARTS))
@@ -269,7 +272,7 @@ def run_pgz(args, rank, world):
     pass1_ms = stage["ms_sync"] + stage["ms_inflate"]
     alg1 = total_in + 2 * total_out                  # compressed bytes read + u16 symbols written
     ach1 = alg1 / (pass1_ms * 1e-3) / 1e9
-    alg4 = 3 * total_out                             # u16 symbols read + bytes written
+    alg4 = 3 * total_out + window_bytes              # u16 symbols and windows read, bytes written
     ach4 = alg4 / (stage["ms_translate"] * 1e-3) / 1e9 if stage["ms_translate"] > 0 else None
     alg5 = total_out                                 # bytes read by the CRC
     ach5 = alg5 / (stage["ms_crc"] * 1e-3) / 1e9 if stage["ms_crc"] > 0 else None
@@ -301,7 +304,8 @@ def run_pgz(args, rank, world):
                      "peak": hbm, "unit": "GB/s", "frac": round(ach1 / hbm, 5),
                      "traffic": round(traffic1) if traffic1 else None, "peak_source": peak_src},
         "roofline_translate": {"bound": "hbm", "kernel": "k_translate", "achieved": round(ach4, 1) if ach4 else None,
-                               "peak": hbm, "unit": "GB/s", "frac": round(ach4 / hbm, 4) if ach4 else None},
+                               "peak": hbm, "unit": "GB/s", "frac": round(ach4 / hbm, 4) if ach4 else None,
+                               "bytes": alg4, "window_bytes": window_bytes},
         "roofline_crc": {"bound": "hbm", "kernel": "k_crc", "achieved": round(ach5, 1) if ach5 else None,
                          "peak": hbm, "unit": "GB/s", "frac": round(ach5 / hbm, 4) if ach5 else None},
         "e2e": {"value": round(world * total_out / (e2e_ms * 1e-3) / 1e9, 3), "unit": "GB/s",

@@ -18,7 +18,6 @@ using namespace pgz;
 
 namespace {
 
-constexpr uint64_t kSegBytes = 4096;
 constexpr uint64_t kMaxPartSymbols = (1ull << 31) - 256;   // part positions are 32-bit in the kernels
 constexpr int kMaxRetries = 32;
 
@@ -277,7 +276,7 @@ int layout(Plan& P) {
         for (int c = F.chunk0; c < F.chunk0 + F.nchunks; ++c) cap_sum += P.chunks[c].cap;
         const uint64_t bound = std::min(F.out_cap, cap_sum);
         F.seg0 = seg;
-        F.nseg = (bound + kSegBytes - 1) / kSegBytes;
+        F.nseg = (bound + crc_segment_bytes() - 1) / crc_segment_bytes();
         P.seg0.push_back(seg);
         seg += F.nseg;
     }
@@ -356,6 +355,13 @@ int read_chunks(pgz_ctx* ctx, Plan& P) {
     cudaMemcpyAsync(P.h_chunks.p, P.d_chunks.p, P.chunks.size() * sizeof(ChunkDesc), cudaMemcpyDeviceToHost,
                     ctx->stream);
     return cuda_status(cudaStreamSynchronize(ctx->stream));
+}
+
+// placeholder counts of the last run's parts (after the run; not timed), then the results
+int count_and_read_chunks(pgz_ctx* ctx, Plan& P) {
+    launch_count_ph(P.d_chunks.as<ChunkDesc>(), (int)P.chunks.size(), P.d_sym.as<uint16_t>(), ctx->stream);
+    if (cudaPeekAtLastError() != cudaSuccess) return PGZ_E_CUDA;
+    return read_chunks(ctx, P);
 }
 
 // Adjusts the plan after a failed run; returns true if a re-run may succeed.
@@ -471,7 +477,7 @@ int execute(pgz_ctx* ctx, Plan& P, pgz_stats* st) {
         for (size_t f = 0; f < P.files.size(); ++f)
             if (hf[f].bad_chunk != 0xffffffffu) need_chunks = true;
         if (need_chunks || st) {
-            e = read_chunks(ctx, P);
+            e = st ? count_and_read_chunks(ctx, P) : read_chunks(ctx, P);
             if (e) return e;
         }
         P.results_valid = true;
@@ -679,7 +685,7 @@ int pgz_decompress_at(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, uint64_t
     P.fill = ctx->fill_buf.as<uint8_t>();
     e = execute(ctx, P, nullptr);
     if (e == PGZ_OK || e == PGZ_E_CAPACITY) {
-        if (read_chunks(ctx, P)) return PGZ_E_CUDA;
+        if (count_and_read_chunks(ctx, P)) return PGZ_E_CUDA;
     }
     const ChunkDesc* res = P.h_chunks.as<ChunkDesc>();
     if (e == PGZ_OK && res[0].state != CS_DONE) e = PGZ_E_NOSYNC;
@@ -835,7 +841,7 @@ static const ChunkDesc* inspect_results(pgz_ctx* ctx) {
     Plan& P = ctx->plan;
     if (!P.results_valid || P.chunks.empty()) return nullptr;
     cudaSetDevice(ctx->cfg.device);
-    if (read_chunks(ctx, P)) return nullptr;
+    if (count_and_read_chunks(ctx, P)) return nullptr;
     return P.h_chunks.as<ChunkDesc>();
 }
 

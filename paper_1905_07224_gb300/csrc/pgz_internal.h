@@ -112,8 +112,12 @@ void launch_chain(const FileDesc* files, const ChunkDesc* chunks, int nfiles, in
                   const uint16_t* sym, uint16_t* gmaps, uint8_t* wstart, uint8_t* windows, cudaStream_t s);
 void launch_translate(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint64_t max_cap,
                       const uint16_t* sym, const uint8_t* windows, const uint8_t* fill_window, cudaStream_t s);
+// total_seg: CRC segments of crc_segment_bytes() output bytes over all members (FileDesc::seg0, nseg)
+uint64_t crc_segment_bytes();
 void launch_crc(FileDesc* files, int nfiles, uint64_t total_seg, const uint64_t* seg0, cudaStream_t s);
 void launch_finalize(FileDesc* files, int nfiles, cudaStream_t s);
+// ChunkDesc::nph and last_ph from the symbols of every finished part (statistics and inspection only)
+void launch_count_ph(ChunkDesc* chunks, int nchunks, const uint16_t* sym, cudaStream_t s);
 int kernels_per_run();
 void upload_crc_tables();
 

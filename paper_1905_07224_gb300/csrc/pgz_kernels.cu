@@ -65,10 +65,10 @@ __constant__ uint8_t c_dext[30] = {0, 0, 0, 0, 1, 1, 2, 2, 3, 3, 4, 4, 5, 5, 6, 
 // RFC 1951 3.2.7: order of the code-length code lengths
 __constant__ uint8_t c_clorder[19] = {16, 17, 18, 0, 8, 7, 9, 6, 10, 5, 11, 4, 12, 3, 13, 2, 14, 1, 15};
 // CRC-32 tables (filled by upload_crc_tables)
-__constant__ uint32_t c_crc_tab[256];   // register after one byte b from a zero register
-__constant__ uint32_t c_x2k[64];        // x^(2^k) mod P
-__constant__ uint32_t c_lane_shift[32]; // x^(8*128*k) mod P
-__constant__ uint32_t c_x4096;          // x^(8*4096) mod P
+__constant__ uint32_t c_crc_tab[4][256];   // [0][b]: register after byte b from a zero register; [k]: k more zero bytes
+__constant__ uint32_t c_x2k[64];           // x^(2^k) mod P
+__constant__ uint32_t c_lane_shift[32];    // x^(8*kPiece*k) mod P
+__constant__ uint32_t c_xseg;              // x^(8*kCrcSeg) mod P
 
 // literal/length lookup entry: bits 0-4 bits to drop, 8-16 value, 17-19
 // extra-bit count (K_LENX), 28-31 kind.  K_LEN carries the exact length
@@ -1506,150 +1506,191 @@ __global__ void __launch_bounds__(1024) k_chain_expand(const FileDesc* __restric
 // ---------------------------------------------------------------------------
 
 // Persistent: block b translates parts b, b + gridDim.x, ...; the part's
-// window w_i is loaded once into shared memory (only if the part produced a
-// placeholder).  A thread turns 8 symbols (one 16-byte load) into 8 bytes:
-// without a placeholder two byte permutations pack them, otherwise each
-// placeholder is looked up in the window.  Four loads per thread in flight.
+// window w_i is copied into shared memory (only if the part produced a
+// placeholder) while the block's previous part is translated (two tables).  The shared table is the window followed by the 256 byte
+// values, so a symbol s (a byte b < 0x100, or 0x8000 | j for U_j) becomes
+// T[s ^ 0x8000]: window byte j for a placeholder, b for a byte, with no
+// branch.  Parts without any placeholder pack their bytes with byte
+// permutations.
+//
+// A warp writes a contiguous run of slices of 512 symbols, a lane 16
+// symbols (two 16-byte loads) of each; the loads of the next slice are in
+// flight while a slice is translated.
+// Output bytes P..P+15 of a lane (P = out_off + symbol index) go out as the
+// two aligned 8-byte words from P - m (m = out_off mod 8); the m bytes before
+// P come from the previous lane (lane 31's from the previous slice), the m
+// bytes after P + 15 - m are the next lane's first word.  Partial slices and
+// the first slice of a warp's run take byte stores where a neighbour is
+// missing.
 constexpr int kTransThreads = 512;
+constexpr uint32_t kTransSlice = 512;                  // symbols per slice (16 per lane)
+constexpr size_t kTransSmem = 2 * (kWin + 256);         // two window tables
 
-__global__ void __launch_bounds__(kTransThreads) k_translate(const FileDesc* __restrict__ files, ChunkDesc* chunks,
-                                                             int nchunks, const uint16_t* __restrict__ sym,
-                                                             const uint8_t* __restrict__ windows,
-                                                             const uint8_t* __restrict__ fillw) {
-    __shared__ __align__(16) uint8_t W[kWin];
-    __shared__ unsigned long long s_nph, s_last;
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// 8 symbols -> 8 bytes (symbols past nv are taken as byte 0)
+__device__ __forceinline__ uint64_t translate8(const uint8_t* T, uint4 q, uint32_t nv, bool ph) {
+    uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+    if (nv < 8) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (2u * k >= nv) w4[k] = 0;
+            else if (2u * k + 1 >= nv) w4[k] &= 0xffffu;
+        }
+    }
+    uint32_t b0, b1;
+    if (!ph) {
+        b0 = __byte_perm(w4[0], w4[1], 0x6420);
+        b1 = __byte_perm(w4[2], w4[3], 0x6420);
+    } else {
+        uint32_t pr[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t w = w4[k] ^ 0x80008000u;
+            pr[k] = (uint32_t)T[w & 0xffffu] | ((uint32_t)T[w >> 16] << 8);
+        }
+        b0 = __byte_perm(pr[0], pr[1], 0x5410);
+        b1 = __byte_perm(pr[2], pr[3], 0x5410);
+    }
+    return (uint64_t)b0 | ((uint64_t)b1 << 32);
+}
+
+__global__ void __launch_bounds__(kTransThreads, 2) k_translate(const FileDesc* __restrict__ files, ChunkDesc* chunks,
+                                                                int nchunks, const uint16_t* __restrict__ sym,
+                                                                const uint8_t* __restrict__ windows,
+                                                                const uint8_t* __restrict__ fillw) {
+    extern __shared__ __align__(16) uint8_t Wbuf[];      // two tables of kWin + 256 bytes (kTransSmem)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        ChunkDesc& C = chunks[c];
+    if (threadIdx.x < 256) {
+        Wbuf[kWin + threadIdx.x] = (uint8_t)threadIdx.x;
+        Wbuf[2 * kWin + 256 + threadIdx.x] = (uint8_t)threadIdx.x;
+    }
+    // the window of part c goes into table `buf` by asynchronous copies, one group per part
+    auto fetch = [&](int c, int buf) {
+        if (c < nchunks) {
+            const ChunkDesc& C = chunks[c];
+            if (files[C.file].status == PGZ_OK && C.state == CS_DONE && C.n != 0 && C.anyph) {
+                const uint8_t* src = fillw ? fillw : windows + (uint64_t)c * kWin;
+                const uint32_t dst = smem_u32(Wbuf + buf * (kWin + 256));
+                for (uint32_t k = threadIdx.x; k < kWin / 16; k += blockDim.x) cp_async16(dst + 16 * k, src + 16 * k);
+            }
+        }
+        cp_async_commit();
+    };
+    fetch(blockIdx.x, 0);
+    int buf = 0;
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x, buf ^= 1) {
+        fetch(c + gridDim.x, buf ^ 1);                    // the next part's window, while this part runs
+        cp_async_wait<1>();                               // this part's window (this thread's copies) ...
+        __syncthreads();                                  // ... and everyone else's
+        const uint8_t* W = Wbuf + buf * (kWin + 256);
+        const ChunkDesc& C = chunks[c];
         const FileDesc& F = files[C.file];
-        if (F.status != PGZ_OK || C.state != CS_DONE || C.n == 0) continue;   // uniform per block
-        const uint64_t t1 = C.n;
         const bool ph = C.anyph != 0;
-        __syncthreads();                                  // the previous part's window is no longer read
-        if (threadIdx.x == 0) {
-            s_nph = 0;
-            s_last = 0;
-        }
-        if (ph) {
-            const uint4* src = reinterpret_cast<const uint4*>(fillw ? fillw : windows + (uint64_t)c * kWin);
-            for (uint32_t k = threadIdx.x; k < kWin / 16; k += blockDim.x) reinterpret_cast<uint4*>(W)[k] = src[k];
-        }
-        __syncthreads();
+        if (F.status == PGZ_OK && C.state == CS_DONE && C.n != 0) {   // uniform per block
         const uint16_t* s = sym + C.sym_base;
         // output byte P of the member goes to out[P - out_lo] when out_lo <= P < out_hi
         uint8_t* out = F.out;
         const uint64_t lo = F.out_lo, hi = F.out_hi;
         const bool vec = F.out_lo == 0 && F.out_hi == kNone && ((reinterpret_cast<uintptr_t>(out) & 7) == 0);
-        const uint32_t m = (uint32_t)(C.out_off & 7);
-        uint32_t nph = 0, last = 0, last_i = 0xffffffffu, last_w[4] = {0, 0, 0, 0};
-        constexpr int U = 4;
-        // warp `warp` writes the contiguous slices [ws, we) of 256 symbols; lane 31's bytes of a
-        // slice are carried to lane 0 of the next, so every word inside the range is one 8-byte store
-        const uint32_t n32 = (uint32_t)t1;
-        const uint32_t nsl = (n32 + 255) / 256, per = (nsl + nwarp - 1) / nwarp;
-        const uint32_t ws = min(nsl, per * (uint32_t)warp) * 256u, we = min(nsl, per * (uint32_t)(warp + 1)) * 256u;
-        uint64_t carry = 0;
-        uint32_t carry_nv = 0;                            // valid symbols of the carried lane (0: none)
-        for (uint32_t wb = ws; wb < we; wb += 256u * U) {
-            uint4 qv[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const uint32_t i = wb + 256u * u + 8u * (uint32_t)lane;
-                qv[u] = (i < n32 && i < we) ? *reinterpret_cast<const uint4*>(s + i) : make_uint4(0, 0, 0, 0);
+        const uint32_t m = (uint32_t)(C.out_off & 7), sh = 8u * m;
+        const uint32_t n32 = (uint32_t)C.n;
+        const uint32_t nsl = (n32 + kTransSlice - 1) / kTransSlice, per = (nsl + nwarp - 1) / nwarp;
+        const uint32_t j0 = min(nsl, per * (uint32_t)warp), j1 = min(nsl, per * (uint32_t)(warp + 1));
+        // loads of slice j + 1 are in flight while slice j is translated
+        auto load = [&](uint32_t j, uint4& a, uint4& b) {
+            const uint32_t i = j * kTransSlice + 16u * (uint32_t)lane;
+            a = (j < j1 && i < n32) ? *reinterpret_cast<const uint4*>(s + i) : make_uint4(0, 0, 0, 0);
+            b = (j < j1 && i + 8 < n32) ? *reinterpret_cast<const uint4*>(s + i + 8) : make_uint4(0, 0, 0, 0);
+        };
+        uint4 n0, n1;
+        load(j0, n0, n1);
+        uint64_t carry = 0;                               // lane 31's second word of the previous slice
+        for (uint32_t j = j0; j < j1; ++j) {
+            const uint4 q0 = n0, q1 = n1;
+            load(j + 1, n0, n1);
+            const uint32_t i = j * kTransSlice + 16u * (uint32_t)lane;
+            const bool full = (j + 1) * kTransSlice <= n32;   // uniform: every lane holds 16 symbols
+            const uint32_t nv = full ? 16u : (i < n32 ? min(n32 - i, 16u) : 0u);
+            const uint64_t v0 = translate8(W, q0, nv < 8 ? nv : 8u, ph);
+            const uint64_t v1 = translate8(W, q1, nv > 8 ? nv - 8 : 0u, ph);
+            const uint64_t P = C.out_off + i;
+            if (!vec || !full) {          // each lane stores its own bytes (clipped to [lo, hi) when !vec)
+                for (uint32_t k = 0; k < nv; ++k) {
+                    const uint64_t q = P + k;
+                    if (q >= lo && q < hi) out[q - lo] = (uint8_t)((k < 8 ? v0 : v1) >> (8 * (k & 7)));
+                }
+                continue;
             }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const uint32_t sb = wb + 256u * u;
-                if (sb >= we) break;                      // uniform
-                const uint32_t i = sb + 8u * (uint32_t)lane;
-                const uint32_t nv = i < n32 ? min(n32 - i, 8u) : 0u;
-                uint32_t w4[4] = {qv[u].x, qv[u].y, qv[u].z, qv[u].w};
-                if (nv < 8) {                                 // symbols past the part's end are bytes 0
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        if (2u * k >= nv) w4[k] = 0;
-                        else if (2u * k + 1 >= nv) w4[k] &= 0xffffu;
-                    }
-                }
-                const uint32_t anyp = (w4[0] | w4[1] | w4[2] | w4[3]) & 0x80008000u;
-                uint32_t b0, b1;
-                if (!anyp) {
-                    b0 = __byte_perm(w4[0], w4[1], 0x6420);
-                    b1 = __byte_perm(w4[2], w4[3], 0x6420);
-                } else {
-                    uint32_t pr[4];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const uint32_t w = w4[k];
-                        const uint32_t lo = (w & 0x8000u) ? (uint32_t)W[w & 0x7fffu] : (w & 0xffu);
-                        const uint32_t hi = (w & 0x80000000u) ? (uint32_t)W[(w >> 16) & 0x7fffu] : ((w >> 16) & 0xffu);
-                        pr[k] = lo | (hi << 8);
-                        nph += __popc(w & 0x80008000u);
-                    }
-                    b0 = __byte_perm(pr[0], pr[1], 0x5410);
-                    b1 = __byte_perm(pr[2], pr[3], 0x5410);
-                    last_i = i;                               // the exact position is worked out once, at the end
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) last_w[k] = w4[k];
-                }
-                const uint64_t val = (uint64_t)b0 | ((uint64_t)b1 << 32);
-                const uint64_t P = C.out_off + i;
-                if (!vec) {                               // byte stores, clipped to [lo, hi)
-                    for (uint32_t k = 0; k < nv; ++k)
-                        if (P + k >= lo && P + k < hi) out[P + k - lo] = (uint8_t)(val >> (8 * k));
-                    continue;
-                }
-                if (m == 0) {
-                    if (nv == 8) *reinterpret_cast<uint64_t*>(out + P) = val;
-                    else
-                        for (uint32_t k = 0; k < nv; ++k) out[P + k] = (uint8_t)(val >> (8 * k));
-                    continue;
-                }
-                // the previous lane holds 8 symbols whenever this one holds any; lane 0's
-                // predecessor is the previous slice's lane 31 (carried)
-                uint64_t prev = __shfl_up_sync(FULL, val, 1);
-                uint32_t prev_nv = 8;
-                if (lane == 0) {
-                    prev = carry;
-                    prev_nv = carry_nv;
-                }
-                carry = shfl64(val, 31);
-                carry_nv = sb + 248u < n32 ? min(n32 - (sb + 248u), 8u) : 0u;
-                const uint32_t next_nv = i + 8u < n32 ? min(n32 - (i + 8u), 8u) : 0u;
-                const uint32_t head = 8 - m;              // my bytes in the aligned word at P - m
-                if (prev_nv == 8 && nv >= head) {
-                    *reinterpret_cast<uint64_t*>(out + P - m) = (val << (8 * m)) | (prev >> (64 - 8 * m));
-                } else {
-                    for (uint32_t k = 0; k < nv && k < head; ++k) out[P + k] = (uint8_t)(val >> (8 * k));
-                }
-                // lane 31: the next slice's lane 0 takes the tail only inside this warp's range
-                const uint32_t nx = sb + 256u;
-                const uint32_t next0_nv = (nx < we && nx < n32) ? min(n32 - nx, 8u) : 0u;
-                const bool tail_by_next = nv == 8 && (lane < 31 ? next_nv >= head : next0_nv >= head);
-                if (!tail_by_next)
-                    for (uint32_t k = head; k < nv; ++k) out[P + k] = (uint8_t)(val >> (8 * k));
+            if (m == 0) {
+                *reinterpret_cast<uint64_t*>(out + P) = v0;
+                *reinterpret_cast<uint64_t*>(out + P + 8) = v1;
+                continue;
+            }
+            uint64_t prev = __shfl_up_sync(FULL, v1, 1);
+            if (lane == 0) prev = carry;
+            carry = shfl64(v1, 31);
+            const bool have_prev = lane > 0 || j > j0;    // the previous slice of this run was full
+            if (have_prev) {
+                *reinterpret_cast<uint64_t*>(out + P - m) = (v0 << sh) | (prev >> (64 - sh));
+            } else {
+                for (uint32_t k = 0; k < 8 - m; ++k) out[P + k] = (uint8_t)(v0 >> (8 * k));
+            }
+            *reinterpret_cast<uint64_t*>(out + P + 8 - m) = (v1 << sh) | (v0 >> (64 - sh));
+            // my last m bytes start the next lane's first word; lane 31 writes them itself unless
+            // the next slice is full and in this run
+            if (lane == 31) {
+                const bool next_full = j + 1 < j1 && (j + 2) * kTransSlice <= n32;
+                if (!next_full)
+                    for (uint32_t k = 16 - m; k < 16; ++k) out[P + k] = (uint8_t)(v1 >> (8 * (k - 8)));
             }
         }
-        if (ph) {                                         // placeholder count and extent of the part
-            if (last_i != 0xffffffffu) {                  // one past the last placeholder of the last slice that had one
-                const uint32_t fl = ((last_w[0] >> 15) & 1u) | ((last_w[0] >> 30) & 2u) | ((last_w[1] >> 13) & 4u) |
-                                    ((last_w[1] >> 28) & 8u) | ((last_w[2] >> 11) & 16u) | ((last_w[2] >> 26) & 32u) |
-                                    ((last_w[3] >> 9) & 64u) | ((last_w[3] >> 24) & 128u);
-                last = last_i + (32u - __clz(fl));
+        }
+        __syncthreads();                                  // table `buf` is refilled two parts later
+    }
+    cp_async_wait<0>();
+}
+
+// placeholder count of every part and one past its last placeholder (for
+// statistics and inspection; not on the decompression path)
+__global__ void __launch_bounds__(256) k_count_ph(ChunkDesc* chunks, int nchunks, const uint16_t* __restrict__ sym) {
+    __shared__ unsigned long long s_n, s_last;
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        ChunkDesc& C = chunks[c];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_n = 0;
+            s_last = 0;
+        }
+        __syncthreads();
+        const uint64_t n = C.state == CS_DONE ? C.n : 0;
+        const uint16_t* p = sym + C.sym_base;
+        unsigned long long cnt = 0, last = 0;
+        for (uint64_t i = threadIdx.x; i < n; i += blockDim.x)
+            if (p[i] & kPH) {
+                ++cnt;
+                last = i + 1;
             }
-            for (int d = 16; d; d >>= 1) {
-                nph += __shfl_xor_sync(FULL, nph, d);
-                last = max(last, __shfl_xor_sync(FULL, last, d));
-            }
-            if (lane == 0) {
-                atomicAdd(&s_nph, (unsigned long long)nph);
-                atomicMax(&s_last, (unsigned long long)last);
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                C.nph = s_nph;
-                C.last_ph = s_last;
-            }
+        for (int d = 16; d; d >>= 1) {
+            cnt += __shfl_xor_sync(FULL, cnt, d);
+            last = max(last, __shfl_xor_sync(FULL, last, d));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&s_n, cnt);
+            atomicMax(&s_last, last);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            C.nph = s_n;
+            C.last_ph = s_last;
         }
     }
 }
@@ -1675,50 +1716,70 @@ __device__ uint32_t xpow8(uint64_t n) {       // x^(8n) mod P
     return r;
 }
 
-constexpr uint32_t kCrcSeg = 4096;    // bytes per warp step
-constexpr uint32_t kPiece = 128;      // bytes per lane
+constexpr uint32_t kCrcSeg = 8192;    // bytes per warp step
+constexpr uint32_t kPiece = 256;      // bytes per lane (kCrcSeg / 32)
+constexpr int kCrcThreads = 1024;     // one block per SM
+constexpr size_t kCrcSmem = 4 * 256 * 32 * sizeof(uint32_t);   // 128 KiB: four tables, one copy per lane
 
-// raw CRC register (zero start) of a 128-byte piece, a byte per step, from a
-// table replicated once per lane (entry b of lane l at word 32*b + l: every
-// lane reads its own bank)
-__device__ __forceinline__ uint32_t crc_bytes(const uint32_t* T, int lane, const uint8_t* p, uint64_t n) {
+// Slicing by four (four table lookups per 32-bit word, RFC 1952 CRC in the
+// reflected form): with x = r ^ w, the register after the word's four bytes
+// is T3[x0] ^ T2[x1] ^ T1[x2] ^ T0[x3], where Tk is the byte table followed
+// by k zero bytes.  Each lane reads its own copy of the tables (entry b of
+// table k of lane l at word 32 * (256 k + b) + l), so the lookups of a warp
+// never share a bank.
+__device__ __forceinline__ uint32_t crc_word(const uint32_t* Tl, uint32_t r, uint32_t w) {
+    const uint32_t x = r ^ w;
+    return Tl[32u * (768u + (x & 0xffu))] ^ Tl[32u * (512u + ((x >> 8) & 0xffu))] ^
+           Tl[32u * (256u + ((x >> 16) & 0xffu))] ^ Tl[32u * (x >> 24)];
+}
+
+// raw CRC register (zero start) of n bytes at p; Tl is the lane's table copy
+__device__ __forceinline__ uint32_t crc_bytes(const uint32_t* Tl, const uint8_t* p, uint64_t n) {
     uint32_t r = 0;
     if (n == kPiece && ((reinterpret_cast<uintptr_t>(p) & 15) == 0)) {
         const uint4* v = reinterpret_cast<const uint4*>(p);
-        uint4 x[8];                                       // the whole piece in flight first
+        constexpr int H = kPiece / 32;                    // 16-byte loads per half piece
+        uint4 x[H];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) x[q] = v[q];
+        for (int q = 0; q < H; ++q) x[q] = v[q];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const uint32_t w4[4] = {x[q].x, x[q].y, x[q].z, x[q].w};
+        for (int h = 0; h < 2; ++h) {
+            uint4 y[H];
+            if (h == 0) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                uint32_t wv = w4[j];
+                for (int q = 0; q < H; ++q) y[q] = v[H + q];   // the second half in flight meanwhile
+            }
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    r = T[32u * ((r ^ wv) & 0xffu) + lane] ^ (r >> 8);
-                    wv >>= 8;
-                }
+            for (int q = 0; q < H; ++q) {
+                r = crc_word(Tl, r, x[q].x);
+                r = crc_word(Tl, r, x[q].y);
+                r = crc_word(Tl, r, x[q].z);
+                r = crc_word(Tl, r, x[q].w);
+            }
+            if (h == 0) {
+#pragma unroll
+                for (int q = 0; q < H; ++q) x[q] = y[q];
             }
         }
     } else {
-        for (uint64_t i = 0; i < n; ++i) r = T[32u * ((r ^ p[i]) & 0xffu) + lane] ^ (r >> 8);
+        for (uint64_t i = 0; i < n; ++i) r = Tl[32u * ((r ^ p[i]) & 0xffu)] ^ (r >> 8);
     }
     return r;
 }
 
-// Each warp takes a contiguous run of 4 KiB segments: the 32 lanes' pieces
-// of a segment are combined by their shift to the segment end, segments are
+// Each warp takes a contiguous run of segments: the 32 lanes' pieces of a
+// segment are combined by their shift to the segment end, segments are
 // folded in order (R(A||B) = R(A) x^(8|B|) + R(B)), and a run is shifted to
 // the end of its member once and XOR-accumulated there.
-__global__ void __launch_bounds__(256) k_crc(FileDesc* files, int nfiles, uint64_t total_seg, const uint64_t* seg0,
-                                             uint64_t segs_per_warp) {
-    __shared__ uint32_t T[256 * 32];
+__global__ void __launch_bounds__(kCrcThreads, 1) k_crc(FileDesc* files, int nfiles, uint64_t total_seg,
+                                                        const uint64_t* seg0, uint64_t segs_per_warp) {
+    extern __shared__ uint32_t T[];                       // 4 x 256 x 32 words
     __shared__ uint32_t LS[32];
-    for (int k = threadIdx.x; k < 256 * 32; k += blockDim.x) T[k] = c_crc_tab[k >> 5];
+    for (int k = threadIdx.x; k < 4 * 256 * 32; k += blockDim.x) T[k] = c_crc_tab[k >> 13][(k >> 5) & 255];
     if (threadIdx.x < 32) LS[threadIdx.x] = c_lane_shift[threadIdx.x];
     __syncthreads();
     const int lane = threadIdx.x & 31;
+    const uint32_t* Tl = T + lane;
     const uint64_t w = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const uint64_t s_begin = w * segs_per_warp;
     if (s_begin >= total_seg) return;
@@ -1752,11 +1813,11 @@ __global__ void __launch_bounds__(256) k_crc(FileDesc* files, int nfiles, uint64
         const uint64_t pb = pa + kPiece < se ? pa + kPiece : se;
         uint32_t r = 0;
         if (pa < pb) {
-            r = crc_bytes(T, lane, F.out + pa, pb - pa);
+            r = crc_bytes(Tl, F.out + pa, pb - pa);
             r = (se - a == kCrcSeg) ? gf2_mul(r, LS[31 - lane]) : gf2_mul(r, xpow8(se - pb));
         }
         for (int d = 16; d; d >>= 1) r ^= __shfl_xor_sync(FULL, r, d);
-        acc = (run_end == 0 ? 0u : gf2_mul(acc, se - a == kCrcSeg ? c_x4096 : xpow8(se - a))) ^ r;
+        acc = (run_end == 0 ? 0u : gf2_mul(acc, se - a == kCrcSeg ? c_xseg : xpow8(se - a))) ^ r;
         run_end = se;
     }
     flush();
@@ -1857,16 +1918,50 @@ void launch_translate(const FileDesc* files, ChunkDesc* chunks, int nchunks, uin
                       const uint16_t* sym, const uint8_t* windows, const uint8_t* fillw, cudaStream_t s) {
     if (nchunks <= 0) return;
     (void)max_cap;
-    const int grid = nchunks < 152 * 4 ? nchunks : 152 * 4;
-    k_translate<<<grid, kTransThreads, 0, s>>>(files, chunks, nchunks, sym, windows, fillw);
+    static int resident[64] = {};                         // blocks of k_translate that fit on the device at once
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int slot = dev >= 0 && dev < 64 ? dev : 0;
+    if (!resident[slot]) {
+        int sms = 0, per_sm = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            cudaFuncSetAttribute(k_translate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTransSmem) ==
+                cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_translate, kTransThreads, kTransSmem) == cudaSuccess &&
+            sms > 0 && per_sm > 0)
+            resident[slot] = sms * per_sm;
+        else
+            cudaGetLastError();
+    }
+    const int cap = resident[slot] ? resident[slot] : 152 * 2;
+    const int grid = nchunks < cap ? nchunks : cap;
+    k_translate<<<grid, kTransThreads, kTransSmem, s>>>(files, chunks, nchunks, sym, windows, fillw);
+}
+
+uint64_t crc_segment_bytes() { return kCrcSeg; }
+
+void launch_count_ph(ChunkDesc* chunks, int nchunks, const uint16_t* sym, cudaStream_t s) {
+    if (nchunks <= 0) return;
+    k_count_ph<<<nchunks < 1216 ? nchunks : 1216, 256, 0, s>>>(chunks, nchunks, sym);
 }
 
 void launch_crc(FileDesc* files, int nfiles, uint64_t total_seg, const uint64_t* seg0, cudaStream_t s) {
     if (nfiles <= 0 || total_seg == 0) return;
-    const uint64_t target = 152ull * 56;                  // warps (7 blocks of 8 warps per SM)
+    static int sms[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int slot = dev >= 0 && dev < 64 ? dev : 0;
+    if (!sms[slot]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0) sms[slot] = n;
+        else cudaGetLastError();
+        cudaFuncSetAttribute(k_crc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCrcSmem);
+    }
+    const uint64_t wpb = kCrcThreads / 32;
+    const uint64_t target = (uint64_t)(sms[slot] ? sms[slot] : 152) * wpb;   // one block per SM
     const uint64_t spw = (total_seg + target - 1) / target;
     const uint64_t warps = (total_seg + spw - 1) / spw;
-    k_crc<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(files, nfiles, total_seg, seg0, spw);
+    k_crc<<<(unsigned)((warps + wpb - 1) / wpb), kCrcThreads, kCrcSmem, s>>>(files, nfiles, total_seg, seg0, spw);
 }
 
 void launch_finalize(FileDesc* files, int nfiles, cudaStream_t s) {
@@ -1887,31 +1982,33 @@ static uint32_t h_mul(uint32_t a, uint32_t b) {
 }
 
 void upload_crc_tables() {
-    uint32_t tab[256], x2k[64], ls[32];
+    uint32_t tab[4][256], x2k[64], ls[32];
     for (uint32_t b = 0; b < 256; ++b) {
         uint32_t r = b;
         for (int k = 0; k < 8; ++k) r = (r & 1u) ? (r >> 1) ^ kPoly : (r >> 1);
-        tab[b] = r;
+        tab[0][b] = r;
     }
+    for (int k = 1; k < 4; ++k)                // k further zero bytes
+        for (uint32_t b = 0; b < 256; ++b) tab[k][b] = (tab[k - 1][b] >> 8) ^ tab[0][tab[k - 1][b] & 0xffu];
     x2k[0] = 0x40000000u;                      // x
     for (int k = 1; k < 64; ++k) x2k[k] = h_mul(x2k[k - 1], x2k[k - 1]);
-    for (int l = 0; l < 32; ++l) {             // x^(8*128*l)
+    for (int l = 0; l < 32; ++l) {             // x^(8*kPiece*l)
         uint64_t e = 8ull * kPiece * (uint64_t)l;
         uint32_t r = 0x80000000u;
         for (int k = 0; e; ++k, e >>= 1)
             if (e & 1) r = h_mul(r, x2k[k]);
         ls[l] = r;
     }
-    uint32_t x4096 = 0x80000000u;
+    uint32_t xseg = 0x80000000u;
     {
-        uint64_t e = 8ull * 4096;
+        uint64_t e = 8ull * kCrcSeg;
         for (int k = 0; e; ++k, e >>= 1)
-            if (e & 1) x4096 = h_mul(x4096, x2k[k]);
+            if (e & 1) xseg = h_mul(xseg, x2k[k]);
     }
     cudaMemcpyToSymbol(c_crc_tab, tab, sizeof tab);
     cudaMemcpyToSymbol(c_x2k, x2k, sizeof x2k);
     cudaMemcpyToSymbol(c_lane_shift, ls, sizeof ls);
-    cudaMemcpyToSymbol(c_x4096, &x4096, sizeof x4096);
+    cudaMemcpyToSymbol(c_xseg, &xseg, sizeof xseg);
 }
 
 }  // namespace pgz

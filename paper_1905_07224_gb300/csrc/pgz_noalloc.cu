@@ -216,7 +216,8 @@ extern "C" int pgz_decompress_noalloc(const uint8_t* gz, uint64_t gz_len, uint8_
         F.group0 = 0;
         F.ngroups = ng;
         F.seg0 = 0;
-        F.nseg = ((out_cap < (uint64_t)kNaMaxOut ? out_cap : (uint64_t)kNaMaxOut) + 4095) / 4096;
+        F.nseg = ((out_cap < (uint64_t)kNaMaxOut ? out_cap : (uint64_t)kNaMaxOut) + crc_segment_bytes() - 1) /
+                 crc_segment_bytes();
         F.out_hi = kNone;
         F.bad_chunk = 0xffffffffu;
         const uint64_t seg0 = 0;
