@@ -123,6 +123,7 @@ struct Plan {
     uint64_t sym_total = 0, max_cap = 0, total_seg = 0;
     bool chain = true, translate = true, crc = true;
     bool results_valid = false;   // the device chunk array holds the last run's results
+    int wpb = 4;                  // warps per block of the pass-1 kernels (sizes the token scratch)
     const uint8_t* fill = nullptr;   // device window of fill bytes (mode 1)
     DBuf d_files, d_chunks, d_g0, d_gn, d_gfile, d_seg0, d_sym, d_windows, d_gmaps, d_wstart, d_tok, d_queue;
     PBuf h_files, h_chunks;
@@ -290,7 +291,7 @@ int layout(Plan& P) {
     if (!e) e = P.d_gfile.ensure(ng * sizeof(int32_t));
     if (!e) e = P.d_seg0.ensure(nf * sizeof(uint64_t));
     if (!e) e = P.d_sym.ensure(P.sym_total * sizeof(uint16_t));
-    if (!e) e = P.d_tok.ensure((size_t)pass1_warps((int)nc) * token_words_per_part() * sizeof(uint32_t));
+    if (!e) e = P.d_tok.ensure((size_t)pass1_warps((int)nc, P.wpb) * token_words_per_part() * sizeof(uint32_t));
     if (!e) e = P.d_queue.ensure(2 * sizeof(uint32_t));
     if (!e && P.chain) e = P.d_windows.ensure(nc * (size_t)kWin);
     if (!e && P.chain) e = P.d_gmaps.ensure(ng * (size_t)kWin * sizeof(uint16_t));
@@ -462,6 +463,7 @@ int execute(pgz_ctx* ctx, Plan& P, pgz_stats* st) {
     uint64_t retries = 0, false_syncs = 0;
     const bool timed = st != nullptr;
     int status = PGZ_OK;
+    P.wpb = ctx->kp.wpb;
     for (;;) {
         reset_results(P);
         int e = layout(P);
@@ -550,12 +552,16 @@ void pgz_config_init(pgz_config* cfg) {
     cfg->max_block = 4u << 20;
     cfg->dev_mem_budget = 0;
     cfg->spin_cap = 0;
+    cfg->warps_per_block = 4;
 }
 
 int pgz_create(pgz_ctx** out, const pgz_config* cfg) {
     if (!out || !cfg) return PGZ_E_ARG;
     *out = nullptr;
     if (cfg->threads_per_chunk != 32 || cfg->confirm_blocks < 0 || (cfg->n_chunks <= 0 && cfg->chunk_bytes == 0))
+        return PGZ_E_ARG;
+    if (cfg->warps_per_block != 0 && cfg->warps_per_block != 2 && cfg->warps_per_block != 4 &&
+        cfg->warps_per_block != 8)
         return PGZ_E_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) return PGZ_E_CUDA;
@@ -570,6 +576,7 @@ int pgz_create(pgz_ctx** out, const pgz_config* cfg) {
     ctx->kp.min_block = cfg->min_block;
     ctx->kp.max_block = cfg->max_block;
     ctx->kp.confirm_blocks = cfg->confirm_blocks;
+    ctx->kp.wpb = cfg->warps_per_block ? cfg->warps_per_block : 4;
     upload_crc_tables();
     for (int k = 0; k < 8; ++k) cudaEventCreate(&ctx->ev[k]);
     if (cudaGetLastError() != cudaSuccess) {
@@ -1010,6 +1017,60 @@ void pgz_index_free(pgz_index* idx) {
     if (!idx) return;
     idx->windows.release();
     delete idx;
+}
+
+int pgz_autotune(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, uint8_t* out, uint64_t out_cap,
+                 const uint64_t* chunk_bytes, int n_chunk_bytes, const int* warps_per_block, int n_wpb, int reps,
+                 pgz_tune_entry* entries, pgz_tune_entry* best) {
+    if (!ctx || !chunk_bytes || !warps_per_block || n_chunk_bytes <= 0 || n_wpb <= 0 || reps < 1) return PGZ_E_ARG;
+    for (int a = 0; a < n_chunk_bytes; ++a)
+        if (chunk_bytes[a] < 4096) return PGZ_E_ARG;
+    for (int b = 0; b < n_wpb; ++b)
+        if (warps_per_block[b] != 2 && warps_per_block[b] != 4 && warps_per_block[b] != 8) return PGZ_E_ARG;
+    cudaSetDevice(ctx->cfg.device);
+    const pgz_config saved = ctx->cfg;
+    const int saved_wpb = ctx->kp.wpb;
+    pgz_tune_entry pick{};
+    pick.status = PGZ_E_ARG;
+    int first_bad = PGZ_OK;
+    std::vector<float> t((size_t)reps);
+    for (int a = 0; a < n_chunk_bytes; ++a) {
+        for (int b = 0; b < n_wpb; ++b) {
+            pgz_tune_entry e{};
+            e.chunk_bytes = chunk_bytes[a];
+            e.warps_per_block = warps_per_block[b];
+            ctx->cfg.n_chunks = 0;
+            ctx->cfg.chunk_bytes = e.chunk_bytes;
+            ctx->cfg.warps_per_block = e.warps_per_block;
+            ctx->kp.wpb = e.warps_per_block;
+            uint64_t n = 0;
+            e.status = pgz_decompress(ctx, gz, gz_len, out, out_cap, &n, nullptr);   // settles buffers and plan
+            for (int r = 0; r < reps && e.status == PGZ_OK; ++r) {
+                cudaEventRecord(ctx->ev[6], ctx->stream);
+                e.status = pgz_decompress(ctx, gz, gz_len, out, out_cap, &n, nullptr);
+                cudaEventRecord(ctx->ev[7], ctx->stream);
+                if (cudaEventSynchronize(ctx->ev[7]) != cudaSuccess) e.status = PGZ_E_CUDA;
+                else cudaEventElapsedTime(&t[(size_t)r], ctx->ev[6], ctx->ev[7]);
+            }
+            if (e.status == PGZ_OK) {
+                std::sort(t.begin(), t.end());
+                e.ms = t[(size_t)reps / 2];
+                if (pick.status != PGZ_OK || e.ms < pick.ms) pick = e;
+            } else if (first_bad == PGZ_OK) {
+                first_bad = e.status;
+            }
+            if (entries) entries[(size_t)a * n_wpb + b] = e;
+        }
+    }
+    ctx->cfg = saved;
+    ctx->kp.wpb = saved_wpb;
+    if (pick.status != PGZ_OK) return first_bad;
+    ctx->cfg.n_chunks = 0;
+    ctx->cfg.chunk_bytes = pick.chunk_bytes;
+    ctx->cfg.warps_per_block = pick.warps_per_block;
+    ctx->kp.wpb = pick.warps_per_block;
+    if (best) *best = pick;
+    return PGZ_OK;
 }
 
 const char* pgz_strerror(int status) {

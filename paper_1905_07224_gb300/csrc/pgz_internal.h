@@ -39,7 +39,7 @@ struct KParams {
     uint32_t min_block;
     uint32_t max_block;
     int confirm_blocks;
-    int pad;
+    int wpb;               // warps per block of the pass-1 kernels: 2, 4 or 8 (0: 4)
 };
 
 // one gzip member
@@ -98,14 +98,14 @@ struct ChunkDesc {
 
 // host-side launch wrappers (pgz_kernels.cu)
 // tok: token_words_per_part() u32 of parallel-block-decoder scratch for each of
-//      pass1_warps(nchunks) warps (at most nchunks rounded up to 4);
+//      pass1_warps(nchunks, p.wpb) warps (at most nchunks rounded up to p.wpb);
 // queue: one u32 work counter per kernel (zeroed by the launcher on the stream).
 void launch_sync(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, uint32_t* tok,
                  uint32_t* queue, const KParams& p, cudaStream_t s);
 void launch_inflate(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, uint32_t* tok,
                     uint32_t* queue, const KParams& p, cudaStream_t s);
 uint64_t token_words_per_part();
-int pass1_warps(int nchunks);
+int pass1_warps(int nchunks, int wpb);
 void launch_plan(FileDesc* files, ChunkDesc* chunks, int nfiles, cudaStream_t s);
 void launch_chain(const FileDesc* files, const ChunkDesc* chunks, int nfiles, int ngroups,
                   const int32_t* group_chunk0, const int32_t* group_n, const int32_t* group_file,

@@ -1159,7 +1159,9 @@ __device__ __forceinline__ void init_smem(WarpSmem& S, const KParams& p, int lan
     __syncwarp();
 }
 
-constexpr int kWarpsPerBlock = 4;
+// pass-1 CTA shapes: warps per block and the blocks per SM the register
+// budget is set for (about 20 resident warps per SM, 96 registers a thread)
+constexpr int pass1_min_blocks(int wpb) { return wpb == 2 ? 10 : (wpb == 4 ? 5 : 2); }
 
 // Work queue of the pass-1 kernels: each resident warp takes the next part
 // index until the parts run out, so parts of uneven work (many members of
@@ -1174,7 +1176,8 @@ __device__ __forceinline__ int next_part(uint32_t* queue, int lane) {
 // ---------------------------------------------------------------------------
 // k_sync: block start of each part and its first block
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, 5)
+template <int WPB>
+__global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
     k_sync(const FileDesc* __restrict__ files, ChunkDesc* chunks, int nchunks, uint16_t* symbuf, uint32_t* tokbuf,
            uint32_t* queue, KParams p) {
     __shared__ uint16_t kraft3[512];
@@ -1252,7 +1255,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 5)
 // ---------------------------------------------------------------------------
 // k_inflate: pass 1 of each part up to the next part's block start
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, 5)
+template <int WPB>
+__global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
     k_inflate(const FileDesc* __restrict__ files, ChunkDesc* chunks, int nchunks, uint16_t* symbuf, uint32_t* tokbuf,
               uint32_t* queue, KParams p) {
     WarpSmem& S = warp_smem();
@@ -1840,23 +1844,29 @@ __global__ void k_finalize(FileDesc* files, int nfiles) {
 // host wrappers
 // ---------------------------------------------------------------------------
 static size_t warp_smem_bytes() { return sizeof(WarpSmem); }
-static_assert(kWarpsPerBlock * sizeof(WarpSmem) <= 48 * 1024, "per-block shared memory above the default limit");
 
-// resident blocks of the pass-1 kernels on the current device (both kernels
-// have the same launch bounds and shared memory)
-static int pass1_resident_blocks() {
+static int wpb_of(const KParams& p) { return p.wpb == 2 || p.wpb == 8 ? p.wpb : 4; }
+static int wpb_slot(int wpb) { return wpb == 2 ? 0 : (wpb == 4 ? 1 : 2); }
+
+// resident blocks of the pass-1 kernels of a CTA shape on the current device
+// (both kernels have the same launch bounds and shared memory); also raises
+// the kernels' dynamic shared-memory limit once
+template <int WPB>
+static int pass1_resident_blocks_t() {
     static int cached[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     const int slot = dev >= 0 && dev < 64 ? dev : 0;
     if (!cached[slot]) {
+        const int smem = (int)(WPB * warp_smem_bytes());
         int sms = 0, per_sm_sync = 0, per_sm_inflate = 0;
         const bool ok =
+            cudaFuncSetAttribute(k_sync<WPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
+            cudaFuncSetAttribute(k_inflate<WPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_sync, k_sync, 32 * kWarpsPerBlock,
-                                                          kWarpsPerBlock * warp_smem_bytes()) == cudaSuccess &&
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_inflate, k_inflate, 32 * kWarpsPerBlock,
-                                                          kWarpsPerBlock * warp_smem_bytes()) == cudaSuccess;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_sync, k_sync<WPB>, 32 * WPB, smem) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_inflate, k_inflate<WPB>, 32 * WPB, smem) ==
+                cudaSuccess;
         const int v = std::max(1, sms) * std::max(1, std::min(per_sm_sync, per_sm_inflate));
         if (!ok) {
             cudaGetLastError();
@@ -1867,28 +1877,49 @@ static int pass1_resident_blocks() {
     return cached[slot];
 }
 
-int pass1_warps(int nchunks) {
+static int pass1_resident_blocks(int wpb) {
+    switch (wpb_slot(wpb)) {
+        case 0: return pass1_resident_blocks_t<2>();
+        case 1: return pass1_resident_blocks_t<4>();
+        default: return pass1_resident_blocks_t<8>();
+    }
+}
+
+int pass1_warps(int nchunks, int wpb) {
     if (nchunks <= 0) return 0;
-    const int blocks = std::min((nchunks + kWarpsPerBlock - 1) / kWarpsPerBlock, pass1_resident_blocks());
-    return blocks * kWarpsPerBlock;
+    wpb = wpb == 2 || wpb == 8 ? wpb : 4;
+    const int blocks = std::min((nchunks + wpb - 1) / wpb, pass1_resident_blocks(wpb));
+    return blocks * wpb;
+}
+
+template <int WPB>
+static void launch_pass1(bool sync, const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym,
+                         uint32_t* tok, uint32_t* queue, const KParams& p, cudaStream_t s) {
+    const int grid = pass1_warps(nchunks, WPB) / WPB;
+    const size_t smem = WPB * warp_smem_bytes();
+    if (sync) k_sync<WPB><<<grid, 32 * WPB, smem, s>>>(files, chunks, nchunks, sym, tok, queue, p);
+    else k_inflate<WPB><<<grid, 32 * WPB, smem, s>>>(files, chunks, nchunks, sym, tok, queue, p);
+}
+
+static void launch_pass1_any(bool sync, const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym,
+                             uint32_t* tok, uint32_t* queue, const KParams& p, cudaStream_t s) {
+    if (nchunks <= 0) return;
+    cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
+    switch (wpb_slot(wpb_of(p))) {
+        case 0: launch_pass1<2>(sync, files, chunks, nchunks, sym, tok, queue, p, s); break;
+        case 1: launch_pass1<4>(sync, files, chunks, nchunks, sym, tok, queue, p, s); break;
+        default: launch_pass1<8>(sync, files, chunks, nchunks, sym, tok, queue, p, s); break;
+    }
 }
 
 void launch_sync(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, uint32_t* tok,
                  uint32_t* queue, const KParams& p, cudaStream_t s) {
-    if (nchunks <= 0) return;
-    const int wpb = kWarpsPerBlock;
-    cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
-    k_sync<<<pass1_warps(nchunks) / wpb, 32 * wpb, wpb * warp_smem_bytes(), s>>>(files, chunks, nchunks, sym, tok,
-                                                                                 queue, p);
+    launch_pass1_any(true, files, chunks, nchunks, sym, tok, queue, p, s);
 }
 
 void launch_inflate(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, uint32_t* tok,
                     uint32_t* queue, const KParams& p, cudaStream_t s) {
-    if (nchunks <= 0) return;
-    const int wpb = kWarpsPerBlock;
-    cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
-    k_inflate<<<pass1_warps(nchunks) / wpb, 32 * wpb, wpb * warp_smem_bytes(), s>>>(files, chunks, nchunks, sym,
-                                                                                    tok, queue, p);
+    launch_pass1_any(false, files, chunks, nchunks, sym, tok, queue, p, s);
 }
 
 uint64_t token_words_per_part() { return kTokPerPart; }

@@ -158,7 +158,7 @@ extern "C" int pgz_decompress_noalloc(const uint8_t* gz, uint64_t gz_len, uint8_
     uint16_t* d_sym = reinterpret_cast<uint16_t*>(base + kOffSym);
     uint32_t* d_tok = reinterpret_cast<uint32_t*>(base + kOffTok);
     uint32_t* d_queue = reinterpret_cast<uint32_t*>(base + kOffQueue);
-    if (token_words_per_part() != kTokWords || pass1_warps(kNaMaxParts) > kNaMaxParts) return PGZ_E_ARG;
+    if (token_words_per_part() != kTokWords || pass1_warps(kNaMaxParts, 4) > kNaMaxParts) return PGZ_E_ARG;
 
     KParams kp{};
     pgz_config cfg;
@@ -168,6 +168,7 @@ extern "C" int pgz_decompress_noalloc(const uint8_t* gz, uint64_t gz_len, uint8_
     kp.min_block = cfg.min_block;
     kp.max_block = cfg.max_block;
     kp.confirm_blocks = cfg.confirm_blocks;
+    kp.wpb = 4;
 
     const uint64_t csize = gz_len - 8 - s0, end_bit = (gz_len - 8) * 8;
     uint64_t n = (csize + kNaPartBytes - 1) / kNaPartBytes;

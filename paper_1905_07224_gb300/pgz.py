@@ -28,7 +28,7 @@ class pgz_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("cuda_stream", VP), ("chunk_bytes", U64), ("n_chunks", ctypes.c_int),
                 ("threads_per_chunk", ctypes.c_int), ("allowed", ctypes.c_uint8 * 32),
                 ("confirm_blocks", ctypes.c_int), ("min_block", ctypes.c_uint32), ("max_block", ctypes.c_uint32),
-                ("dev_mem_budget", U64), ("spin_cap", U64)]
+                ("dev_mem_budget", U64), ("spin_cap", U64), ("warps_per_block", ctypes.c_int)]
 
 
 class pgz_stats(ctypes.Structure):
@@ -36,6 +36,14 @@ class pgz_stats(ctypes.Structure):
                 ("false_syncs", U64), ("retries", U64), ("placeholders", U64), ("symbols", U64),
                 ("ms_sync", ctypes.c_float), ("ms_inflate", ctypes.c_float), ("ms_chain", ctypes.c_float),
                 ("ms_translate", ctypes.c_float), ("ms_crc", ctypes.c_float), ("ms_total", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class pgz_tune_entry(ctypes.Structure):
+    _fields_ = [("chunk_bytes", U64), ("warps_per_block", ctypes.c_int), ("status", ctypes.c_int),
+                ("ms", ctypes.c_float)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -77,6 +85,8 @@ def _load():
         "pgz_inspect_window": (ctypes.c_int, [VP, ctypes.c_int, VP]),
         "pgz_kernel_launches": (U64, [VP]),
         "pgz_decompress_noalloc": (ctypes.c_int, [VP, U64, VP, U64, P(U64), VP]),
+        "pgz_autotune": (ctypes.c_int, [VP, VP, U64, VP, U64, P(U64), ctypes.c_int, P(ctypes.c_int), ctypes.c_int,
+                                        ctypes.c_int, P(pgz_tune_entry), P(pgz_tune_entry)]),
         "pgz_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
@@ -100,7 +110,7 @@ EXPORTED = ["pgz_config_init", "pgz_create", "pgz_destroy", "pgz_decompress", "p
             "pgz_decompress_at", "pgz_decompress_batch", "pgz_batch_prepare", "pgz_batch_run", "pgz_batch_free",
             "pgz_index_build", "pgz_index_info", "pgz_decompress_range", "pgz_index_free", "pgz_inspect_parts",
             "pgz_inspect_symbols", "pgz_inspect_window", "pgz_kernel_launches", "pgz_strerror",
-            "pgz_decompress_noalloc"]
+            "pgz_decompress_noalloc", "pgz_autotune"]
 
 
 def pgz_strerror(status: int) -> str:
@@ -195,6 +205,18 @@ class Batch:
         if self.h:
             lib().pgz_batch_free(self.h)
             self.h = None
+
+
+def pgz_autotune(ctx: int, gz_ptr: int, gz_len: int, out_ptr: int, out_cap: int, chunk_bytes, warps_per_block,
+                 reps: int = 3):
+    """(status, [entry dicts], best dict); device addresses; sets the context's part size and CTA shape."""
+    cb = (U64 * len(chunk_bytes))(*chunk_bytes)
+    wp = (ctypes.c_int * len(warps_per_block))(*warps_per_block)
+    ent = (pgz_tune_entry * (len(chunk_bytes) * len(warps_per_block)))()
+    best = pgz_tune_entry()
+    r = lib().pgz_autotune(ctx, gz_ptr, gz_len, out_ptr, out_cap, cb, len(chunk_bytes), wp, len(warps_per_block),
+                           reps, ent, ctypes.byref(best))
+    return r, [e.as_dict() for e in ent], best.as_dict()
 
 
 def pgz_index_build(ctx: int, gz_ptr: int, gz_len: int) -> int:

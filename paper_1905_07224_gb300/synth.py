@@ -38,11 +38,15 @@ def fastq(n_bytes: int, read_len: int = 100, p_n: float = 0.001, seed: int = 0) 
     """Exactly ``n_bytes`` of synthetic FASTQ text (see module docstring)."""
     if n_bytes <= 0:
         return b""
-    L = int(read_len)
-    rng = np.random.default_rng(seed)
+    return _fastq_records(n_bytes, int(read_len), p_n, np.random.default_rng(seed), 0, 0)
+
+
+def _fastq_records(n_bytes: int, L: int, p_n: float, rng, first: int, skip: int) -> bytes:
+    """Records ``first``, ``first + 1``, ... drawn from ``rng``; the first ``skip`` bytes are dropped and
+    exactly ``n_bytes`` are returned."""
     fixed = 2 * L + 4                      # seq + "\n+\n" + qual + "\n"
-    min_rec = len(f"@SIM.0 length={L}\n") + fixed
-    n_rec = n_bytes // min_rec + 2
+    min_rec = len(f"@SIM.{first} length={L}\n") + fixed
+    n_rec = (n_bytes + skip) // min_rec + 2
     bases = np.frombuffer(b"ACGT", dtype=np.uint8)[rng.integers(0, 4, size=(n_rec, L))]
     if p_n > 0:
         bases[rng.random((n_rec, L)) < p_n] = ord("N")
@@ -53,7 +57,7 @@ def fastq(n_bytes: int, read_len: int = 100, p_n: float = 0.001, seed: int = 0) 
     body[:, L:L + 3] = np.frombuffer(b"\n+\n", dtype=np.uint8)
     body[:, L + 3:2 * L + 3] = qual
     body[:, 2 * L + 3] = 10
-    heads = [f"@SIM.{i} length={L}\n".encode() for i in range(n_rec)]
+    heads = [f"@SIM.{i} length={L}\n".encode() for i in range(first, first + n_rec)]
     hlen = np.fromiter((len(h) for h in heads), dtype=np.int64, count=n_rec)
     rec_len = hlen + fixed
     off = np.zeros(n_rec + 1, dtype=np.int64)
@@ -65,8 +69,45 @@ def fastq(n_bytes: int, read_len: int = 100, p_n: float = 0.001, seed: int = 0) 
     np.cumsum(hlen[:-1], out=hstart[1:])
     out[np.repeat(off[:-1] - hstart, hlen) + np.arange(hbytes.size)] = hbytes
     out[(off[:-1] + hlen)[:, None] + np.arange(fixed)[None, :]] = body
-    assert total >= n_bytes
-    return out[:n_bytes].tobytes()
+    assert total >= n_bytes + skip
+    return out[skip:skip + n_bytes].tobytes()
+
+
+def _fastq_record_at(byte: int, L: int):
+    """(record index, offset inside it) of byte ``byte`` of the record stream: a record's length depends only
+    on the number of digits of its index."""
+    fixed = 2 * L + 4
+    tail = len(f" length={L}\n") + len("@SIM.") + fixed
+    i, pos, d = 0, 0, 1
+    while True:
+        n = 9 * 10 ** (d - 1) if d > 1 else 10           # indices with d digits (0..9 for d = 1)
+        size = n * (tail + d)
+        if byte < pos + size:
+            k = (byte - pos) // (tail + d)
+            return i + k, (byte - pos) - k * (tail + d)
+        i, pos, d = i + n, pos + size, d + 1
+
+
+def _fastq_piece(args):
+    n_bytes, L, p_n, seed, k, piece = args
+    first, skip = _fastq_record_at(k * piece, L)
+    return _fastq_records(n_bytes, L, p_n, np.random.default_rng([seed, k]), first, skip)
+
+
+def fastq_large(n_bytes: int, read_len: int = 150, p_n: float = 0.01, seed: int = 2, piece: int = 256 << 20,
+                processes: int | None = None) -> bytes:
+    """Exactly ``n_bytes`` of FASTQ text for inputs too large for one draw: piece k covers bytes
+    [k * piece, (k + 1) * piece) of the record stream (records numbered from 0, so the concatenation is one
+    stream), with its own generator ``default_rng([seed, k])``; pieces are drawn in parallel."""
+    import multiprocessing as mp
+    L = int(read_len)
+    jobs = [(min(piece, n_bytes - k * piece), L, p_n, seed, k, piece) for k in range((n_bytes + piece - 1) // piece)]
+    if processes is None:
+        processes = min(len(jobs), max(1, len(os.sched_getaffinity(0))))
+    if processes <= 1 or len(jobs) <= 1:
+        return b"".join(_fastq_piece(j) for j in jobs)
+    with mp.get_context("spawn").Pool(processes) as pool:
+        return b"".join(pool.map(_fastq_piece, jobs, chunksize=1))
 
 
 # ---------------------------------------------------------------------------
@@ -121,6 +162,36 @@ def gzip_compress(data: bytes, level: int = 6) -> bytes:
     """Single-member gzip (10-byte header) via host zlib at ``level``."""
     c = zlib.compressobj(level, zlib.DEFLATED, 31)
     return c.compress(data) + c.flush()
+
+
+def _deflate_piece(args):
+    data, dict_bytes, level, last = args
+    c = zlib.compressobj(level, zlib.DEFLATED, -15, 8, zlib.Z_DEFAULT_STRATEGY, *([dict_bytes] if dict_bytes else []))
+    return c.compress(data) + c.flush(zlib.Z_FINISH if last else zlib.Z_SYNC_FLUSH)
+
+
+def gzip_compress_parallel(data: bytes, level: int = 6, piece: int = 64 << 20, processes: int | None = None) -> bytes:
+    """One gzip member (RFC 1952, 10-byte header) of ``data`` compressed by host zlib in parallel pieces, the
+    way pigz does: piece k is deflated with the previous 32 KiB as its preset dictionary and ends with a sync
+    flush (an empty stored block), so the pieces form one DEFLATE stream.  CRC-32 and ISIZE (length mod 2^32)
+    come from ``zlib.crc32`` and ``len``."""
+    import multiprocessing as mp
+    n = len(data)
+    mv = memoryview(data)
+    jobs = []
+    for a in range(0, max(n, 1), piece):
+        b = min(n, a + piece)
+        jobs.append((bytes(mv[a:b]), bytes(mv[max(0, a - 32768):a]) if a else b"", level, b >= n))
+    if processes is None:
+        processes = min(len(jobs), max(1, len(os.sched_getaffinity(0))))
+    if processes <= 1 or len(jobs) <= 1:
+        body = b"".join(_deflate_piece(j) for j in jobs)
+    else:
+        with mp.get_context("spawn").Pool(processes) as pool:
+            body = b"".join(pool.map(_deflate_piece, jobs, chunksize=1))
+    head = bytes([0x1F, 0x8B, 8, 0, 0, 0, 0, 0, 0, 255])
+    tail = (zlib.crc32(data) & 0xFFFFFFFF).to_bytes(4, "little") + (n & 0xFFFFFFFF).to_bytes(4, "little")
+    return head + body + tail
 
 
 def log_uniform_sizes(n: int, lo: int, hi: int, rng: np.random.Generator) -> np.ndarray:
