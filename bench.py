@@ -7,13 +7,15 @@ files (block-start search, pass 1, window chain, translation, CRC-32/ISIZE
 check) with inputs and outputs resident in device memory, in two forms:
 
   batched (the reported value): both files in one run of the pass kernels,
-      parts of --chunk-bytes compressed bytes taken from a device work queue,
-      captured once in a CUDA graph (pgz_batch_prepare / pgz_batch_run);
+      parts taken from a device work queue, captured once in a CUDA graph
+      (pgz_batch_prepare / pgz_batch_run); part size and pass-1 CTA shape
+      are chosen by the library's autotuner (pgz_autotune) on the same files
+      unless --chunk-bytes fixes the size;
   plain: one file at a time through pgz_decompress with 1024 equal parts per
       file, with sync-failure and placeholder statistics per level.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pgz|reference]
-                  [--workload fastq256|fastq1m] [--chunk-bytes B]
+                  [--workload fastq256|fastq1m|fastq4g|batch512] [--chunk-bytes B]
                   [--profile-case MIB:LEVEL:CALLS]
 
 Prints one JSON line.  --impl reference times the CPU oracle (the plain
@@ -36,7 +38,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 L2_BYTES = 126 * (1 << 20)
-CHUNK_BYTES = 64 << 10        # compressed bytes per part (about two DEFLATE blocks of zlib output)
+CHUNK_BYTES = 64 << 10        # compressed bytes per part when the autotuner is not run
+TUNE_CHUNKS = [32 << 10, 64 << 10, 128 << 10, 256 << 10, 512 << 10]   # the autotuner's part sizes ...
+TUNE_WPB = [2, 4, 8]                                                # ... and pass-1 CTA shapes (warps)
 PLAIN_PARTS = 1024            # parts per file of the plain one-file-at-a-time form
 METRIC = "decompressed GB/s on 1 GB300 (batched vs plain), %HBM roofline"
 # DRAM bytes (read + write) of pass 1 per decompressed byte: ncu capture of k_sync and k_inflate on one
@@ -180,9 +184,19 @@ def run_pgz(args, rank, world):
             tdist.barrier()
         return e0.elapsed_time(e1) / args.steps, pgz.pgz_kernel_launches(ctx) - l0
 
-    # ---- batched: every file of the step in one graph-captured run of the pass kernels
+    # ---- batched: every file of the step in one graph-captured run of the pass kernels, with the part size
+    # and pass-1 CTA shape chosen by the library's autotuner on these files (unless --chunk-bytes fixes them)
     ctx_b = pgz.pgz_create(pgz.pgz_config_init(device=dev, cuda_stream=stream.cuda_stream, n_chunks=0,
-                                               chunk_bytes=args.chunk_bytes))
+                                               chunk_bytes=args.chunk_bytes or CHUNK_BYTES))
+    tune = None
+    if not args.chunk_bytes:
+        st, entries, best = pgz.pgz_autotune(ctx_b, jobs, TUNE_CHUNKS, TUNE_WPB, 2)
+        if st != 0:
+            raise RuntimeError(f"pgz_autotune failed: {pgz.pgz_strerror(st)}")
+        tune = {"best": [best["chunk_bytes"], best["warps_per_block"]],
+                "ms": {f"{e['chunk_bytes'] >> 10}K/{e['warps_per_block']}w": round(e["ms"], 2) for e in entries}}
+    chunk_bytes = tune["best"][0] if tune else args.chunk_bytes
+    wpb = tune["best"][1] if tune else 4
     batch = pgz.Batch(ctx_b, jobs)
 
     def step_batched():
@@ -292,7 +306,7 @@ def run_pgz(args, rank, world):
         "data": "synthetic",
         "config": {"workload": desc, "form": "batched (all files of the step in one graph-captured run)",
                    "files": len(files), "out_bytes_per_step": total_out, "in_bytes_per_step": total_in,
-                   "chunk_bytes": args.chunk_bytes, "parts": batch_parts,
+                   "chunk_bytes": chunk_bytes, "warps_per_block": wpb, "parts": batch_parts,
                    "l2": "inputs (%.0f MB) and outputs (%.0f MB) larger than L2" % (total_in / 1e6, total_out / 1e6),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "compressed_MBps": round(world * total_in / (ms * 1e-3) / 1e6, 1),
@@ -314,10 +328,144 @@ def run_pgz(args, rank, world):
                 "path": "pinned host -> device copies, pgz_batch_run, device -> pinned host copies"},
         "gpu_launches": int(launches),
         "clocks": clocks,
+        "autotune": tune,
     }
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(files)
     return line
+
+
+def _stage_line(stage, total_in, total_out, window_bytes, hbm):
+    stage = {k: v for k, v in stage.items() if k.startswith("ms_")}
+    t = stage["ms_translate"] * 1e-3
+    c = stage["ms_crc"] * 1e-3
+    return {"stages_ms": {k: round(v, 3) for k, v in stage.items()},
+            "roofline_translate": {"achieved": round((3 * total_out + window_bytes) / t / 1e9, 1) if t else None,
+                                   "frac": round((3 * total_out + window_bytes) / t / 1e9 / hbm, 4) if t else None},
+            "roofline_crc": {"achieved": round(total_out / c / 1e9, 1) if c else None,
+                             "frac": round(total_out / c / 1e9 / hbm, 4) if c else None}}
+
+
+def run_tune4g(args):
+    """4 GiB FASTQ (150 bp, 1 % N, seed 2) at gzip -6, ISIZE = 0: the autotuner's sweep of part size x pass-1
+    CTA shape, then the chosen pair timed."""
+    import numpy as np
+    import torch
+    from paper_1905_07224_gb300 import build, pgz, synth
+    build.build()
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    raw = synth.fastq_large(4 << 30, 150, 0.01, 2)
+    gz = synth.gzip_compress_parallel(raw, 6)
+    t_make = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    ctx = pgz.pgz_create(pgz.pgz_config_init(device=0, cuda_stream=stream.cuda_stream))
+    d_in = torch.from_numpy(np.frombuffer(gz, dtype=np.uint8).copy()).cuda()
+    d_out = torch.empty(len(raw) + 4096, dtype=torch.uint8, device="cuda")
+    chunks = [32 << 10, 64 << 10, 128 << 10, 256 << 10, 512 << 10, 1 << 20, 2 << 20, 4 << 20]
+    st, entries, best = pgz.pgz_autotune(ctx, [(d_in.data_ptr(), len(gz), d_out.data_ptr(), d_out.numel())], chunks,
+                                         [2, 4, 8], 2)
+    if st != 0:
+        raise RuntimeError(f"pgz_autotune failed: {pgz.pgz_strerror(st)}")
+    ref = torch.from_numpy(np.frombuffer(raw, dtype=np.uint8).copy()).cuda()
+    if not torch.equal(d_out[:len(raw)], ref):
+        raise RuntimeError("output mismatch")
+    for _ in range(args.warmup):
+        pgz.pgz_decompress(ctx, d_in.data_ptr(), len(gz), d_out.data_ptr(), d_out.numel())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        st, n, _ = pgz.pgz_decompress(ctx, d_in.data_ptr(), len(gz), d_out.data_ptr(), d_out.numel())
+        if st != 0 or n != len(raw):
+            raise RuntimeError(f"pgz_decompress failed: {pgz.pgz_strerror(st)}")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    st, n, s = pgz.pgz_decompress(ctx, d_in.data_ptr(), len(gz), d_out.data_ptr(), d_out.numel(), True)
+    _, _, nph = pgz.pgz_inspect_parts(ctx)
+    pgz.pgz_destroy(ctx)
+    hbm = _peaks().get("hbm_gbs") or 6800.0
+    line = {"workload": "4 GiB synthetic FASTQ (150 bp, 1 % N, seed 2), gzip -6 (parallel pieces, one member), "
+                        "ISIZE 0", "in_bytes": len(gz), "out_bytes": len(raw), "isize": int.from_bytes(gz[-4:], "little"),
+            "make_s": round(t_make, 1), "tune": [{**e, "ms": round(e["ms"], 3)} for e in entries],
+            "best": {**best, "ms": round(best["ms"], 3)}, "parts": s["chunks"],
+            "value": round(len(raw) / (ms * 1e-3) / 1e9, 3), "unit": "GB/s", "ms_per_call": round(ms, 3),
+            "placeholder_fraction": round(s["placeholders"] / max(1, s["symbols"]), 4),
+            "false_syncs": s["false_syncs"], "retries": s["retries"], "empty_parts": s["empty_chunks"]}
+    line.update(_stage_line(s, len(gz), len(raw), int((nph > 0).sum()) * 32768, hbm))
+    return line
+
+
+def run_batch512(args):
+    """512 members, log-uniform 64 KiB .. 64 MiB (seed 3), FASTQ and Markov text, levels 1/6/9: one
+    graph-captured batched run against one pgz_decompress call per member."""
+    import numpy as np
+    import torch
+    from paper_1905_07224_gb300 import build, pgz, synth
+    build.build()
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    files = synth.make_files(synth.batch_manifest(512, 3))
+    t_make = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    total_out = sum(len(r) for r, _ in files)
+    total_in = sum(len(g) for _, g in files)
+    d_in = [torch.from_numpy(np.frombuffer(g, dtype=np.uint8).copy()).cuda() for _, g in files]
+    d_out = [torch.empty(len(r) + 4096, dtype=torch.uint8, device="cuda") for r, _ in files]
+    jobs = [(d_in[k].data_ptr(), len(g), d_out[k].data_ptr(), d_out[k].numel()) for k, (_, g) in enumerate(files)]
+
+    def timed(step):
+        for _ in range(args.warmup):
+            step()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    def check():
+        torch.cuda.synchronize()
+        for k, (raw, _) in enumerate(files):
+            ref = torch.from_numpy(np.frombuffer(raw, dtype=np.uint8).copy()).cuda()
+            if not torch.equal(d_out[k][:len(raw)], ref):
+                raise RuntimeError(f"output mismatch (member {k})")
+            d_out[k].zero_()
+
+    ctx = pgz.pgz_create(pgz.pgz_config_init(device=0, cuda_stream=stream.cuda_stream,
+                                             chunk_bytes=args.chunk_bytes or CHUNK_BYTES))
+    batch = pgz.Batch(ctx, jobs)
+
+    def step_batched():
+        r, res, _ = batch.run()
+        if r != 0:
+            raise RuntimeError(f"pgz_batch_run failed: {pgz.pgz_strerror(r)}")
+
+    step_batched()
+    check()
+    ms_b = timed(step_batched)
+    r, _, s = pgz.pgz_decompress_batch(ctx, jobs, stats=True)
+    batch.free()
+
+    def step_plain():
+        for k, (gp, gl, op, oc) in enumerate(jobs):
+            st, n, _ = pgz.pgz_decompress(ctx, gp, gl, op, oc)
+            if st != 0:
+                raise RuntimeError(f"pgz_decompress failed: {pgz.pgz_strerror(st)}")
+
+    step_plain()
+    check()
+    ms_p = timed(step_plain)
+    pgz.pgz_destroy(ctx)
+    return {"workload": "512 synthetic members, log-uniform 64 KiB-64 MiB (seed 3), FASTQ/Markov, gzip -1/-6/-9",
+            "in_bytes": total_in, "out_bytes": total_out, "make_s": round(t_make, 1), "parts": s["chunks"],
+            "batched": {"value": round(total_out / (ms_b * 1e-3) / 1e9, 3), "ms_per_step": round(ms_b, 3),
+                        "form": "one graph-captured run, device work queue"},
+            "plain": {"value": round(total_out / (ms_p * 1e-3) / 1e9, 3), "ms_per_step": round(ms_p, 3),
+                      "form": "one pgz_decompress per member"},
+            "unit": "GB/s", "stages_ms_batched": {k: round(v, 3) for k, v in s.items() if k.startswith("ms_")}}
 
 
 def cpu_baseline(files, budget_s: float = 20.0):
@@ -403,15 +551,19 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pgz", choices=["pgz", "reference"])
-    ap.add_argument("--workload", default="fastq256", choices=["fastq256", "fastq1m"])
-    ap.add_argument("--chunk-bytes", type=int, default=CHUNK_BYTES)
+    ap.add_argument("--workload", default="fastq256", choices=["fastq256", "fastq1m", "fastq4g", "batch512"],
+                    help="fastq256: the benchmark; fastq4g: autotuner sweep on 4 GiB; batch512: 512 members")
+    ap.add_argument("--chunk-bytes", type=int, default=0, help="fixed part size (default: autotuned)")
     ap.add_argument("--profile-case", default=None, metavar="MIB:LEVEL:CALLS",
                     help="run one small checked case for an ncu capture and print its stage times")
     args = ap.parse_args()
     if args.profile_case:
-        print(json.dumps(run_profile_case(args.profile_case, args.chunk_bytes)), flush=True)
+        print(json.dumps(run_profile_case(args.profile_case, args.chunk_bytes or CHUNK_BYTES)), flush=True)
         return
     args.warmup = max(3, args.warmup)
+    if args.workload in ("fastq4g", "batch512") and args.impl == "pgz":
+        print(json.dumps(run_tune4g(args) if args.workload == "fastq4g" else run_batch512(args)), flush=True)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":

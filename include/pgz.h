@@ -209,19 +209,20 @@ typedef struct pgz_tune_entry {
 /* Autotuner.  The number of parts n is a free parameter of the method
    (Section "Full file decompression in two passes": n roughly equal parts);
    this picks the part size and the pass-1 CTA shape for the caller's data.
-   For every pair chunk_bytes[a] x warps_per_block[b] it runs pgz_decompress on
-   (gz, out) -- device buffers with pgz_decompress's rules -- once untimed and
-   reps times timed (CUDA events on the context's stream), and then sets the
-   context's chunk_bytes and warps_per_block (n_chunks = 0) to the pair with
-   the smallest median time among those whose calls returned PGZ_OK.
+   For every pair chunk_bytes[a] x warps_per_block[b] it runs
+   pgz_decompress_batch on the n_jobs jobs (device buffers, the batch rules;
+   one job is one member) once untimed and reps times timed (CUDA events on the
+   context's stream), and then sets the context's chunk_bytes and
+   warps_per_block (n_chunks = 0) to the pair with the smallest median time
+   among those whose calls returned PGZ_OK for every job.
    entries: n_chunk_bytes * n_wpb results, row-major by chunk size (NULL: not
-   returned); best: the chosen pair (NULL: not returned).  out holds the last
-   call's output.  Returns PGZ_E_ARG for empty lists, chunk sizes below 4 KiB,
-   CTA shapes other than 2, 4 or 8 warps, or reps < 1; if no pair succeeded,
-   the first failing status (the context is left unchanged). */
-int pgz_autotune(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, uint8_t* out, uint64_t out_cap,
-                 const uint64_t* chunk_bytes, int n_chunk_bytes, const int* warps_per_block, int n_wpb, int reps,
-                 pgz_tune_entry* entries, pgz_tune_entry* best);
+   returned); best: the chosen pair (NULL: not returned).  The jobs' outputs and
+   statuses are those of the last call.  Returns PGZ_E_ARG for empty lists,
+   chunk sizes below 4 KiB, CTA shapes other than 2, 4 or 8 warps, or reps < 1;
+   if no pair succeeded, the first failing status (the context is left
+   unchanged). */
+int pgz_autotune(pgz_ctx* ctx, pgz_job* jobs, int n_jobs, const uint64_t* chunk_bytes, int n_chunk_bytes,
+                 const int* warps_per_block, int n_wpb, int reps, pgz_tune_entry* entries, pgz_tune_entry* best);
 
 /* Number of kernels this library launched on ctx since it was created. */
 uint64_t pgz_kernel_launches(const pgz_ctx* ctx);

@@ -1019,10 +1019,11 @@ void pgz_index_free(pgz_index* idx) {
     delete idx;
 }
 
-int pgz_autotune(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, uint8_t* out, uint64_t out_cap,
-                 const uint64_t* chunk_bytes, int n_chunk_bytes, const int* warps_per_block, int n_wpb, int reps,
-                 pgz_tune_entry* entries, pgz_tune_entry* best) {
-    if (!ctx || !chunk_bytes || !warps_per_block || n_chunk_bytes <= 0 || n_wpb <= 0 || reps < 1) return PGZ_E_ARG;
+int pgz_autotune(pgz_ctx* ctx, pgz_job* jobs, int n_jobs, const uint64_t* chunk_bytes, int n_chunk_bytes,
+                 const int* warps_per_block, int n_wpb, int reps, pgz_tune_entry* entries, pgz_tune_entry* best) {
+    if (!ctx || !jobs || n_jobs <= 0 || !chunk_bytes || !warps_per_block || n_chunk_bytes <= 0 || n_wpb <= 0 ||
+        reps < 1)
+        return PGZ_E_ARG;
     for (int a = 0; a < n_chunk_bytes; ++a)
         if (chunk_bytes[a] < 4096) return PGZ_E_ARG;
     for (int b = 0; b < n_wpb; ++b)
@@ -1043,11 +1044,10 @@ int pgz_autotune(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, uint8_t* out,
             ctx->cfg.chunk_bytes = e.chunk_bytes;
             ctx->cfg.warps_per_block = e.warps_per_block;
             ctx->kp.wpb = e.warps_per_block;
-            uint64_t n = 0;
-            e.status = pgz_decompress(ctx, gz, gz_len, out, out_cap, &n, nullptr);   // settles buffers and plan
+            e.status = pgz_decompress_batch(ctx, n_jobs, jobs, nullptr);   // settles buffers and plan
             for (int r = 0; r < reps && e.status == PGZ_OK; ++r) {
                 cudaEventRecord(ctx->ev[6], ctx->stream);
-                e.status = pgz_decompress(ctx, gz, gz_len, out, out_cap, &n, nullptr);
+                e.status = pgz_decompress_batch(ctx, n_jobs, jobs, nullptr);
                 cudaEventRecord(ctx->ev[7], ctx->stream);
                 if (cudaEventSynchronize(ctx->ev[7]) != cudaSuccess) e.status = PGZ_E_CUDA;
                 else cudaEventElapsedTime(&t[(size_t)r], ctx->ev[6], ctx->ev[7]);

@@ -85,8 +85,8 @@ def _load():
         "pgz_inspect_window": (ctypes.c_int, [VP, ctypes.c_int, VP]),
         "pgz_kernel_launches": (U64, [VP]),
         "pgz_decompress_noalloc": (ctypes.c_int, [VP, U64, VP, U64, P(U64), VP]),
-        "pgz_autotune": (ctypes.c_int, [VP, VP, U64, VP, U64, P(U64), ctypes.c_int, P(ctypes.c_int), ctypes.c_int,
-                                        ctypes.c_int, P(pgz_tune_entry), P(pgz_tune_entry)]),
+        "pgz_autotune": (ctypes.c_int, [VP, P(pgz_job), ctypes.c_int, P(U64), ctypes.c_int, P(ctypes.c_int),
+                                        ctypes.c_int, ctypes.c_int, P(pgz_tune_entry), P(pgz_tune_entry)]),
         "pgz_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
@@ -207,15 +207,16 @@ class Batch:
             self.h = None
 
 
-def pgz_autotune(ctx: int, gz_ptr: int, gz_len: int, out_ptr: int, out_cap: int, chunk_bytes, warps_per_block,
-                 reps: int = 3):
-    """(status, [entry dicts], best dict); device addresses; sets the context's part size and CTA shape."""
+def pgz_autotune(ctx: int, jobs, chunk_bytes, warps_per_block, reps: int = 3):
+    """(status, [entry dicts], best dict); jobs: list of (gz_ptr, gz_len, out_ptr, out_cap) device addresses;
+    sets the context's part size and CTA shape."""
+    arr = _jobs(jobs)
     cb = (U64 * len(chunk_bytes))(*chunk_bytes)
     wp = (ctypes.c_int * len(warps_per_block))(*warps_per_block)
     ent = (pgz_tune_entry * (len(chunk_bytes) * len(warps_per_block)))()
     best = pgz_tune_entry()
-    r = lib().pgz_autotune(ctx, gz_ptr, gz_len, out_ptr, out_cap, cb, len(chunk_bytes), wp, len(warps_per_block),
-                           reps, ent, ctypes.byref(best))
+    r = lib().pgz_autotune(ctx, arr, len(jobs), cb, len(chunk_bytes), wp, len(warps_per_block), reps, ent,
+                           ctypes.byref(best))
     return r, [e.as_dict() for e in ent], best.as_dict()
 
 

@@ -55,8 +55,8 @@ def test_autotune_picks_the_fastest_working_pair():
     d = to_device(gz)
     out = empty(len(raw) + 4096)
     chunks, wpbs = [32 << 10, 64 << 10, 256 << 10], [2, 4, 8]
-    st, entries, best = ctx.pgz.pgz_autotune(ctx.h, d.data_ptr(), len(gz), out.data_ptr(), out.numel(), chunks,
-                                             wpbs, 2)
+    job = [(d.data_ptr(), len(gz), out.data_ptr(), out.numel())]
+    st, entries, best = ctx.pgz.pgz_autotune(ctx.h, job, chunks, wpbs, 2)
     assert st == 0
     assert len(entries) == 9 and all(e["status"] == 0 and e["ms"] > 0 for e in entries)
     assert [(e["chunk_bytes"], e["warps_per_block"]) for e in entries] == [(c, w) for c in chunks for w in wpbs]
@@ -69,10 +69,8 @@ def test_autotune_picks_the_fastest_working_pair():
     parts = (len(gz) - 18 + best["chunk_bytes"] - 1) // best["chunk_bytes"]
     assert s["chunks"] == parts
     # invalid lists are rejected without running anything
-    assert ctx.pgz.pgz_autotune(ctx.h, d.data_ptr(), len(gz), out.data_ptr(), out.numel(), [1024], [4], 1)[0] \
-        == ctx.pgz.PGZ_E_ARG
-    assert ctx.pgz.pgz_autotune(ctx.h, d.data_ptr(), len(gz), out.data_ptr(), out.numel(), [65536], [3], 1)[0] \
-        == ctx.pgz.PGZ_E_ARG
+    assert ctx.pgz.pgz_autotune(ctx.h, job, [1024], [4], 1)[0] == ctx.pgz.PGZ_E_ARG
+    assert ctx.pgz.pgz_autotune(ctx.h, job, [65536], [3], 1)[0] == ctx.pgz.PGZ_E_ARG
     ctx.close()
 
 
