@@ -15,7 +15,7 @@ check) with inputs and outputs resident in device memory, in two forms:
       file, with sync-failure and placeholder statistics per level.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pgz|reference]
-                  [--workload fastq256|fastq1m|fastq4g|batch512] [--chunk-bytes B]
+                  [--workload fastq256|fastq1m|fastq4g|batch512|served] [--chunk-bytes B]
                   [--profile-case MIB:LEVEL:CALLS]
 
 Prints one JSON line.  --impl reference times the CPU oracle (the plain
@@ -468,6 +468,73 @@ def run_batch512(args):
             "unit": "GB/s", "stages_ms_batched": {k: round(v, 3) for k, v in s.items() if k.startswith("ms_")}}
 
 
+def run_served(args):
+    """Served requests: a pool of 256 members, log-uniform 4 KiB .. 256 MiB (seed 4), half FASTQ and half
+    Markov text, levels 1/6/9; Poisson arrivals at offered loads of 1, 4 and 16 GB/s decompressed; 70 % whole
+    members and 30 % byte ranges (offset uniform, length log-uniform 4 KiB .. 1 MiB, clipped); 2000 requests per
+    load under a 64 GiB device-memory budget.  Latency: arrival to completion seen by the host."""
+    import numpy as np
+    import torch
+    from paper_1905_07224_gb300 import build, pgz, synth
+    build.build()
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(4)
+    sizes = synth.log_uniform_sizes(256, 4 << 10, 256 << 20, rng)
+    levels = rng.choice(np.array([1, 6, 9]), size=256)
+    entries = [("fastq" if k % 2 == 0 else "markov", int(sizes[k]), int(levels[k]), 400003 + k) for k in range(256)]
+    t0 = time.perf_counter()
+    files = synth.make_files(entries)
+    t_make = time.perf_counter() - t0
+    mean_d = float(np.mean([len(r) for r, _ in files]))
+    srv = pgz.Server(pgz.pgz_config_init(device=0, chunk_bytes=args.chunk_bytes or CHUNK_BYTES), slots=4,
+                     mem_budget=64 << 30)
+    d_in = [torch.from_numpy(np.frombuffer(g, dtype=np.uint8).copy()).cuda() for _, g in files]
+    ids = [srv.add_file(d.data_ptr(), len(g)) for d, (_, g) in zip(d_in, files)]
+    n_req = int(os.environ.get("PGZ_SERVED_REQUESTS", "2000"))
+    results = []
+    for load in (1e9, 4e9, 16e9):
+        lam = load / mean_d
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, size=n_req))
+        reqs = []
+        for _ in range(n_req):
+            f = int(rng.integers(len(files)))
+            D = len(files[f][0])
+            if rng.random() < 0.7:
+                reqs.append((f, None, None, D))
+            else:
+                off = int(rng.integers(D))
+                ln = int(min(D - off, np.exp(rng.uniform(np.log(4 << 10), np.log(1 << 20)))))
+                reqs.append((f, off, ln, ln))
+        outs = [torch.empty(r[3] + 64, dtype=torch.uint8, device="cuda") for r in reqs]
+        torch.cuda.synchronize()
+        qs = []
+        start = time.monotonic()
+        for k, (f, off, ln, _) in enumerate(reqs):
+            while time.monotonic() - start < arrivals[k]:
+                srv.poll()
+            qs.append(srv.submit(ids[f], outs[k].data_ptr(), outs[k].numel(), offset=off or 0, length=ln))
+        while srv.pending():
+            srv.poll()
+        end = max(q.t_done for q in qs)
+        lat = np.array([q.t_done - (start + arrivals[k]) for k, q in enumerate(qs)]) * 1e3
+        bad = sum(q.status != 0 for q in qs)
+        for k in rng.choice(n_req, size=min(40, n_req), replace=False):      # exact bytes, sampled
+            f, off, ln, _ = reqs[k]
+            raw = files[f][0] if off is None else files[f][0][off:off + ln]
+            if outs[k][:len(raw)].cpu().numpy().tobytes() != raw:
+                raise RuntimeError(f"served request {k}: output mismatch")
+        served = sum(r[3] for r in reqs)
+        results.append({"offered_GBps": load / 1e9, "requests": n_req, "failed": int(bad),
+                        "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                        "achieved_GBps": round(served / (end - start) / 1e9, 3),
+                        "span_s": round(end - start, 3)})
+        del outs
+    srv.close()
+    return {"workload": "served: 256 synthetic members, log-uniform 4 KiB-256 MiB (seed 4), FASTQ/Markov, gzip -1/-6/-9; "
+                        "Poisson arrivals, 70 % whole / 30 % ranges, 64 GiB budget, 4 slots",
+            "make_s": round(t_make, 1), "mean_member_bytes": round(mean_d), "loads": results}
+
+
 def cpu_baseline(files, budget_s: float = 20.0):
     """The oracle (plain bit-at-a-time inflater, one thread) on the same files."""
     import oracle
@@ -551,8 +618,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pgz", choices=["pgz", "reference"])
-    ap.add_argument("--workload", default="fastq256", choices=["fastq256", "fastq1m", "fastq4g", "batch512"],
-                    help="fastq256: the benchmark; fastq4g: autotuner sweep on 4 GiB; batch512: 512 members")
+    ap.add_argument("--workload", default="fastq256", choices=["fastq256", "fastq1m", "fastq4g", "batch512", "served"],
+                    help="fastq256: the benchmark; fastq4g: autotuner sweep on 4 GiB; batch512: 512 members; "
+                         "served: request loop at three offered loads")
     ap.add_argument("--chunk-bytes", type=int, default=0, help="fixed part size (default: autotuned)")
     ap.add_argument("--profile-case", default=None, metavar="MIB:LEVEL:CALLS",
                     help="run one small checked case for an ncu capture and print its stage times")
@@ -561,8 +629,9 @@ def main():
         print(json.dumps(run_profile_case(args.profile_case, args.chunk_bytes or CHUNK_BYTES)), flush=True)
         return
     args.warmup = max(3, args.warmup)
-    if args.workload in ("fastq4g", "batch512") and args.impl == "pgz":
-        print(json.dumps(run_tune4g(args) if args.workload == "fastq4g" else run_batch512(args)), flush=True)
+    if args.workload in ("fastq4g", "batch512", "served") and args.impl == "pgz":
+        run = {"fastq4g": run_tune4g, "batch512": run_batch512, "served": run_served}[args.workload]
+        print(json.dumps(run(args)), flush=True)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -224,6 +224,55 @@ typedef struct pgz_tune_entry {
 int pgz_autotune(pgz_ctx* ctx, pgz_job* jobs, int n_jobs, const uint64_t* chunk_bytes, int n_chunk_bytes,
                  const int* warps_per_block, int n_wpb, int reps, pgz_tune_entry* entries, pgz_tune_entry* best);
 
+/* ---------------------------------------------------------------------------
+   Serving: a request loop with continuous batching.  Registered members stay
+   resident (compressed input; for byte ranges also the index of part starts
+   and resolved windows, built by the first range request of a member).  The
+   server owns `slots` contexts, each with its own CUDA stream.  A request is a
+   whole member or a byte range [offset, offset + length) of its decompressed
+   output (Problem 1 with known starts: decoding begins at the indexed block
+   start before the range, with the indexed window as context).  pgz_server_poll
+   finishes the runs whose work has completed and admits queued requests, in
+   arrival order, into free slots: all requests admitted to one slot form one
+   run of the pass kernels, and the runs of different slots overlap on the
+   GPU.  The queue is spread over the free slots, and one run takes at most
+   mem_budget / slots of scratch (but at least one request).  A request is
+   admitted while the scratch charged to running requests (compressed size +
+   3 x decompressed size each) stays within mem_budget; one that alone exceeds
+   it fails with PGZ_E_NOMEM.  One host thread drives a server.  Every result is exactly the
+   member's decompressed bytes, whatever else runs beside it.
+   --------------------------------------------------------------------------- */
+typedef struct pgz_server pgz_server;
+
+typedef struct pgz_request {
+    int file;                   /* id from pgz_server_add_file */
+    int whole;                  /* 1: the whole member (offset, length ignored); 0: a byte range */
+    uint64_t offset, length;    /* range in decompressed bytes */
+    uint8_t* out;               /* device: output buffer */
+    uint64_t out_cap;
+    int status;                 /* result: -1 while queued or running, then a pgz_status */
+    uint64_t out_len;           /* result: bytes written */
+    double t_submit, t_start, t_done;   /* host steady-clock seconds: submitted, admitted, completed */
+} pgz_request;
+
+/* mem_budget: bytes of scratch for running requests (0 = no limit); slots >= 1.
+   cfg as for pgz_create (cfg->cuda_stream is ignored: each slot has a stream). */
+int pgz_server_create(pgz_server** out, const pgz_config* cfg, int slots, uint64_t mem_budget);
+/* Registers a member held by the caller in device memory (4-byte aligned) for
+   the server's lifetime; reads its header and trailer.  *file receives the id. */
+int pgz_server_add_file(pgz_server* srv, const uint8_t* gz, uint64_t gz_len, int* file);
+/* Queues a request; the server keeps the pointer until the request is done.
+   PGZ_E_ARG for an unknown member, a range outside the member, or out too small. */
+int pgz_server_submit(pgz_server* srv, pgz_request* req);
+/* Completes finished runs and admits queued requests; never waits for the GPU.
+   *n_done (nullable): requests completed by this call. */
+int pgz_server_poll(pgz_server* srv, int* n_done);
+/* Polls until every submitted request is done. */
+int pgz_server_drain(pgz_server* srv);
+/* Requests queued or running. */
+int pgz_server_pending(const pgz_server* srv);
+void pgz_server_destroy(pgz_server* srv);
+
 /* Number of kernels this library launched on ctx since it was created. */
 uint64_t pgz_kernel_launches(const pgz_ctx* ctx);
 

@@ -2,7 +2,9 @@
 // part planning, the launch sequence of the two passes, recovery from false
 // block starts, batches replayed as CUDA graphs, and the random-access index.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <deque>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -514,6 +516,56 @@ int execute(pgz_ctx* ctx, Plan& P, pgz_stats* st) {
     }
 }
 
+// a byte range [d_off, d_off + len) of an indexed member as a mode-2 member of P:
+// the indexed parts covering it, each from its known block start, the last one
+// up to the next indexed start; wins receives (part in P, indexed part) pairs
+// whose windows come from the index
+void plan_range(Plan& P, const pgz_index* idx, uint64_t d_off, uint64_t len, uint8_t* out,
+                std::vector<std::pair<size_t, size_t>>& wins) {
+    const size_t np = idx->sync.size();
+    size_t a = 0;
+    while (a + 1 < np && idx->off[a + 1] <= d_off) ++a;
+    size_t b = a;
+    while (b + 1 < np && idx->off[b + 1] < d_off + len) ++b;
+    const MemberInfo& mi = idx->info[0];
+    FileDesc F{};
+    F.gz = idx->gz;
+    F.gz_len = idx->gz_len;
+    F.out = out;
+    F.out_cap = len;
+    F.s0_bit = mi.s0 * 8;
+    F.end_bit = (idx->gz_len - 8) * 8;
+    F.mode = 2;
+    F.out_base = idx->off[a];
+    F.out_lo = d_off;
+    F.out_hi = d_off + len;
+    F.chunk0 = (int32_t)P.chunks.size();
+    F.nchunks = (int32_t)(b - a + 1);
+    F.group0 = (int32_t)P.g0.size();
+    F.ngroups = 0;
+    for (size_t k = a; k <= b; ++k) {
+        ChunkDesc C{};
+        C.lo = idx->sync[k];
+        C.hi = idx->sync[k] + 1;
+        C.file = (int32_t)P.files.size();
+        C.index = (int32_t)k;
+        C.given = 1;
+        C.stop_hint = (k == b) ? idx->stop[k] : kNone;
+        C.sync = kNone;
+        C.cap = round_up(idx->n[k] + 8, 8);
+        wins.emplace_back(P.chunks.size(), k);
+        P.chunks.push_back(C);
+    }
+    P.files.push_back(F);
+}
+
+void copy_range_windows(Plan& P, const pgz_index* idx, const std::vector<std::pair<size_t, size_t>>& wins,
+                        cudaStream_t s) {
+    for (const auto& w : wins)
+        cudaMemcpyAsync(P.d_windows.as<uint8_t>() + w.first * kWin, idx->windows.as<uint8_t>() + w.second * kWin, kWin,
+                        cudaMemcpyDeviceToDevice, s);
+}
+
 void begin_plan(Plan& P) {
     P.files.clear();
     P.chunks.clear();
@@ -531,6 +583,147 @@ void begin_plan(Plan& P) {
 bool aligned4(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3) == 0; }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// serving state
+// ---------------------------------------------------------------------------
+namespace {
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct SrvFile {
+    const uint8_t* gz = nullptr;
+    uint64_t gz_len = 0;
+    MemberInfo mi{};
+    uint64_t d_est = 0;          // decompressed size bound used for charging (ISIZE is exact below 4 GiB)
+    pgz_index* idx = nullptr;    // part starts and resolved windows, built by the first range request
+};
+
+struct SrvSlot {
+    pgz_ctx* ctx = nullptr;      // own stream, plan and scratch
+    cudaEvent_t done = nullptr;  // recorded after the run's last operation
+    bool busy = false;
+    uint64_t charged = 0;
+    std::vector<pgz_request*> reqs;
+};
+
+constexpr int kServerMaxBatch = 256;   // requests in one run
+
+}  // namespace
+
+struct pgz_server {
+    pgz_config cfg{};
+    uint64_t budget = 0, in_use = 0;
+    std::vector<SrvFile> files;
+    std::vector<SrvSlot> slots;
+    std::deque<pgz_request*> queue;
+};
+
+namespace {
+
+uint64_t request_cost(const pgz_server* S, const pgz_request* r) {
+    const SrvFile& f = S->files[(size_t)r->file];
+    if (r->whole) return f.gz_len + 3 * f.d_est;
+    // the parts covering the range: about the range plus two parts of output
+    const uint64_t csize = std::max<uint64_t>(1, f.gz_len - 8 - f.mi.s0);
+    const uint64_t part_out = f.d_est / std::max<uint64_t>(1, (csize + S->cfg.chunk_bytes - 1) / std::max<uint64_t>(1, S->cfg.chunk_bytes));
+    return 3 * (r->length + 2 * part_out) + 2 * S->cfg.chunk_bytes;
+}
+
+void complete(pgz_request* r, int status, uint64_t n, int* n_done) {
+    r->status = status;
+    r->out_len = n;
+    r->t_done = now_s();
+    if (n_done) ++*n_done;
+}
+
+// one run of the pass kernels over the requests of `batch` on slot s (asynchronous)
+int launch_slot(pgz_server* S, SrvSlot& sl, std::vector<pgz_request*>& batch, int* n_done) {
+    pgz_ctx* ctx = sl.ctx;
+    // range requests need their member's index (a full decode, once per member)
+    std::vector<pgz_request*> ok;
+    for (pgz_request* r : batch) {
+        SrvFile& f = S->files[(size_t)r->file];
+        if (!r->whole && !f.idx) {
+            const int e = pgz_index_build(ctx, f.gz, f.gz_len, &f.idx);
+            if (e) {
+                complete(r, e, 0, n_done);
+                continue;
+            }
+        }
+        if (!r->whole && (r->offset > f.idx->total || r->length > f.idx->total - r->offset)) {
+            complete(r, PGZ_E_ARG, 0, n_done);
+            continue;
+        }
+        if (!r->whole && r->length == 0) {
+            complete(r, PGZ_OK, 0, n_done);
+            continue;
+        }
+        ok.push_back(r);
+    }
+    batch.swap(ok);
+    if (batch.empty()) return PGZ_OK;
+    Plan& P = ctx->plan;
+    begin_plan(P);
+    std::vector<std::vector<std::pair<size_t, size_t>>> wins(batch.size());
+    bool any_whole = false;
+    for (size_t k = 0; k < batch.size(); ++k) {
+        pgz_request* r = batch[k];
+        const SrvFile& f = S->files[(size_t)r->file];
+        if (r->whole) {
+            plan_member(ctx, P, f.gz, f.gz_len, r->out, r->out_cap, f.mi, 0);
+            any_whole = true;
+        } else {
+            plan_range(P, f.idx, r->offset, r->length, r->out, wins[k]);
+        }
+    }
+    P.chain = any_whole;
+    P.wpb = ctx->kp.wpb;
+    reset_results(P);
+    int e = layout(P);
+    if (!e && cuda_status(P.d_windows.ensure(P.chunks.size() * (size_t)kWin))) e = PGZ_E_NOMEM;
+    if (!e) {
+        upload_static(P, ctx->stream);
+        for (size_t k = 0; k < batch.size(); ++k)
+            if (!batch[k]->whole) copy_range_windows(P, S->files[(size_t)batch[k]->file].idx, wins[k], ctx->stream);
+        e = enqueue(ctx, P, ctx->stream, false);
+    }
+    if (!e && cudaEventRecord(sl.done, ctx->stream) != cudaSuccess) e = PGZ_E_CUDA;
+    if (e) {
+        for (pgz_request* r : batch) complete(r, e, 0, n_done);
+        return e;
+    }
+    const double t = now_s();
+    for (pgz_request* r : batch) r->t_start = t;
+    sl.reqs = batch;
+    sl.busy = true;
+    return PGZ_OK;
+}
+
+// results of a finished run; a run that needs recovery (false start, capacity) is re-run to completion here
+void finish_slot(pgz_server* S, SrvSlot& sl, int* n_done) {
+    pgz_ctx* ctx = sl.ctx;
+    Plan& P = ctx->plan;
+    const FileDesc* hf = P.h_files.as<FileDesc>();
+    bool again = false;
+    for (size_t f = 0; f < P.files.size(); ++f)
+        if (hf[f].bad_chunk != 0xffffffffu) again = true;
+    if (again) execute(ctx, P, nullptr);
+    for (size_t k = 0; k < sl.reqs.size(); ++k) {
+        pgz_request* r = sl.reqs[k];
+        const int st = (int)hf[k].status;
+        complete(r, st, st == PGZ_OK ? (r->whole ? hf[k].total : r->length) : (r->whole ? hf[k].total : 0), n_done);
+    }
+    S->in_use -= sl.charged;
+    sl.charged = 0;
+    sl.reqs.clear();
+    sl.busy = false;
+}
+
+}  // namespace
+
 
 // ---------------------------------------------------------------------------
 // C ABI
@@ -964,51 +1157,17 @@ int pgz_decompress_range(pgz_ctx* ctx, const pgz_index* idx, uint64_t d_off, uin
     if (d_off > idx->total || len > idx->total - d_off) return PGZ_E_ARG;
     if (len == 0) return PGZ_OK;
     cudaSetDevice(ctx->cfg.device);
-    // parts covering [d_off, d_off + len)
-    const size_t np = idx->sync.size();
-    size_t a = 0;
-    while (a + 1 < np && idx->off[a + 1] <= d_off) ++a;
-    size_t b = a;
-    while (b + 1 < np && idx->off[b + 1] < d_off + len) ++b;
     Plan& P = ctx->plan;
     begin_plan(P);
-    const MemberInfo& mi = idx->info[0];
-    FileDesc F{};
-    F.gz = idx->gz;
-    F.gz_len = idx->gz_len;
-    F.out = out;
-    F.out_cap = len;
-    F.s0_bit = mi.s0 * 8;
-    F.end_bit = (idx->gz_len - 8) * 8;
-    F.mode = 2;
-    F.out_base = idx->off[a];
-    F.out_lo = d_off;
-    F.out_hi = d_off + len;
-    F.chunk0 = 0;
-    F.nchunks = (int32_t)(b - a + 1);
-    F.group0 = 0;
-    F.ngroups = 0;
-    P.files.push_back(F);
-    for (size_t k = a; k <= b; ++k) {
-        ChunkDesc C{};
-        C.lo = idx->sync[k];
-        C.hi = idx->sync[k] + 1;
-        C.index = (int32_t)k;
-        C.given = 1;
-        C.stop_hint = (k == b) ? idx->stop[k] : kNone;
-        C.sync = kNone;
-        C.cap = round_up(idx->n[k] + 8, 8);
-        P.chunks.push_back(C);
-    }
+    std::vector<std::pair<size_t, size_t>> wins;
+    plan_range(P, idx, d_off, len, out, wins);
     P.chain = false;
     P.crc = false;
+    P.wpb = ctx->kp.wpb;
     int e = layout(P);
     if (e) return e;
-    // the windows of these parts come from the index
     if (cuda_status(P.d_windows.ensure(P.chunks.size() * (size_t)kWin))) return PGZ_E_NOMEM;
-    for (size_t k = a; k <= b; ++k)
-        cudaMemcpyAsync(P.d_windows.as<uint8_t>() + (k - a) * kWin, idx->windows.as<uint8_t>() + k * kWin, kWin,
-                        cudaMemcpyDeviceToDevice, ctx->stream);
+    copy_range_windows(P, idx, wins, ctx->stream);
     e = execute(ctx, P, nullptr);
     return e;
 }
@@ -1071,6 +1230,143 @@ int pgz_autotune(pgz_ctx* ctx, pgz_job* jobs, int n_jobs, const uint64_t* chunk_
     ctx->kp.wpb = pick.warps_per_block;
     if (best) *best = pick;
     return PGZ_OK;
+}
+
+int pgz_server_create(pgz_server** out, const pgz_config* cfg, int slots, uint64_t mem_budget) {
+    if (!out || !cfg || slots < 1 || slots > 64) return PGZ_E_ARG;
+    *out = nullptr;
+    pgz_server* S = new (std::nothrow) pgz_server();
+    if (!S) return PGZ_E_NOMEM;
+    S->cfg = *cfg;
+    S->budget = mem_budget;
+    S->slots.resize((size_t)slots);
+    for (SrvSlot& sl : S->slots) {
+        pgz_config c = *cfg;
+        c.cuda_stream = nullptr;
+        int e = pgz_create(&sl.ctx, &c);
+        cudaStream_t st = nullptr;
+        if (!e && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) e = PGZ_E_CUDA;
+        if (!e) sl.ctx->stream = st;
+        if (!e && cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) e = PGZ_E_CUDA;
+        if (e) {
+            pgz_server_destroy(S);
+            return e;
+        }
+    }
+    *out = S;
+    return PGZ_OK;
+}
+
+int pgz_server_add_file(pgz_server* S, const uint8_t* gz, uint64_t gz_len, int* file) {
+    if (!S || !gz || !file || !aligned4(gz)) return PGZ_E_ARG;
+    pgz_ctx* ctx = S->slots[0].ctx;
+    cudaSetDevice(ctx->cfg.device);
+    SrvFile f;
+    f.gz = gz;
+    f.gz_len = gz_len;
+    const int e = read_member(ctx, gz, gz_len, &f.mi);
+    if (e) return e;
+    f.d_est = std::max<uint64_t>(f.mi.isize, gz_len < (1ull << 31) ? 0 : 2 * gz_len);
+    *file = (int)S->files.size();
+    S->files.push_back(f);
+    return PGZ_OK;
+}
+
+int pgz_server_submit(pgz_server* S, pgz_request* r) {
+    if (!S || !r || r->file < 0 || r->file >= (int)S->files.size() || (!r->out && (r->whole || r->length)))
+        return PGZ_E_ARG;
+    if (!r->whole && r->out_cap < r->length) return PGZ_E_ARG;
+    r->status = -1;
+    r->out_len = 0;
+    r->t_submit = now_s();
+    r->t_start = r->t_done = 0;
+    S->queue.push_back(r);
+    return PGZ_OK;
+}
+
+int pgz_server_poll(pgz_server* S, int* n_done) {
+    if (!S) return PGZ_E_ARG;
+    if (n_done) *n_done = 0;
+    cudaSetDevice(S->cfg.device);
+    for (SrvSlot& sl : S->slots) {
+        if (!sl.busy) continue;
+        const cudaError_t q = cudaEventQuery(sl.done);
+        if (q == cudaErrorNotReady) continue;
+        if (q != cudaSuccess) return PGZ_E_CUDA;
+        finish_slot(S, sl, n_done);
+    }
+    // the queue is spread over the free slots (each run takes its share of the queued requests and at most
+    // budget / slots of scratch), so the runs of several slots are on the GPU at once
+    int free_slots = 0;
+    for (const SrvSlot& sl : S->slots) free_slots += sl.busy ? 0 : 1;
+    const uint64_t run_cap = S->budget ? std::max<uint64_t>(1, S->budget / S->slots.size()) : 0;
+    for (SrvSlot& sl : S->slots) {
+        if (sl.busy) continue;
+        if (S->queue.empty()) break;
+        const int share = std::max(1, (int)((S->queue.size() + free_slots - 1) / std::max(1, free_slots)));
+        --free_slots;
+        std::vector<pgz_request*> batch;
+        uint64_t charge = 0;
+        while (!S->queue.empty() && (int)batch.size() < std::min(kServerMaxBatch, share)) {
+            pgz_request* r = S->queue.front();
+            const uint64_t c = request_cost(S, r);
+            if (S->budget && c > S->budget) {                // can never be admitted
+                S->queue.pop_front();
+                complete(r, PGZ_E_NOMEM, 0, n_done);
+                continue;
+            }
+            if (S->budget && S->in_use + charge + c > S->budget) break;
+            if (run_cap && !batch.empty() && charge + c > run_cap) break;
+            S->queue.pop_front();
+            batch.push_back(r);
+            charge += c;
+        }
+        if (batch.empty()) break;                            // the budget is taken by running requests
+        sl.charged = charge;
+        S->in_use += charge;
+        if (launch_slot(S, sl, batch, n_done) != PGZ_OK || !sl.busy) {
+            S->in_use -= charge;
+            sl.charged = 0;
+        }
+    }
+    return PGZ_OK;
+}
+
+int pgz_server_pending(const pgz_server* S) {
+    if (!S) return 0;
+    int n = (int)S->queue.size();
+    for (const SrvSlot& sl : S->slots) n += (int)sl.reqs.size();
+    return n;
+}
+
+int pgz_server_drain(pgz_server* S) {
+    if (!S) return PGZ_E_ARG;
+    for (;;) {
+        const int e = pgz_server_poll(S, nullptr);
+        if (e) return e;
+        if (pgz_server_pending(S) == 0) return PGZ_OK;
+        for (SrvSlot& sl : S->slots)                         // wait for one run instead of spinning
+            if (sl.busy) {
+                cudaEventSynchronize(sl.done);
+                break;
+            }
+    }
+}
+
+void pgz_server_destroy(pgz_server* S) {
+    if (!S) return;
+    for (SrvSlot& sl : S->slots) {
+        if (sl.ctx) {
+            cudaSetDevice(sl.ctx->cfg.device);
+            cudaStream_t st = sl.ctx->stream;
+            pgz_destroy(sl.ctx);
+            if (st) cudaStreamDestroy(st);
+        }
+        if (sl.done) cudaEventDestroy(sl.done);
+    }
+    for (SrvFile& f : S->files)
+        if (f.idx) pgz_index_free(f.idx);
+    delete S;
 }
 
 const char* pgz_strerror(int status) {

@@ -49,6 +49,12 @@ class pgz_tune_entry(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class pgz_request(ctypes.Structure):
+    _fields_ = [("file", ctypes.c_int), ("whole", ctypes.c_int), ("offset", U64), ("length", U64), ("out", VP),
+                ("out_cap", U64), ("status", ctypes.c_int), ("out_len", U64), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
 class pgz_job(ctypes.Structure):
     _fields_ = [("gz", VP), ("gz_len", U64), ("out", VP), ("out_cap", U64), ("out_len", U64),
                 ("status", ctypes.c_int)]
@@ -87,6 +93,13 @@ def _load():
         "pgz_decompress_noalloc": (ctypes.c_int, [VP, U64, VP, U64, P(U64), VP]),
         "pgz_autotune": (ctypes.c_int, [VP, P(pgz_job), ctypes.c_int, P(U64), ctypes.c_int, P(ctypes.c_int),
                                         ctypes.c_int, ctypes.c_int, P(pgz_tune_entry), P(pgz_tune_entry)]),
+        "pgz_server_create": (ctypes.c_int, [P(VP), P(pgz_config), ctypes.c_int, U64]),
+        "pgz_server_add_file": (ctypes.c_int, [VP, VP, U64, P(ctypes.c_int)]),
+        "pgz_server_submit": (ctypes.c_int, [VP, P(pgz_request)]),
+        "pgz_server_poll": (ctypes.c_int, [VP, P(ctypes.c_int)]),
+        "pgz_server_drain": (ctypes.c_int, [VP]),
+        "pgz_server_pending": (ctypes.c_int, [VP]),
+        "pgz_server_destroy": (None, [VP]),
         "pgz_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
@@ -110,7 +123,8 @@ EXPORTED = ["pgz_config_init", "pgz_create", "pgz_destroy", "pgz_decompress", "p
             "pgz_decompress_at", "pgz_decompress_batch", "pgz_batch_prepare", "pgz_batch_run", "pgz_batch_free",
             "pgz_index_build", "pgz_index_info", "pgz_decompress_range", "pgz_index_free", "pgz_inspect_parts",
             "pgz_inspect_symbols", "pgz_inspect_window", "pgz_kernel_launches", "pgz_strerror",
-            "pgz_decompress_noalloc", "pgz_autotune"]
+            "pgz_decompress_noalloc", "pgz_autotune", "pgz_server_create", "pgz_server_add_file",
+            "pgz_server_submit", "pgz_server_poll", "pgz_server_drain", "pgz_server_pending", "pgz_server_destroy"]
 
 
 def pgz_strerror(status: int) -> str:
@@ -218,6 +232,57 @@ def pgz_autotune(ctx: int, jobs, chunk_bytes, warps_per_block, reps: int = 3):
     r = lib().pgz_autotune(ctx, arr, len(jobs), cb, len(chunk_bytes), wp, len(warps_per_block), reps, ent,
                            ctypes.byref(best))
     return r, [e.as_dict() for e in ent], best.as_dict()
+
+
+class Server:
+    """pgz_server_*: submitted requests are kept alive here until they are done."""
+
+    def __init__(self, cfg: pgz_config, slots: int = 4, mem_budget: int = 0):
+        h = VP()
+        r = lib().pgz_server_create(ctypes.byref(h), ctypes.byref(cfg), slots, mem_budget)
+        if r:
+            raise PgzError(r, "pgz_server_create")
+        self.h = h.value
+        self.live = []
+
+    def add_file(self, gz_ptr: int, gz_len: int) -> int:
+        f = ctypes.c_int(-1)
+        r = lib().pgz_server_add_file(self.h, gz_ptr, gz_len, ctypes.byref(f))
+        if r:
+            raise PgzError(r, "pgz_server_add_file")
+        return f.value
+
+    def submit(self, file: int, out_ptr: int, out_cap: int, offset: int = 0, length: int | None = None):
+        """A whole member (length None) or the byte range [offset, offset + length); returns the request."""
+        req = pgz_request(file=file, whole=1 if length is None else 0, offset=offset, length=length or 0,
+                          out=out_ptr, out_cap=out_cap)
+        r = lib().pgz_server_submit(self.h, ctypes.byref(req))
+        if r:
+            raise PgzError(r, "pgz_server_submit")
+        self.live.append(req)
+        return req
+
+    def poll(self) -> int:
+        n = ctypes.c_int(0)
+        r = lib().pgz_server_poll(self.h, ctypes.byref(n))
+        if r:
+            raise PgzError(r, "pgz_server_poll")
+        self.live = [q for q in self.live if q.status < 0]
+        return n.value
+
+    def drain(self):
+        r = lib().pgz_server_drain(self.h)
+        if r:
+            raise PgzError(r, "pgz_server_drain")
+        self.live = []
+
+    def pending(self) -> int:
+        return lib().pgz_server_pending(self.h)
+
+    def close(self):
+        if self.h:
+            lib().pgz_server_destroy(self.h)
+            self.h = None
 
 
 def pgz_index_build(ctx: int, gz_ptr: int, gz_len: int) -> int:
