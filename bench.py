@@ -187,7 +187,8 @@ def run_pgz(args, rank, world):
     # ---- batched: every file of the step in one graph-captured run of the pass kernels, with the part size
     # and pass-1 CTA shape chosen by the library's autotuner on these files (unless --chunk-bytes fixes them)
     ctx_b = pgz.pgz_create(pgz.pgz_config_init(device=dev, cuda_stream=stream.cuda_stream, n_chunks=0,
-                                               chunk_bytes=args.chunk_bytes or CHUNK_BYTES))
+                                               chunk_bytes=args.chunk_bytes or CHUNK_BYTES,
+                                               warps_per_block=args.warps_per_block))
     tune = None
     if not args.chunk_bytes:
         st, entries, best = pgz.pgz_autotune(ctx_b, jobs, TUNE_CHUNKS, TUNE_WPB, 2)
@@ -196,7 +197,7 @@ def run_pgz(args, rank, world):
         tune = {"best": [best["chunk_bytes"], best["warps_per_block"]],
                 "ms": {f"{e['chunk_bytes'] >> 10}K/{e['warps_per_block']}w": round(e["ms"], 2) for e in entries}}
     chunk_bytes = tune["best"][0] if tune else args.chunk_bytes
-    wpb = tune["best"][1] if tune else 4
+    wpb = tune["best"][1] if tune else args.warps_per_block
     batch = pgz.Batch(ctx_b, jobs)
 
     def step_batched():
@@ -584,7 +585,7 @@ def run_reference(args):
             "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def run_profile_case(spec: str, chunk_bytes: int):
+def run_profile_case(spec: str, chunk_bytes: int, wpb: int = 4):
     """--profile-case MIB:LEVEL:CALLS -- a small fixed case for ncu captures: one synthetic FASTQ file
     (150 bp, seed 1) of MIB MiB at gzip LEVEL, decompressed CALLS times through pgz_decompress on device
     buffers; the output of the last call is checked byte for byte and its stage times printed."""
@@ -597,7 +598,7 @@ def run_profile_case(spec: str, chunk_bytes: int):
     gz = synth.gzip_compress(raw, level)
     stream = torch.cuda.current_stream()
     ctx = pgz.pgz_create(pgz.pgz_config_init(device=0, cuda_stream=stream.cuda_stream, n_chunks=0,
-                                             chunk_bytes=chunk_bytes))
+                                             chunk_bytes=chunk_bytes, warps_per_block=wpb))
     d_in = torch.from_numpy(np.frombuffer(gz, dtype=np.uint8).copy()).cuda()
     d_out = torch.empty(len(raw) + 4096, dtype=torch.uint8, device="cuda")
     for _ in range(calls):
@@ -622,11 +623,14 @@ def main():
                     help="fastq256: the benchmark; fastq4g: autotuner sweep on 4 GiB; batch512: 512 members; "
                          "served: request loop at three offered loads")
     ap.add_argument("--chunk-bytes", type=int, default=0, help="fixed part size (default: autotuned)")
+    ap.add_argument("--warps-per-block", type=int, default=4, choices=[2, 4, 8],
+                    help="pass-1 CTA shape with a fixed --chunk-bytes or --profile-case")
     ap.add_argument("--profile-case", default=None, metavar="MIB:LEVEL:CALLS",
                     help="run one small checked case for an ncu capture and print its stage times")
     args = ap.parse_args()
     if args.profile_case:
-        print(json.dumps(run_profile_case(args.profile_case, args.chunk_bytes or CHUNK_BYTES)), flush=True)
+        print(json.dumps(run_profile_case(args.profile_case, args.chunk_bytes or CHUNK_BYTES, args.warps_per_block)),
+              flush=True)
         return
     args.warmup = max(3, args.warmup)
     if args.workload in ("fastq4g", "batch512", "served") and args.impl == "pgz":

@@ -92,7 +92,7 @@ struct WarpSmem {
     uint8_t lens[320];
     uint8_t cllens[32];
     uint32_t masks[32 * 32];   // parallel decoding: token starts in the first 1024 bits of each lane's segment;
-                               // reused by exec_range: words 0-511 a position -> token map (1024 entries),
+                               // reused by exec_range: words 0-255 the entries of one pass of 256 positions,
                                // 512-767 the batch's tokens, 768-1023 their output offsets
 };
 
@@ -786,12 +786,12 @@ __device__ uint32_t seg_next(const WarpSmem& S, BitIn& b, bool active, uint64_t 
 }
 
 // Writes up to 256 consecutive tokens of the block (lane j loads tokens
-// 8j..8j+7).  Output positions are spread over the lanes; a position inside a
-// match follows the copy to its source, resolved through the batch's tokens
-// in shared memory (a position -> token map for the first 1024 positions,
-// binary search beyond) until it reaches a literal or a position before the
-// batch (already final in the part's output, or a placeholder before the part
-// start).  Loads of four positions per lane are in flight together.
+// 8j..8j+7).  Output positions go in passes of 256, lane l taking 8
+// consecutive ones (one 16-byte store); a position inside a match takes its
+// source: a source before the pass (the part's output so far,
+// or a placeholder U_j before the part start) is loaded; a source inside the
+// pass is resolved by pointer jumping over the pass's entries in shared memory
+// (overlapping copies included, with no division).
 __device__ __forceinline__ int exec_range(WarpSmem& S, OutState& o, const uint32_t* tks, uint32_t ntok, bool check,
                                           uint64_t& block_n, int lane) {
     uint32_t t[8], L[8], sum = 0;
@@ -818,9 +818,10 @@ __device__ __forceinline__ int exec_range(WarpSmem& S, OutState& o, const uint32
             if (L[i] && !(t[i] >> 31) && !allowed_has(S.allowed, t[i] & 0xffu)) bad = true;
         if (__any_sync(FULL, bad)) return CE_BYTE;
     }
-    uint16_t* map = reinterpret_cast<uint16_t*>(S.masks);
-    uint32_t* tokS = S.masks + 512;
-    uint32_t* stS = S.masks + 768;
+    if (total == 0) return CE_OK;
+    uint32_t* stage = S.masks;                             // 256 entries: the positions of one pass
+    uint32_t* tokS = S.masks + 512;                        // the batch's tokens
+    uint32_t* stS = S.masks + 768;                         // their output offsets from base
     uint32_t s0 = incl - sum;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -828,80 +829,96 @@ __device__ __forceinline__ int exec_range(WarpSmem& S, OutState& o, const uint32
         if (idx < ntok) {
             tokS[idx] = t[i];
             stS[idx] = s0;
-            const uint32_t e = s0 + L[i] < 1024u ? s0 + L[i] : 1024u;
-            for (uint32_t x = s0; x < e; ++x) map[x] = (uint16_t)idx;
         }
         s0 += L[i];
     }
     __syncwarp();
     uint16_t* out = o.sym;
     bool bad = false;
-    constexpr int U = 8;                                   // positions per lane in flight
-    for (uint32_t r0 = 0; r0 < total; r0 += 32u * U) {
-        uint32_t rel[U], val[U];
-        int32_t src[U];
-        uint32_t need = 0;                                 // bit u: position u not resolved yet
+    const uint32_t end = base + total;
+    // passes over [A, A + 256) with A a multiple of 8; lane l takes positions A + 8l .. A + 8l + 7.  A source
+    // before max(A, base) is final (earlier passes, earlier batches, or a placeholder before the part start)
+    // and is loaded; a source inside the pass is a pointer to its stage entry, strictly earlier, so pointer
+    // jumping (each entry replaced by the entry it points to) ends with every entry a symbol.  An entry is
+    // 0x10000 | symbol when resolved, else the pass index of its source.
+    for (uint32_t A = base & ~7u; A < end; A += 256u) {
+        const uint32_t p0 = A + 8u * (uint32_t)lane;
+        const uint32_t lo_pos = A > base ? A : base;       // first position of the pass that is this batch's
+        uint32_t e[8];
+        uint32_t open = 0;                                 // bit u: e[u] still a pointer
+        if (p0 + 8u > base && p0 < end) {
+            const uint32_t r0 = (p0 > base ? p0 : base) - base;
+            uint32_t lo = 0, hi = ntok - 1;                // last token starting at or before r0
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi + 1) >> 1;
+                if (stS[mid] <= r0) lo = mid;
+                else hi = mid - 1;
+            }
+            uint32_t ti = lo;
+            uint32_t next = ti + 1 < ntok ? stS[ti + 1] : 0xffffffffu;
+            uint32_t tk = tokS[ti];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            rel[u] = r0 + 32u * u + (uint32_t)lane;
-            src[u] = INT32_MIN;
-            val[u] = 0;
-            if (rel[u] < total) need |= 1u << u;
-        }
-        // one hop per pass for every unresolved position: a literal ends the chain,
-        // a source before the batch ends it with a load, else continue at the
-        // source (strictly earlier in the batch, so every chain ends)
-        while (need) {
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (!((need >> u) & 1u)) continue;
-                uint32_t ti;
-                if (rel[u] < 1024u) {
-                    ti = map[rel[u]];
-                } else {                                   // binary search over the starts
-                    uint32_t lo = 0, hi = ntok - 1;
-                    while (lo < hi) {
-                        const uint32_t mid = (lo + hi + 1) >> 1;
-                        if (stS[mid] <= rel[u]) lo = mid;
-                        else hi = mid - 1;
-                    }
-                    ti = lo;
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t P = p0 + (uint32_t)u;
+                e[u] = 0x10000u;
+                if (P < base || P >= end) continue;
+                if (P - base >= next) {                    // the next token (tokens are at least 1 long)
+                    ++ti;
+                    next = ti + 1 < ntok ? stS[ti + 1] : 0xffffffffu;
+                    tk = tokS[ti];
                 }
-                const uint32_t tk = tokS[ti];
                 if (!(tk >> 31)) {
-                    val[u] = tk & 0xffu;
-                    need &= ~(1u << u);
+                    e[u] = 0x10000u | (tk & 0xffu);
                     continue;
                 }
-                const uint32_t sk = stS[ti], dk = (tk & 0xffffu) + 1u;
-                int32_t q = (int32_t)rel[u] - (int32_t)dk;
-                if (q >= (int32_t)sk) q = (int32_t)sk - (int32_t)dk + (int32_t)((rel[u] - sk) % dk);
-                if (q < 0) {
-                    src[u] = (int32_t)base + q;
-                    need &= ~(1u << u);
+                const int32_t src = (int32_t)P - (int32_t)((tk & 0xffffu) + 1u);
+                if (src < (int32_t)lo_pos) {
+                    if (src < 0) {
+                        if (o.known) bad = true;
+                        o.neg = true;
+                    }
+                    e[u] = 0x10000u | sym_at(out, src);
                 } else {
-                    rel[u] = (uint32_t)q;
+                    e[u] = (uint32_t)src - A;
+                    open |= 1u << u;
                 }
             }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) e[u] = 0x10000u;
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (src[u] != INT32_MIN) {
-                if (src[u] < 0) {
-                    if (o.known) bad = true;
-                    o.neg = true;
+        for (int u = 0; u < 8; ++u) stage[8u * lane + u] = e[u];
+        __syncwarp();
+        while (__any_sync(FULL, open != 0)) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if ((open >> u) & 1u) e[u] = stage[e[u]];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if ((open >> u) & 1u) {
+                    stage[8u * lane + u] = e[u];
+                    if (e[u] & 0x10000u) open &= ~(1u << u);
                 }
-                val[u] = sym_at(out, src[u]);
+            __syncwarp();
+        }
+        if (p0 >= base && p0 + 8u <= end) {                // all 8 mine: one 16-byte store
+            uint4 v;
+            v.x = (e[0] & 0xffffu) | (e[1] << 16);
+            v.y = (e[2] & 0xffffu) | (e[3] << 16);
+            v.z = (e[4] & 0xffffu) | (e[5] << 16);
+            v.w = (e[6] & 0xffffu) | (e[7] << 16);
+            *reinterpret_cast<uint4*>(out + p0) = v;
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t P = p0 + (uint32_t)u;
+                if (P >= base && P < end) out[P] = (uint16_t)e[u];
             }
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const uint32_t p = r0 + 32u * u + (uint32_t)lane;
-            if (p < total) out[base + p] = (uint16_t)val[u];
-        }
+        __syncwarp();                                      // this pass is final for the next one
     }
     if (__any_sync(FULL, bad)) return CE_DIST;
-    __syncwarp();
     o.n = base + total;
     block_n += total;
     return CE_OK;
