@@ -592,6 +592,8 @@ def run_profile_case(spec: str, chunk_bytes: int, wpb: int = 4):
     import numpy as np
     import torch
     from paper_1905_07224_gb300 import build, pgz, synth
+    if spec.startswith("batch:"):
+        return run_profile_batch(int(spec.split(":")[1]), chunk_bytes, wpb)
     mib, level, calls = (int(x) for x in spec.split(":"))
     build.build()
     raw = synth.fastq(mib << 20, 150, 0.001, 1)
@@ -613,6 +615,33 @@ def run_profile_case(spec: str, chunk_bytes: int, wpb: int = 4):
             **{k: (round(v, 3) if isinstance(v, float) else v) for k, v in s.items()}}
 
 
+def run_profile_batch(calls: int, chunk_bytes: int, wpb: int):
+    """--profile-case batch:CALLS -- the benchmark's two files decoded together by pgz_decompress_batch (the
+    batched form without the graph), CALLS times; outputs checked."""
+    import numpy as np
+    import torch
+    from paper_1905_07224_gb300 import build, pgz
+    build.build()
+    files, desc = make_workload("fastq256")
+    stream = torch.cuda.current_stream()
+    ctx = pgz.pgz_create(pgz.pgz_config_init(device=0, cuda_stream=stream.cuda_stream, n_chunks=0,
+                                             chunk_bytes=chunk_bytes, warps_per_block=wpb))
+    d_in = [torch.from_numpy(np.frombuffer(g, dtype=np.uint8).copy()).cuda() for _, _, g in files]
+    d_out = [torch.empty(len(r) + 4096, dtype=torch.uint8, device="cuda") for _, r, _ in files]
+    jobs = [(d_in[k].data_ptr(), len(g), d_out[k].data_ptr(), d_out[k].numel()) for k, (_, _, g) in enumerate(files)]
+    for _ in range(calls):
+        r, res, s = pgz.pgz_decompress_batch(ctx, jobs, stats=True)
+        if r != 0:
+            raise RuntimeError(f"pgz_decompress_batch failed: {pgz.pgz_strerror(r)}")
+    torch.cuda.synchronize()
+    for k, (_, raw, _) in enumerate(files):
+        if d_out[k][:len(raw)].cpu().numpy().tobytes() != raw:
+            raise RuntimeError("output mismatch")
+    pgz.pgz_destroy(ctx)
+    return {"case": desc + " (batched)", "chunk_bytes": chunk_bytes, "warps_per_block": wpb,
+            **{k: (round(v, 3) if isinstance(v, float) else v) for k, v in s.items()}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -625,8 +654,9 @@ def main():
     ap.add_argument("--chunk-bytes", type=int, default=0, help="fixed part size (default: autotuned)")
     ap.add_argument("--warps-per-block", type=int, default=4, choices=[2, 4, 8],
                     help="pass-1 CTA shape with a fixed --chunk-bytes or --profile-case")
-    ap.add_argument("--profile-case", default=None, metavar="MIB:LEVEL:CALLS",
-                    help="run one small checked case for an ncu capture and print its stage times")
+    ap.add_argument("--profile-case", default=None, metavar="MIB:LEVEL:CALLS|batch:CALLS",
+                    help="run one checked case for an ncu capture and print its stage times: one FASTQ file, or "
+                         "the benchmark's two files as one batch")
     args = ap.parse_args()
     if args.profile_case:
         print(json.dumps(run_profile_case(args.profile_case, args.chunk_bytes or CHUNK_BYTES, args.warps_per_block)),
