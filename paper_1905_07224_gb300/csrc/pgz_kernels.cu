@@ -823,17 +823,22 @@ __device__ __forceinline__ int exec_range(WarpSmem& S, OutState& o, const uint32
     uint32_t* tokS = S.masks + 512;                        // the batch's tokens
     uint32_t* stS = S.masks + 768;                         // their output offsets from base
     uint32_t s0 = incl - sum;
+    uint16_t* out = o.sym;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const uint32_t idx = 8u * lane + i;
         if (idx < ntok) {
             tokS[idx] = t[i];
             stS[idx] = s0;
+            // a match's source before the batch is final already: bring its line toward L2 now, so the
+            // passes below find it there
+            const int32_t src = (int32_t)(base + s0) - (int32_t)((t[i] & 0xffffu) + 1u);
+            if ((t[i] >> 31) && src >= 0 && (uint32_t)src < base)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(out + src));
         }
         s0 += L[i];
     }
     __syncwarp();
-    uint16_t* out = o.sym;
     bool bad = false;
     const uint32_t end = base + total;
     // passes over [A, A + 256) with A a multiple of 8; lane l takes positions A + 8l .. A + 8l + 7.  A source
@@ -1099,10 +1104,11 @@ __device__ int one_block(WarpSmem& S, uint32_t* tokbuf, BitIn& br, OutState& o, 
 //     32 offsets of a lane;
 //  2. the code-length code is complete: sum of 2^-l over its lengths is 1,
 //     from a 512-entry table of three-field sums;
-//  3. the whole dynamic header is valid (read_dynamic<true>), one offset at a
-//     time by the whole warp, lowest offset first.
-// The full block decode then follows in k_sync.  Stages 1-3 are implied by
-// the complete checks, so no offset that passes those is dropped here.
+//  3. the whole dynamic header is valid (the checks of read_dynamic<true>),
+//     32 listed offsets at a time, one per lane (hdr_ok_lane).
+// The full block decode then follows in k_sync, lowest offset first.  Stages
+// 1-3 are implied by the complete checks, so no offset that passes those is
+// dropped here.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t fsr(uint32_t lo, uint32_t hi, uint32_t s) { return __funnelshift_r(lo, hi, s); }
 
@@ -1125,44 +1131,191 @@ __device__ uint32_t cl_complete(const uint16_t* kraft3, uint32_t w0, uint32_t w1
     return kr == 128u;
 }
 
-__device__ uint64_t find_candidate(WarpSmem& S, const uint16_t* kraft3, const FileDesc& F, uint64_t lo, uint64_t hi,
-                                   int lane) {
+// The whole dynamic-header check of one candidate by one lane, with no
+// shared state (the checks of read_dynamic<true>): the code-length code is
+// decoded canonically from its lengths -- code length by comparing the next
+// 7 bits (MSB first) against the left-aligned limits of lengths 1..6, symbol
+// from the lengths' offsets and the symbols sorted by (length, value) -- and
+// the literal/length and distance length sets are checked as they are read.
+// The caller has already checked that the code-length code is complete.
+__device__ bool hdr_ok_lane(const FileDesc& F, uint64_t p) {
+    BitIn br;
+    br.setup(F.gz, F.gz_len);
+    br.seek(p + 3);
+    br.refill();
+    const uint32_t hlit = br.peek(5) + 257;
+    br.drop(5);
+    const uint32_t hdist = br.peek(5) + 1;
+    br.drop(5);
+    const uint32_t hclen = br.peek(4) + 4;
+    br.drop(4);
+    if (hlit > 286 || hdist > 30) return false;
+    uint64_t lens = 0;                                     // 3 bits per code-length symbol 0..18
+    br.refill();
+#pragma unroll
+    for (uint32_t k = 0; k < 19; ++k) {
+        if (k == 10) br.refill();
+        if (k < hclen) {
+            lens |= (uint64_t)br.peek(3) << (3 * c_clorder[k]);
+            br.drop(3);
+        }
+    }
+    uint64_t cnt8 = 0;                                     // symbols of each length (8 bits per length)
+#pragma unroll
+    for (int t = 0; t < 19; ++t) {
+        const uint32_t l = (uint32_t)(lens >> (3 * t)) & 7u;
+        if (l) cnt8 += 1ull << (8 * l);
+    }
+    uint32_t first = 0, offs = 0, limA = 0, limB = 0xffff0000u;
+    uint64_t base8 = 0, next8 = 0;
+#pragma unroll
+    for (int l = 1; l <= 7; ++l) {
+        const uint32_t cprev = (uint32_t)(cnt8 >> (8 * (l - 1))) & 0xffu, c = (uint32_t)(cnt8 >> (8 * l)) & 0xffu;
+        first = (first + cprev) << 1;                     // first code of length l
+        const uint32_t lim = (first + c) << (7 - l);      // left-aligned end of the length-l codes
+        if (l <= 4) limA |= (lim > 255u ? 255u : lim) << (8 * (l - 1));
+        else if (l <= 6) limB |= (lim > 255u ? 255u : lim) << (8 * (l - 5));
+        base8 |= (uint64_t)((offs - first + 128u) & 0xffu) << (8 * l);
+        next8 |= (uint64_t)offs << (8 * l);
+        offs += c;
+    }
+    uint64_t slo = 0, shi = 0;                             // symbols sorted by (length, value), 5 bits each
+#pragma unroll
+    for (int t = 0; t < 19; ++t) {
+        const uint32_t l = (uint32_t)(lens >> (3 * t)) & 7u;
+        if (l) {
+            const uint32_t i = (uint32_t)(next8 >> (8 * l)) & 0xffu;
+            next8 += 1ull << (8 * l);
+            if (i < 12) slo |= (uint64_t)t << (5 * i);
+            else shi |= (uint64_t)t << (5 * (i - 12));
+        }
+    }
+    const uint32_t total = hlit + hdist;
+    uint32_t i = 0, prev = 0, kl = 0, kd = 0, nl = 0, nd = 0, ml = 0, md = 0;
+    bool eob = false;
+    while (i < total) {
+        br.refill();
+        const uint32_t v = __brev(br.peek(7)) >> 25;      // the next 7 bits, first bit most significant
+        const uint32_t vv = v * 0x01010101u;
+        const uint32_t l = 1u + ((__popc(__vcmpgeu4(vv, limA)) + __popc(__vcmpgeu4(vv, limB))) >> 3);
+        const uint32_t ix = ((uint32_t)(base8 >> (8 * l)) & 0xffu) - 128u + (v >> (7 - l));
+        const uint32_t sym = ix < 12 ? (uint32_t)(slo >> (5 * ix)) & 31u : (uint32_t)(shi >> (5 * (ix - 12))) & 31u;
+        br.drop(l);
+        uint32_t rep = 1, val;
+        if (sym < 16) {
+            val = sym;
+            prev = sym;
+        } else if (sym == 16) {
+            if (i == 0) return false;
+            val = prev;
+            rep = 3 + br.peek(2);
+            br.drop(2);
+        } else if (sym == 17) {
+            val = 0;
+            rep = 3 + br.peek(3);
+            br.drop(3);
+            prev = 0;
+        } else {
+            val = 0;
+            rep = 11 + br.peek(7);
+            br.drop(7);
+            prev = 0;
+        }
+        if (i + rep > total) return false;
+        if (val) {
+            const uint32_t e2 = i + rep;
+            const uint32_t nlit = i < hlit ? ((e2 < hlit ? e2 : hlit) - i) : 0u;
+            const uint32_t ndst = rep - nlit;
+            kl += nlit * (32768u >> val);
+            kd += ndst * (32768u >> val);
+            nl += nlit;
+            nd += ndst;
+            if (nlit && val > ml) ml = val;
+            if (ndst && val > md) md = val;
+            if (i <= 256 && 256 < e2) eob = true;
+            if (kl > 32768u || kd > 32768u) return false;
+        }
+        i += rep;
+    }
+    if (!eob) return false;
+    if (!(kl == 32768u || (nl == 1 && ml == 1))) return false;
+    if (!(kd == 32768u || nd == 0 || (nd == 1 && md == 1))) return false;
+    return br.pos() <= F.end_bit;
+}
+
+// Search state of a part, kept by the caller between candidates: the next
+// window to filter, and a list of up to 32 filtered offsets (one per lane,
+// relative to the part's scan start) whose header checks are done.
+struct ScanState {
+    uint64_t next;       // first bit not yet filtered
+    uint64_t mine;       // this lane's list entry
+    uint32_t pass;       // list entries whose whole header passed, not yet returned
+};
+
+__device__ __forceinline__ void scan_begin(ScanState& st, uint64_t lo) {
+    st.next = lo;
+    st.mine = 0;
+    st.pass = 0;
+}
+
+// The next block-start candidate at or after the state's position, lowest
+// first: windows of 1024 bits are filtered (each lane tests 32 offsets with
+// bit masks, then the completeness of the code-length code); the survivors
+// are gathered, one per lane, until 32 are listed or the range ends, and then
+// all whole-header checks of the list run at once, one per lane.
+__device__ uint64_t find_candidate(const uint16_t* kraft3, const FileDesc& F, uint64_t lo, uint64_t hi, int lane,
+                                   ScanState& st) {
     BitIn w;
     w.setup(F.gz, F.gz_len);
     if (hi > F.end_bit) hi = F.end_bit;
-    for (uint64_t T = lo & ~1023ull; T < hi; T += 1024) {
-        const uint64_t base = T + 32ull * (uint64_t)lane;
-        const uint64_t wi = base >> 5;
-        const uint32_t w0 = w.word(wi), w1 = w.word(wi + 1), w2 = w.word(wi + 2), w3 = w.word(wi + 3);
-        const uint64_t x = (uint64_t)w0 | ((uint64_t)w1 << 32);
-        uint64_t y = ~x & ~(x >> 1) & (x >> 2);                // BFINAL = 0, BTYPE = 10
-        y &= ~((x >> 4) & (x >> 5) & (x >> 6) & (x >> 7));     // HLIT <= 29
-        y &= ~((x >> 9) & (x >> 10) & (x >> 11) & (x >> 12));  // HDIST <= 29
-        uint32_t m = (uint32_t)y;
-        if (base < lo) {
-            const uint64_t d = lo - base;
-            m = d >= 32 ? 0u : (m & (~0u << d));
+    for (;;) {
+        if (st.pass) {
+            const int k = __ffs(st.pass) - 1;
+            st.pass &= st.pass - 1;
+            return lo + shfl64(st.mine, k);
         }
-        if (base + 32 > hi) m = base >= hi ? 0u : (m & ((1u << (uint32_t)(hi - base)) - 1u));
-        uint32_t c = 0;
-        for (uint32_t mm = m; mm; mm &= mm - 1) {
-            const uint32_t k = __ffs(mm) - 1;
-            if (cl_complete(kraft3, w0, w1, w2, w3, k)) c |= 1u << k;
+        if (st.next >= hi) return kNone;
+        uint32_t n = 0;                                    // entries listed
+        while (n < 32 && st.next < hi) {
+            const uint64_t T = st.next & ~1023ull;
+            const uint64_t base = T + 32ull * (uint64_t)lane;
+            const uint64_t wi = base >> 5;
+            const uint32_t w0 = w.word(wi), w1 = w.word(wi + 1), w2 = w.word(wi + 2), w3 = w.word(wi + 3);
+            const uint64_t x = (uint64_t)w0 | ((uint64_t)w1 << 32);
+            uint64_t y = ~x & ~(x >> 1) & (x >> 2);                // BFINAL = 0, BTYPE = 10
+            y &= ~((x >> 4) & (x >> 5) & (x >> 6) & (x >> 7));     // HLIT <= 29
+            y &= ~((x >> 9) & (x >> 10) & (x >> 11) & (x >> 12));  // HDIST <= 29
+            uint32_t m = (uint32_t)y;
+            if (base < st.next) {
+                const uint64_t d = st.next - base;
+                m = d >= 32 ? 0u : (m & (~0u << d));
+            }
+            if (base + 32 > hi) m = base >= hi ? 0u : (m & ((1u << (uint32_t)(hi - base)) - 1u));
+            uint32_t c = 0;
+            for (uint32_t mm = m; mm; mm &= mm - 1) {
+                const uint32_t k = __ffs(mm) - 1;
+                if (cl_complete(kraft3, w0, w1, w2, w3, k)) c |= 1u << k;
+            }
+            // list the survivors lowest first (lanes cover increasing offsets) while there is room
+            uint64_t resume = T + 1024;
+            for (uint32_t bl = __ballot_sync(FULL, c != 0); bl; bl = __ballot_sync(FULL, c != 0)) {
+                const int l = __ffs(bl) - 1;
+                const uint32_t cl = __shfl_sync(FULL, c, l);
+                const uint32_t k = __ffs(cl) - 1;
+                const uint64_t pos = T + 32ull * (uint64_t)l + k;
+                if (n == 32) {                            // full: this window resumes here
+                    resume = pos;
+                    break;
+                }
+                if (lane == l) c &= c - 1;
+                if ((uint32_t)lane == n) st.mine = pos - lo;
+                ++n;
+            }
+            st.next = resume < hi ? resume : hi;
         }
-        // lowest first: lanes cover increasing offsets
-        for (uint32_t b = __ballot_sync(FULL, c != 0); b; b = __ballot_sync(FULL, c != 0)) {
-            const int l = __ffs(b) - 1;
-            const uint32_t cl = __shfl_sync(FULL, c, l);
-            const uint32_t k = __ffs(cl) - 1;
-            if (lane == l) c &= c - 1;
-            const uint64_t p = T + 32ull * (uint64_t)l + k;
-            BitIn br;
-            br.setup(F.gz, F.gz_len);
-            br.seek(p + 3);
-            if (read_dynamic<true>(S, br, lane) == CE_OK && br.pos() <= F.end_bit) return p;
-        }
+        const bool ok = (uint32_t)lane < n && hdr_ok_lane(F, lo + st.mine);
+        st.pass = __ballot_sync(FULL, ok);
     }
-    return kNone;
 }
 
 __device__ __forceinline__ WarpSmem& warp_smem() {
@@ -1229,9 +1382,10 @@ __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
             state = CS_FOUND;
         }
     } else {
-        uint64_t lo = C.lo;
+        ScanState scan;
+        scan_begin(scan, C.lo);
         for (;;) {
-            const uint64_t cand = find_candidate(S, kraft3, F, lo, C.hi, lane);
+            const uint64_t cand = find_candidate(kraft3, F, C.lo, C.hi, lane, scan);
             if (cand == kNone) break;
             br.seek(cand);
             o.n = 0;
@@ -1249,7 +1403,6 @@ __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
                 sync = cand;
                 break;
             }
-            lo = cand + 1;
         }
     }
     const bool neg = __any_sync(FULL, o.neg);
