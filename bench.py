@@ -43,9 +43,10 @@ TUNE_CHUNKS = [32 << 10, 64 << 10, 128 << 10, 256 << 10, 512 << 10]   # the auto
 TUNE_WPB = [2, 4, 8]                                                # ... and pass-1 CTA shapes (warps)
 PLAIN_PARTS = 1024            # parts per file of the plain one-file-at-a-time form
 METRIC = "decompressed GB/s on 1 GB300 (batched vs plain), %HBM roofline"
-# DRAM bytes (read + write) of pass 1 per decompressed byte: ncu capture of k_sync and k_inflate on one
-# 256 MiB FASTQ gzip -1 file (profiles/pass1_fastq256_l1.md); None while the kernels differ from the capture
-PASS1_TRAFFIC_PER_OUT_BYTE = None
+# DRAM bytes (read + write) of pass 1 per decompressed byte: ncu capture of k_sync and k_inflate on this
+# workload's batched run at 64 KiB parts and 4 warps per block (profiles/pass1_translate_crc_fastq256_batched.md:
+# 1.625 + 3.449 GB for 536,870,912 bytes out); None while the kernels differ from the capture
+PASS1_TRAFFIC_PER_OUT_BYTE = 5.074e9 / 536870912
 
 
 def _peaks():
