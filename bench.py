@@ -137,6 +137,23 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
+# replicas: every rank decodes its own copy of the workload (independent members, no data exchange)
+# ---------------------------------------------------------------------------
+def max_over_ranks(values, device):
+    """The slowest rank's times (all ranks take part; the process group is initialised)."""
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def whole_job_gbs(bytes_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput: every rank's bytes over the slowest rank's time per step."""
+    return world * bytes_per_rank / (ms * 1e-3) / 1e9
+
+
+# ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
 def run_pgz(args, rank, world):
@@ -276,11 +293,9 @@ def run_pgz(args, rank, world):
     batch.free()
     pgz.pgz_destroy(ctx_b)
     if dist:
-        t = torch.tensor([ms, e2e_ms, ms_plain], device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms, e2e_ms, ms_plain = float(t[0]), float(t[1]), float(t[2])
+        ms, e2e_ms, ms_plain = max_over_ranks([ms, e2e_ms, ms_plain], "cuda")
 
-    gbs = world * total_out / (ms * 1e-3) / 1e9
+    gbs = whole_job_gbs(total_out, world, ms)
     pk = _peaks()
     hbm = pk.get("hbm_gbs")
     peak_src = "measured" if hbm else "fallback"
