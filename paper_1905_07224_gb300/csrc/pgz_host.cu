@@ -488,6 +488,7 @@ int execute(pgz_ctx* ctx, Plan& P, pgz_stats* st) {
         const ChunkDesc* res = P.h_chunks.as<ChunkDesc>();
         for (size_t f = 0; f < P.files.size(); ++f) {
             P.files[f].total = hf[f].total;
+            P.files[f].member_end = hf[f].member_end;
             P.files[f].status = hf[f].status;
             if (hf[f].status == PGZ_OK) continue;
             if (hf[f].bad_chunk != 0xffffffffu && retries < (uint64_t)kMaxRetries &&
@@ -565,6 +566,162 @@ void copy_range_windows(Plan& P, const pgz_index* idx, const std::vector<std::pa
         cudaMemcpyAsync(P.d_windows.as<uint8_t>() + w.first * kWin, idx->windows.as<uint8_t>() + w.second * kWin, kWin,
                         cudaMemcpyDeviceToDevice, s);
 }
+
+// BGZF (SAM/BAM specification): a member whose FEXTRA holds the subfield
+// SI1 = 'B', SI2 = 'C', SLEN = 2 carries its total size minus one; *size is
+// that total.  h holds `avail` bytes from the member start.
+bool bgzf_member_size(const uint8_t* h, uint64_t avail, uint64_t* size) {
+    if (avail < 18 || h[0] != 0x1f || h[1] != 0x8b || h[2] != 8 || !(h[3] & 4)) return false;
+    const uint32_t xlen = h[10] | ((uint32_t)h[11] << 8);
+    if (12ull + xlen > avail) return false;
+    for (uint32_t q = 12; q + 4 <= 12 + xlen;) {
+        const uint32_t slen = h[q + 2] | ((uint32_t)h[q + 3] << 8);
+        if (h[q] == 'B' && h[q + 1] == 'C' && slen == 2 && q + 6 <= 12 + xlen) {
+            *size = (uint64_t)(h[q + 4] | ((uint32_t)h[q + 5] << 8)) + 1;
+            return true;
+        }
+        q += 4 + slen;
+    }
+    return false;
+}
+
+}  // namespace
+
+namespace {
+
+void begin_plan(Plan& P);
+
+// header of the member starting at byte `off` of gz (device memory): *s0 receives the absolute byte offset
+// of its DEFLATE data; PGZ_E_HEADER if no member header starts there
+int member_header_at(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, uint64_t off, uint64_t* s0) {
+    if (off >= gz_len || gz_len - off < 18) return PGZ_E_HEADER;
+    const uint64_t rest = gz_len - off;
+    uint64_t want = std::min<uint64_t>(rest, 4096);
+    for (;;) {
+        if (cuda_status(ctx->hdr.ensure(want))) return PGZ_E_NOMEM;
+        uint8_t* h = ctx->hdr.as<uint8_t>();
+        if (cudaMemcpyAsync(h, gz + off, want, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+            cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+            return PGZ_E_CUDA;
+        uint64_t s = 0;
+        const int r = parse_header(h, want, rest, &s);
+        if (r == -1 && want < rest) {
+            want = std::min<uint64_t>(rest, want * 4);
+            continue;
+        }
+        if (r != PGZ_OK) return PGZ_E_HEADER;
+        *s0 = off + s;
+        return PGZ_OK;
+    }
+}
+
+void add_stats(pgz_stats* acc, const pgz_stats& s) {
+    acc->in_bytes += s.in_bytes;
+    acc->out_bytes += s.out_bytes;
+    acc->chunks += s.chunks;
+    acc->empty_chunks += s.empty_chunks;
+    acc->false_syncs += s.false_syncs;
+    acc->retries += s.retries;
+    acc->placeholders += s.placeholders;
+    acc->symbols += s.symbols;
+    acc->ms_sync += s.ms_sync;
+    acc->ms_inflate += s.ms_inflate;
+    acc->ms_chain += s.ms_chain;
+    acc->ms_translate += s.ms_translate;
+    acc->ms_crc += s.ms_crc;
+    acc->ms_total += s.ms_total;
+}
+
+// Every member of gz (device memory, 4-byte aligned), outputs concatenated in out (RFC 1952 2.2: a gzip
+// file is a series of members).  When every member is a BGZF member (its size in its header), the members
+// are found by walking the headers and decoded in one run; otherwise member after member, each decoded
+// as an open member whose end is where its final block ends.
+int decompress_members(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, uint8_t* out, uint64_t out_cap,
+                       uint64_t* out_len, pgz_stats* st) {
+    *out_len = 0;
+    if (st) memset(st, 0, sizeof *st);
+    if (gz_len < 18) return PGZ_E_HEADER;
+    {   // BGZF: the whole stream is read once on the host to walk the headers
+        const uint64_t first = std::min<uint64_t>(gz_len, 4096);
+        if (cuda_status(ctx->hdr.ensure(first))) return PGZ_E_NOMEM;
+        uint8_t* h = ctx->hdr.as<uint8_t>();
+        if (cudaMemcpyAsync(h, gz, first, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+            cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+            return PGZ_E_CUDA;
+        uint64_t sz = 0;
+        if (bgzf_member_size(h, first, &sz) && sz < gz_len) {
+            if (cuda_status(ctx->hdr.ensure(gz_len))) return PGZ_E_NOMEM;
+            h = ctx->hdr.as<uint8_t>();
+            if (cudaMemcpyAsync(h, gz, gz_len, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+                cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+                return PGZ_E_CUDA;
+            std::vector<std::pair<uint64_t, uint64_t>> mem;
+            bool ok = true;
+            for (uint64_t off = 0; off < gz_len && ok;) {
+                ok = bgzf_member_size(h + off, gz_len - off, &sz) && sz >= 18 && sz <= gz_len - off;
+                if (ok) mem.emplace_back(off, sz);
+                off += ok ? sz : 0;
+            }
+            if (ok) {
+                Plan& P = ctx->plan;
+                begin_plan(P);
+                uint64_t o = 0;
+                for (const auto& m : mem) {
+                    const uint8_t* mh = h + m.first;
+                    uint64_t hl = 0;
+                    if (parse_header(mh, m.second, m.second, &hl) != PGZ_OK) return PGZ_E_HEADER;
+                    const uint8_t* tr = mh + m.second - 8;
+                    MemberInfo mi;
+                    mi.s0 = m.first + hl;
+                    mi.crc = tr[0] | ((uint32_t)tr[1] << 8) | ((uint32_t)tr[2] << 16) | ((uint32_t)tr[3] << 24);
+                    mi.isize = tr[4] | ((uint32_t)tr[5] << 8) | ((uint32_t)tr[6] << 16) | ((uint32_t)tr[7] << 24);
+                    if (o + mi.isize > out_cap) {                 // size needed: the sum of the ISIZE fields
+                        uint64_t need = o;
+                        for (size_t k = P.files.size(); k < mem.size(); ++k) {
+                            const uint8_t* t2 = h + mem[k].first + mem[k].second - 4;
+                            need += t2[0] | ((uint32_t)t2[1] << 8) | ((uint32_t)t2[2] << 16) | ((uint32_t)t2[3] << 24);
+                        }
+                        *out_len = need;
+                        return PGZ_E_CAPACITY;
+                    }
+                    plan_member(ctx, P, gz, m.first + m.second, out + o, mi.isize, mi, 0);
+                    o += mi.isize;
+                }
+                const int e = execute(ctx, P, st);
+                uint64_t total = 0;
+                for (const auto& F : P.files) total += F.total;
+                *out_len = total;
+                return e;
+            }
+        }
+    }
+    uint64_t off = 0, total = 0;
+    for (;;) {
+        uint64_t s0 = 0;
+        int e = member_header_at(ctx, gz, gz_len, off, &s0);
+        if (e) return off == 0 ? e : PGZ_E_UNSUPPORTED;        // data after a member that is no member
+        MemberInfo mi;
+        mi.s0 = s0;
+        mi.crc = mi.isize = 0;                                  // read by the device at the member's end
+        Plan& P = ctx->plan;
+        begin_plan(P);
+        plan_member(ctx, P, gz, gz_len, total < out_cap ? out + total : out + out_cap,
+                    total < out_cap ? out_cap - total : 0, mi, 0);
+        P.files[0].open_end = 1;
+        pgz_stats s1;
+        e = execute(ctx, P, st ? &s1 : nullptr);
+        if (st) add_stats(st, s1);
+        total += P.files[0].total;
+        *out_len = total;
+        if (e) return e;
+        off = P.files[0].member_end;
+        if (off >= gz_len) return PGZ_OK;
+    }
+}
+
+}  // namespace
+
+namespace {
 
 void begin_plan(Plan& P) {
     P.files.clear();
@@ -798,16 +955,7 @@ int pgz_decompress(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, uint8_t* ou
                    uint64_t* out_len, pgz_stats* st) {
     if (!ctx || !gz || !out_len || (!out && out_cap) || !aligned4(gz)) return PGZ_E_ARG;
     cudaSetDevice(ctx->cfg.device);
-    *out_len = 0;
-    MemberInfo mi;
-    int e = read_member(ctx, gz, gz_len, &mi);
-    if (e) return e;
-    Plan& P = ctx->plan;
-    begin_plan(P);
-    plan_member(ctx, P, gz, gz_len, out, out_cap, mi, 0);
-    e = execute(ctx, P, st);
-    *out_len = P.files[0].total;
-    return e;
+    return decompress_members(ctx, gz, gz_len, out, out_cap, out_len, st);
 }
 
 int pgz_decompress_host(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, uint8_t* out, uint64_t out_cap,
@@ -815,21 +963,12 @@ int pgz_decompress_host(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, uint8_
     if (!ctx || !gz || !out_len || (!out && out_cap)) return PGZ_E_ARG;
     cudaSetDevice(ctx->cfg.device);
     *out_len = 0;
-    uint64_t s0 = 0;
-    if (parse_header(gz, gz_len, gz_len, &s0) != PGZ_OK) return PGZ_E_HEADER;
-    MemberInfo mi;
-    mi.s0 = s0;
-    const uint8_t* t = gz + gz_len - 8;
-    mi.crc = t[0] | ((uint32_t)t[1] << 8) | ((uint32_t)t[2] << 16) | ((uint32_t)t[3] << 24);
-    mi.isize = t[4] | ((uint32_t)t[5] << 8) | ((uint32_t)t[6] << 16) | ((uint32_t)t[7] << 24);
+    if (gz_len < 18) return PGZ_E_HEADER;
     if (cuda_status(ctx->in_buf.ensure(gz_len)) || cuda_status(ctx->out_buf.ensure(out_cap))) return PGZ_E_NOMEM;
     if (cudaMemcpyAsync(ctx->in_buf.p, gz, gz_len, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
         return PGZ_E_CUDA;
-    Plan& P = ctx->plan;
-    begin_plan(P);
-    plan_member(ctx, P, ctx->in_buf.as<uint8_t>(), gz_len, ctx->out_buf.as<uint8_t>(), out_cap, mi, 0);
-    int e = execute(ctx, P, st);
-    *out_len = P.files[0].total;
+    const int e = decompress_members(ctx, ctx->in_buf.as<uint8_t>(), gz_len, ctx->out_buf.as<uint8_t>(), out_cap,
+                                     out_len, st);
     if (e == PGZ_OK && *out_len) {
         if (cudaMemcpyAsync(out, ctx->out_buf.p, *out_len, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
             cudaStreamSynchronize(ctx->stream) != cudaSuccess)

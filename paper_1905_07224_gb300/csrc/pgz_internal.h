@@ -56,7 +56,8 @@ struct FileDesc {
     int32_t group0, ngroups;
     uint64_t seg0, nseg;   // 4 KiB CRC segments of the output
     uint32_t mode;         // 0 whole member; 1 from a bit offset (no CRC/ISIZE); 2 byte range of the output
-    uint32_t pad0;
+    uint32_t open_end;     // mode 0: more members may follow; the member ends after its final block, and its
+                           // trailer (CRC-32, ISIZE) is read there
     uint64_t out_base;     // output offset of the first part (mode 2: from the index)
     uint64_t out_lo, out_hi;  // member output bytes [out_lo, out_hi) go to out[P - out_lo]
     // results
@@ -67,6 +68,7 @@ struct FileDesc {
     uint32_t bad_chunk;    // first part with an error (for recovery), or ~0
     uint32_t bad_err;
     uint32_t pad1;
+    uint64_t member_end;   // mode 0: one past the member's trailer, in bytes of gz
 };
 
 // one part of a member

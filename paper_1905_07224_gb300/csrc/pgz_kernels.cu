@@ -1452,7 +1452,7 @@ __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
     uint32_t blocks = C.blocks, final = C.final, err = CE_OK;
     uint64_t end = C.resume;
     if (final) {
-        if (stop != kNone) err = CE_CHAIN;
+        if (stop != kNone && !F.open_end) err = CE_CHAIN;
     } else if (!(stop != kNone && C.resume == stop)) {
         init_smem(S, p, lane);
         BitIn br;
@@ -1474,13 +1474,13 @@ __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
             ++blocks;
             if (fin) {
                 final = 1;
-                if (stop != kNone) err = CE_CHAIN;
+                if (stop != kNone && !F.open_end) err = CE_CHAIN;   // an open member may end before the next part
                 break;
             }
         }
         end = br.pos();
     }
-    if (err == CE_OK && final && F.mode != 2) {          // the trailer must follow the final block
+    if (err == CE_OK && final && F.mode != 2 && !F.open_end) {   // the trailer must follow the final block
         if (((end + 7) >> 3) + 8 != F.gz_len) err = CE_TRAIL;
     }
     const bool neg = __any_sync(FULL, o.neg);
@@ -1502,19 +1502,30 @@ __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
 __global__ void __launch_bounds__(1024) k_plan(FileDesc* files, ChunkDesc* chunks) {
     FileDesc& F = files[blockIdx.x];
     __shared__ uint64_t part[1024];
-    __shared__ uint32_t bad;
+    __shared__ uint32_t bad, fin;
     __shared__ int any_final;
     const int t = threadIdx.x;
     if (t == 0) {
         bad = 0xffffffffu;
+        fin = 0xffffffffu;
         any_final = 0;
     }
+    __syncthreads();
+    // an open member ends with the first part that decoded its final block; the parts after it lie in
+    // what follows the member (the next member, or other data) and are dropped
+    if (F.open_end)
+        for (int i = t; i < F.nchunks; i += 1024) {
+            const ChunkDesc& C = chunks[F.chunk0 + i];
+            if (C.state == CS_DONE && C.final) atomicMin(&fin, (uint32_t)i);
+        }
     __syncthreads();
     uint64_t carry = F.out_base;
     for (int b0 = 0; b0 < F.nchunks; b0 += 1024) {
         const int c = F.chunk0 + b0 + t;
         uint64_t n = 0;
-        if (b0 + t < F.nchunks) {
+        if (b0 + t < F.nchunks && (uint32_t)(b0 + t) > fin) {
+            chunks[c].state = CS_EMPTY;
+        } else if (b0 + t < F.nchunks) {
             ChunkDesc& C = chunks[c];
             if (C.state == CS_DONE) {
                 n = C.n;
@@ -1540,18 +1551,32 @@ __global__ void __launch_bounds__(1024) k_plan(FileDesc* files, ChunkDesc* chunk
         F.total = total;
         F.bad_chunk = bad;
         F.crc_acc = 0;
+        F.member_end = F.gz_len;
         uint32_t st = PGZ_OK;
-        if (bad != 0xffffffffu) {
-            F.bad_err = chunks[F.chunk0 + bad].err;
-            st = F.bad_err == CE_TRAIL ? PGZ_E_UNSUPPORTED : PGZ_E_DATA;
-        } else if (!any_final && F.mode != 2) {
-            st = PGZ_E_DATA;
-        } else if (F.mode == 0 && total > F.out_cap) {
-            st = PGZ_E_CAPACITY;
-        } else if (F.mode == 1 && total > F.out_cap) {
-            st = PGZ_E_CAPACITY;
-        } else if (F.mode == 0 && (uint32_t)total != F.isize_expect) {
-            st = PGZ_E_ISIZE;
+        if (F.open_end && fin != 0xffffffffu && bad == 0xffffffffu) {   // the member's own trailer
+            const uint64_t me = ((chunks[F.chunk0 + fin].end + 7) >> 3) + 8;
+            if (me > F.gz_len) {
+                st = PGZ_E_DATA;
+            } else {
+                const uint8_t* tr = F.gz + me - 8;
+                F.crc_expect = tr[0] | ((uint32_t)tr[1] << 8) | ((uint32_t)tr[2] << 16) | ((uint32_t)tr[3] << 24);
+                F.isize_expect = tr[4] | ((uint32_t)tr[5] << 8) | ((uint32_t)tr[6] << 16) | ((uint32_t)tr[7] << 24);
+                F.member_end = me;
+            }
+        }
+        if (st == PGZ_OK) {
+            if (bad != 0xffffffffu) {
+                F.bad_err = chunks[F.chunk0 + bad].err;
+                st = F.bad_err == CE_TRAIL ? PGZ_E_UNSUPPORTED : PGZ_E_DATA;
+            } else if (!any_final && F.mode != 2) {
+                st = PGZ_E_DATA;
+            } else if (F.mode == 0 && total > F.out_cap) {
+                st = PGZ_E_CAPACITY;
+            } else if (F.mode == 1 && total > F.out_cap) {
+                st = PGZ_E_CAPACITY;
+            } else if (F.mode == 0 && (uint32_t)total != F.isize_expect) {
+                st = PGZ_E_ISIZE;
+            }
         }
         F.status = st;
     }

@@ -170,6 +170,23 @@ def _deflate_piece(args):
     return c.compress(data) + c.flush(zlib.Z_FINISH if last else zlib.Z_SYNC_FLUSH)
 
 
+def bgzf_compress(data: bytes, level: int = 6, block: int = 65280, eof: bool = True) -> bytes:
+    """BGZF (blocked gzip, SAM/BAM specification): ``data`` in members of at most ``block`` input bytes, each a
+    gzip member whose header carries the extra subfield 'BC' (SLEN 2) holding the member's total size minus
+    one; host zlib deflates each block (raw DEFLATE).  With ``eof`` the empty end-of-file member follows."""
+    out = bytearray()
+    members = [data[a:a + block] for a in range(0, len(data), block)] + ([b""] if eof else [])
+    for chunk in members:
+        c = zlib.compressobj(level, zlib.DEFLATED, -15)
+        body = c.compress(chunk) + c.flush()
+        size = 12 + 6 + len(body) + 8
+        head = bytes([0x1F, 0x8B, 8, 4, 0, 0, 0, 0, 0, 255, 6, 0, ord("B"), ord("C"), 2, 0]) + \
+            (size - 1).to_bytes(2, "little")
+        out += head + body + (zlib.crc32(chunk) & 0xFFFFFFFF).to_bytes(4, "little") + \
+            (len(chunk) & 0xFFFFFFFF).to_bytes(4, "little")
+    return bytes(out)
+
+
 def gzip_compress_parallel(data: bytes, level: int = 6, piece: int = 64 << 20, processes: int | None = None) -> bytes:
     """One gzip member (RFC 1952, 10-byte header) of ``data`` compressed by host zlib in parallel pieces, the
     way pigz does: piece k is deflated with the previous 32 KiB as its preset dictionary and ends with a sync

@@ -156,7 +156,7 @@ def test_errors():
         assert ctx.decompress(bad_isize)[0] == P.PGZ_E_ISIZE
         assert ctx.decompress(b"\x1f\x8c" + pgz_ok[2:])[0] == P.PGZ_E_HEADER
         assert ctx.decompress(pgz_ok[:len(pgz_ok) // 2] + pgz_ok[-8:])[0] in (P.PGZ_E_DATA, P.PGZ_E_CRC)
-        assert ctx.decompress(pgz_ok + synth.gzip_compress(b"second", 6))[0] == P.PGZ_E_UNSUPPORTED
+        assert ctx.decompress(pgz_ok + b"not a gzip member")[0] == P.PGZ_E_UNSUPPORTED
         st, _, n, _ = ctx.decompress(pgz_ok, out_cap=1000)
         assert st == P.PGZ_E_CAPACITY and n == len(data)
         # a distance before the member start
@@ -260,5 +260,62 @@ def test_host_entry_point(cfg1):
         st, n, s = ctx.pgz.pgz_decompress_host(ctx.h, gz, out, stats=True)
         assert st == 0 and n == len(data) and out[:n].tobytes() == data
         assert ctx.pgz.pgz_kernel_launches(ctx.h) > 0
+    finally:
+        ctx.close()
+
+
+def test_multi_member_files():
+    """RFC 1952 2.2: a gzip file is a series of members; the output is their concatenation (the oracle decodes
+    every member)."""
+    a = synth.fastq(700000, 150, 0.001, 21)
+    b = synth.markov(300000, 22)
+    c = synth.fastq(90000, 100, 0.001, 23)
+    cases = [
+        [(a, 1), (b, 9)],
+        [(a, 6), (b"", 6), (c, 1), (b, 6)],
+        [(c, 9)] * 5,
+    ]
+    for nparts in (1, 8):
+        ctx = Ctx(n_chunks=nparts)
+        try:
+            for members in cases:
+                gz = b"".join(synth.gzip_compress(d, lv) for d, lv in members)
+                want = b"".join(d for d, _ in members)
+                e, ref, _, _ = oracle.gunzip(gz, cap=len(want) + 1024)
+                assert e == 0 and ref == want
+                st, out, n, s = ctx.decompress(gz, stats=True)
+                assert st == 0, ctx.pgz.pgz_strerror(st)
+                assert out == want
+                # the host-buffer entry point takes the same path
+                host_out = np.zeros(len(want) + 64, dtype=np.uint8)
+                st, n, _ = ctx.pgz.pgz_decompress_host(ctx.h, gz, host_out)
+                assert st == 0 and host_out[:n].tobytes() == want
+                # a damaged second member is caught by its own trailer
+                second = len(synth.gzip_compress(members[0][0], members[0][1]))
+                bad = bytearray(gz)
+                bad[second + len(synth.gzip_compress(members[1][0], members[1][1])) - 5] ^= 1
+                assert ctx.decompress(bytes(bad))[0] in (ctx.pgz.PGZ_E_CRC, ctx.pgz.PGZ_E_ISIZE)
+        finally:
+            ctx.close()
+
+
+@pytest.mark.parametrize("level", [1, 6, 9])
+def test_bgzf_members_in_one_run(level):
+    """BGZF: every member's size is in its header, so all members are found from the headers and decoded in
+    one run."""
+    data = synth.fastq(3 << 20, 150, 0.001, 24 + level)
+    bz = synth.bgzf_compress(data, level)
+    ctx = Ctx()
+    try:
+        st, out, n, s = ctx.decompress(bz, stats=True)
+        assert st == 0, ctx.pgz.pgz_strerror(st)
+        assert out == data
+        assert s["chunks"] >= (len(data) + 65279) // 65280 + 1      # at least one part per member
+        st, _, n, _ = ctx.decompress(bz, out_cap=len(data) - 1)
+        assert st == ctx.pgz.PGZ_E_CAPACITY and n == len(data)
+        bad = bytearray(bz)
+        bad[len(bz) // 2] ^= 0x10                                 # inside some member's data
+        assert ctx.decompress(bytes(bad))[0] in (ctx.pgz.PGZ_E_DATA, ctx.pgz.PGZ_E_CRC, ctx.pgz.PGZ_E_ISIZE,
+                                                 ctx.pgz.PGZ_E_HEADER, ctx.pgz.PGZ_E_UNSUPPORTED)
     finally:
         ctx.close()

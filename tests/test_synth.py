@@ -31,3 +31,16 @@ def test_parallel_gzip_is_one_member():
     assert int.from_bytes(gz[-8:-4], "little") == zlib.crc32(data)
     # about the size of a single-stream compression (preset dictionaries across pieces)
     assert len(gz) < 1.01 * len(synth.gzip_compress(data, 6))
+
+
+def test_bgzf_members_carry_their_sizes():
+    import gzip
+    data = synth.fastq(300000, 150, 0.001, 9)
+    bz = synth.bgzf_compress(data, 6)
+    assert gzip.decompress(bz) == data
+    off, n = 0, 0
+    while off < len(bz):
+        assert bz[off:off + 4] == b"\x1f\x8b\x08\x04" and bz[off + 12:off + 16] == b"BC\x02\x00"
+        off += int.from_bytes(bz[off + 16:off + 18], "little") + 1
+        n += 1
+    assert off == len(bz) and n == (len(data) + 65279) // 65280 + 1
