@@ -51,7 +51,7 @@ typedef enum pgz_status {
     PGZ_E_ISIZE = 5,        /* output length mod 2^32 differs from the trailer */
     PGZ_E_CAPACITY = 6,     /* out_cap too small; *out_len holds the size needed */
     PGZ_E_NOSYNC = 7,       /* no block start after the requested offset */
-    PGZ_E_UNSUPPORTED = 8,  /* data after the first member (multi-member gzip) */
+    PGZ_E_UNSUPPORTED = 8,  /* data after a member that is not a gzip member; a batch job with several members */
     PGZ_E_TIMEOUT = 9,      /* a bounded device wait gave up */
     PGZ_E_CUDA = 10,        /* a CUDA runtime call failed */
     PGZ_E_NOMEM = 11        /* scratch allocation failed or exceeds the budget */
@@ -113,12 +113,17 @@ void pgz_config_init(pgz_config* cfg);
 int pgz_create(pgz_ctx** out, const pgz_config* cfg);
 void pgz_destroy(pgz_ctx* ctx);
 
-/* Exact decompression of one whole gzip member (Section "Full file
+/* Exact decompression of a whole gzip file (Section "Full file
    decompression in two passes (pugz)"; the result is that of Algorithm
-   "DEFLATE decompression" from the stream start).
+   "DEFLATE decompression" from the stream start).  A file of several members
+   (RFC 1952 2.2) gives the concatenation of their outputs, each member
+   checked against its own trailer: BGZF members (their size in the header's
+   'BC' subfield) are all decoded in one run; other members one after
+   another, each ending where its final block ends.
    gz [device, gz_len bytes]: the gzip file; out [device, out_cap bytes].
-   *out_len: bytes written; with PGZ_E_CAPACITY the bytes needed.
-   st (nullable): statistics of this call. */
+   *out_len: bytes written; with PGZ_E_CAPACITY the bytes needed (for members
+   decoded one after another: up to the member that did not fit).
+   st (nullable): statistics of this call (summed over the runs). */
 int pgz_decompress(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len,
                    uint8_t* out, uint64_t out_cap, uint64_t* out_len, pgz_stats* st);
 

@@ -1518,7 +1518,7 @@ const char* pgz_strerror(int status) {
         case PGZ_E_ISIZE: return "ISIZE mismatch";
         case PGZ_E_CAPACITY: return "output buffer too small";
         case PGZ_E_NOSYNC: return "no block start after the offset";
-        case PGZ_E_UNSUPPORTED: return "data after the first gzip member";
+        case PGZ_E_UNSUPPORTED: return "data after a gzip member that is not a gzip member";
         case PGZ_E_TIMEOUT: return "device wait timed out";
         case PGZ_E_CUDA: return "CUDA error";
         case PGZ_E_NOMEM: return "out of device memory";
