@@ -116,3 +116,41 @@ def test_batch_of_512_members_in_one_graph():
         assert e == 0 and out == files[k][0]
         assert d_out[k][:len(out)].cpu().numpy().tobytes() == out
     ctx.close()
+
+
+@pytest.mark.slow
+def test_two_256mib_files_full_size():
+    """The benchmark's workload: 2 x 256 MiB FASTQ (150 bp, seed 1) at gzip -1 and -9, batched (graph, 64 KiB
+    parts, 4 warps per block) and plain (1024 parts per file); sampled parts' u16 symbols against the oracle."""
+    import torch
+    files = synth.make_files([("fastq", 256 << 20, 1, 1), ("fastq", 256 << 20, 9, 1)])
+    ctx = Ctx(chunk_bytes=65536, warps_per_block=4)
+    pgz = ctx.pgz
+    d_in = [to_device(gz) for _, gz in files]
+    d_out = [empty(len(raw) + 4096) for raw, _ in files]
+    jobs = [(d_in[k].data_ptr(), len(gz), d_out[k].data_ptr(), d_out[k].numel()) for k, (_, gz) in enumerate(files)]
+    b = pgz.Batch(ctx.h, jobs)
+    r, res, _ = b.run()
+    assert r == 0
+    torch.cuda.synchronize()
+    for k, (raw, _) in enumerate(files):
+        assert res[k] == (0, len(raw)) and _same_on_device(d_out[k], raw)
+    b.free()
+    ctx.close()
+    plain = Ctx(n_chunks=1024)
+    try:
+        for (raw, gz), d, o in zip(files, d_in, d_out):
+            o.zero_()
+            st, n, s = pgz.pgz_decompress(plain.h, d.data_ptr(), len(gz), o.data_ptr(), o.numel(), True)
+            assert st == 0 and n == len(raw) and _same_on_device(o, raw)
+            assert s["chunks"] == 1024 and s["empty_chunks"] == 0
+            sb, ns, nph = pgz.pgz_inspect_parts(plain.h)
+            end = (len(gz) - 8) * 8
+            for i in (1, 511, 1023):
+                stop = int(sb[i + 1]) if i + 1 < len(sb) else 0
+                ref = oracle.inflate_from(gz, end, int(sb[i]), stop, known=False, cap=int(ns[i]) + 4096)
+                assert ref["status"] == 0
+                assert np.array_equal(pgz.pgz_inspect_symbols(plain.h, i), ref["sym"]), i
+                assert int(nph[i]) == int(np.count_nonzero(ref["sym"] & 0x8000)), i
+    finally:
+        plain.close()

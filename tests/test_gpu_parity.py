@@ -319,3 +319,47 @@ def test_bgzf_members_in_one_run(level):
                                                  ctx.pgz.PGZ_E_HEADER, ctx.pgz.PGZ_E_UNSUPPORTED)
     finally:
         ctx.close()
+
+
+def _false_start_stream():
+    """A member whose stored block carries, as payload, a complete valid DEFLATE stream (six non-final dynamic
+    blocks of text and a final one): inside the payload that stream's first block passes every block-start
+    check, but it is not a block start of the member."""
+    text = synth.fastq(120000, 100, 0.001, 31)
+    fake_text = synth.fastq(14000, 100, 0.001, 32)
+    wf = dw.BitWriter()
+    for k in range(7):
+        part = fake_text[2000 * k:2000 * (k + 1)]
+        dw.write_dynamic(wf, dw.tokens_from_text(part), k == 6)
+    fake = wf.tobytes()
+    pad = b"\x00" * 4000
+    payload = pad + fake + b"\x00" * 64
+    w = dw.BitWriter()
+    dw.write_dynamic(w, dw.tokens_from_text(text[:60000]), False)
+    head_bits = w.nbits
+    dw.write_stored(w, payload, False)
+    dw.write_dynamic(w, dw.tokens_from_text(text[60000:]), True)
+    data = text[:60000] + payload + text[60000:]
+    gz = dw.gzip_wrap(w.tobytes(), data)
+    pay0 = 10 + ((head_bits + 3 + 7) // 8) + 4            # header, first block, stored header; byte of the payload
+    return gz, data, pay0, pay0 + len(pad)
+
+
+def test_false_block_start_is_caught_by_the_chain_check():
+    gz, data, pad0, fake0 = _false_start_stream()
+    assert gz[fake0:fake0 + 1] and oracle.block_ok(gz, (len(gz) - 8) * 8, fake0 * 8, oracle.default_allowed())[0]
+    csize = len(gz) - 18
+    # part counts whose nominal start of some part falls in the padding before the hidden stream
+    picks = [n for n in range(8, 200) if any(pad0 <= 10 + i * ((csize + n - 1) // n) < fake0 for i in range(1, n))]
+    assert picks
+    for n in picks[:3]:
+        ref = oracle.two_pass(gz, n)
+        assert ref["status"] == 0 and ref["out"] == data
+        ctx = Ctx(n_chunks=n)
+        try:
+            st, out, _, s = ctx.decompress(gz, stats=True)
+            assert st == 0, ctx.pgz.pgz_strerror(st)
+            assert out == data
+            assert s["false_syncs"] >= 1 and s["retries"] >= 1
+        finally:
+            ctx.close()
