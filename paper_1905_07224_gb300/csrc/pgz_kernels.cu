@@ -92,8 +92,8 @@ struct WarpSmem {
     uint8_t lens[320];
     uint8_t cllens[32];
     uint32_t masks[32 * 32];   // parallel decoding: token starts in the first 1024 bits of each lane's segment;
-                               // reused by exec_range: words 0-255 the entries of one pass of 256 positions,
-                               // 512-767 the batch's tokens, 768-1023 their output offsets
+                               // reused by exec_range: words 0-511 the entries of two passes of 256
+                               // positions, 512-767 the batch's tokens, 768-1023 their output offsets
 };
 
 __device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
@@ -434,6 +434,13 @@ struct OutState {
     bool known;        // the context before the part is empty (member start)
     bool neg;          // this lane copied from before the part start (a placeholder source)
 };
+
+__device__ __forceinline__ void cp_async4(uint32_t dst_shared, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst_shared), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // the symbol at part position q: q < 0 lies in the symbolic context.  Part
 // positions are 32-bit (a part holds fewer than 2^31 symbols).
@@ -785,6 +792,77 @@ __device__ uint32_t seg_next(const WarpSmem& S, BitIn& b, bool active, uint64_t 
     return st;
 }
 
+// Stage entries of exec_range: kEntryRes | symbol when resolved; else the
+// index of the source in the same pass, or kEntryCross | its index in the
+// previous pass.
+constexpr uint32_t kEntryRes = 0x10000u, kEntryCross = 0x20000u;
+
+struct PassMasks {
+    uint32_t am, hm, cm, om;   // bit u: async copy, its upper half, cross entry, open in-pass pointer
+    uint32_t neg;              // a source lies before the part start (a placeholder)
+};
+
+// The entries of the pass at A (positions A + 8 lane .. + 7) into stage buffer
+// b; positions before fin are final in the part's output and are copied
+// asynchronously into their entries (the 32-bit word holding the symbol).
+__device__ __forceinline__ PassMasks build_pass(uint32_t* masks, const uint32_t* tokS, const uint32_t* stS,
+                                                uint32_t ntok, uint32_t base, uint32_t end, const uint16_t* out,
+                                                uint32_t A, uint32_t fin, int b, int lane) {
+    PassMasks m{0, 0, 0, 0, 0};
+    uint32_t* buf = masks + 256 * b;
+    const uint32_t p0 = A + 8u * (uint32_t)lane;
+    if (!(p0 + 8u > base && p0 < end)) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) buf[8u * lane + u] = kEntryRes;
+        return m;
+    }
+    const uint32_t sh = (uint32_t)__cvta_generic_to_shared(buf);
+    const uint32_t r0 = (p0 > base ? p0 : base) - base;
+    uint32_t lo = 0, hi = ntok - 1;                        // last token starting at or before r0
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (stS[mid] <= r0) lo = mid;
+        else hi = mid - 1;
+    }
+    uint32_t ti = lo;
+    uint32_t next = ti + 1 < ntok ? stS[ti + 1] : 0xffffffffu;
+    uint32_t tk = tokS[ti];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const uint32_t P = p0 + (uint32_t)u;
+        const uint32_t slot = 8u * lane + u;
+        if (P < base || P >= end) {
+            buf[slot] = kEntryRes;
+            continue;
+        }
+        if (P - base >= next) {                            // the next token (tokens are at least 1 long)
+            ++ti;
+            next = ti + 1 < ntok ? stS[ti + 1] : 0xffffffffu;
+            tk = tokS[ti];
+        }
+        if (!(tk >> 31)) {
+            buf[slot] = kEntryRes | (tk & 0xffu);
+            continue;
+        }
+        const int32_t src = (int32_t)P - (int32_t)((tk & 0xffffu) + 1u);
+        if (src < 0) {                                     // a placeholder U_j before the part start
+            m.neg = 1;
+            buf[slot] = kEntryRes | sym_at(out, src);
+        } else if ((uint32_t)src < fin) {                  // final: copy its word into the entry
+            cp_async4(sh + 4u * slot, reinterpret_cast<const uint32_t*>(out) + ((uint32_t)src >> 1));
+            m.am |= 1u << u;
+            m.hm |= ((uint32_t)src & 1u) << u;
+        } else if ((uint32_t)src < A) {                    // inside the previous pass
+            buf[slot] = kEntryCross | ((uint32_t)src - (A - 256u));
+            m.cm |= 1u << u;
+        } else {                                           // inside this pass
+            buf[slot] = (uint32_t)src - A;
+            m.om |= 1u << u;
+        }
+    }
+    return m;
+}
+
 // Writes up to 256 consecutive tokens of the block (lane j loads tokens
 // 8j..8j+7).  Output positions go in passes of 256, lane l taking 8
 // consecutive ones (one 16-byte store); a position inside a match takes its
@@ -792,6 +870,10 @@ __device__ uint32_t seg_next(const WarpSmem& S, BitIn& b, bool active, uint64_t 
 // or a placeholder U_j before the part start) is loaded; a source inside the
 // pass is resolved by pointer jumping over the pass's entries in shared memory
 // (overlapping copies included, with no division).
+// PIPE: the passes are pipelined (the next pass's final sources copied
+// asynchronously while a pass resolves; k_inflate); else one pass at a time
+// with direct loads (k_sync, whose block-start search leaves fewer registers).
+template <bool PIPE>
 __device__ __forceinline__ int exec_range(WarpSmem& S, OutState& o, const uint32_t* tks, uint32_t ntok, bool check,
                                           uint64_t& block_n, int lane) {
     uint32_t t[8], L[8], sum = 0;
@@ -819,7 +901,6 @@ __device__ __forceinline__ int exec_range(WarpSmem& S, OutState& o, const uint32
         if (__any_sync(FULL, bad)) return CE_BYTE;
     }
     if (total == 0) return CE_OK;
-    uint32_t* stage = S.masks;                             // 256 entries: the positions of one pass
     uint32_t* tokS = S.masks + 512;                        // the batch's tokens
     uint32_t* stS = S.masks + 768;                         // their output offsets from base
     uint32_t s0 = incl - sum;
@@ -841,6 +922,87 @@ __device__ __forceinline__ int exec_range(WarpSmem& S, OutState& o, const uint32
     __syncwarp();
     bool bad = false;
     const uint32_t end = base + total;
+    if constexpr (PIPE) {
+    // Passes over [A, A + 256) with A a multiple of 8; lane l takes positions A + 8l .. A + 8l + 7.  A pass's
+    // entries live in one of two stage buffers of 256 words: kRes | symbol when resolved, else the index of
+    // the source inside the same pass (strictly earlier), or kCross | index of the source in the previous
+    // pass.  While pass j is resolved, pass j + 1 is built: each of its sources that is final already (before
+    // pass j: earlier passes and batches) is copied asynchronously -- the 32-bit word holding the symbol,
+    // straight into the source's entry -- so those loads overlap pass j's work.  Pointer jumping (each entry
+    // replaced by the entry it points to) then resolves a pass; its successor's cross entries are read from
+    // it next, before its buffer is reused.
+    constexpr uint32_t kRes = kEntryRes;
+    int cur = 0;
+    uint32_t A = base & ~7u;
+    PassMasks m = build_pass(S.masks, tokS, stS, ntok, base, end, out, A, base, cur, lane);
+    uint32_t neg = m.neg;
+    cp_async_commit();
+    for (;;) {
+        const uint32_t A1 = A + 256u;
+        const bool more = A1 < end;
+        PassMasks m1{0, 0, 0, 0, 0};
+        if (more) m1 = build_pass(S.masks, tokS, stS, ntok, base, end, out, A1, A > base ? A : base, cur ^ 1, lane);
+        neg |= m1.neg;
+        cp_async_commit();
+        cp_async_wait<1>();                                // this pass's copies (this lane's) have landed
+        uint32_t* buf = S.masks + 256 * cur;
+        const uint32_t p0 = A + 8u * (uint32_t)lane;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if ((m.am >> u) & 1u) {
+                const uint32_t w = buf[8u * lane + u];
+                buf[8u * lane + u] = kRes | (((m.hm >> u) & 1u) ? (w >> 16) : (w & 0xffffu));
+            }
+        __syncwarp();
+        uint32_t e[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) e[u] = buf[8u * lane + u];
+        uint32_t open = m.om;
+        while (__any_sync(FULL, open != 0)) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if ((open >> u) & 1u) e[u] = buf[e[u]];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if ((open >> u) & 1u) {
+                    buf[8u * lane + u] = e[u];
+                    if (e[u] & kRes) open &= ~(1u << u);
+                }
+            __syncwarp();
+        }
+        if (more) {                                        // the next pass's sources in this one
+            uint32_t* nb = S.masks + 256 * (cur ^ 1);
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if ((m1.cm >> u) & 1u) nb[8u * lane + u] = buf[nb[8u * lane + u] & 0xffu];
+        }
+        if (p0 >= base && p0 + 8u <= end) {                // all 8 mine: one 16-byte store
+            uint4 v;
+            v.x = (e[0] & 0xffffu) | (e[1] << 16);
+            v.y = (e[2] & 0xffffu) | (e[3] << 16);
+            v.z = (e[4] & 0xffffu) | (e[5] << 16);
+            v.w = (e[6] & 0xffffu) | (e[7] << 16);
+            *reinterpret_cast<uint4*>(out + p0) = v;
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t P = p0 + (uint32_t)u;
+                if (P >= base && P < end) out[P] = (uint16_t)e[u];
+            }
+        }
+        __syncwarp();                                      // this pass is final; its buffer may be reused
+        if (!more) break;
+        A = A1;
+        cur ^= 1;
+        m = m1;
+    }
+    cp_async_wait<0>();
+    if (neg) {
+        o.neg = true;
+        if (o.known) bad = true;
+    }
+    } else {
+    uint32_t* stage = S.masks;                             // 256 entries: the positions of one pass
     // passes over [A, A + 256) with A a multiple of 8; lane l takes positions A + 8l .. A + 8l + 7.  A source
     // before max(A, base) is final (earlier passes, earlier batches, or a placeholder before the part start)
     // and is loaded; a source inside the pass is a pointer to its stage entry, strictly earlier, so pointer
@@ -923,12 +1085,14 @@ __device__ __forceinline__ int exec_range(WarpSmem& S, OutState& o, const uint32
         }
         __syncwarp();                                      // this pass is final for the next one
     }
+    }
     if (__any_sync(FULL, bad)) return CE_DIST;
     o.n = base + total;
     block_n += total;
     return CE_OK;
 }
 
+template <bool PIPE>
 __device__ int par_block(WarpSmem& S, uint32_t* tokbuf, BitIn& br, OutState& o, bool check, uint64_t max_block,
                          uint64_t end_bit, uint64_t& block_n, int lane) {
     uint32_t* tb = tokbuf + (uint64_t)lane * kTokCap;
@@ -1017,7 +1181,7 @@ __device__ int par_block(WarpSmem& S, uint32_t* tokbuf, BitIn& br, OutState& o, 
             const uint32_t vs = __shfl_sync(FULL, my_vs, k), ve = __shfl_sync(FULL, my_ve, k);
             const uint32_t* rng = tokbuf + (uint64_t)k * kTokCap;
             for (uint32_t x = vs; x < ve; x += 256) {
-                const int e = exec_range(S, o, rng + x, ve - x < 256 ? ve - x : 256, check, block_n, lane);
+                const int e = exec_range<PIPE>(S, o, rng + x, ve - x < 256 ? ve - x : 256, check, block_n, lane);
                 if (e) return e;
                 if (max_block && block_n >= max_block) return CE_SIZE;
             }
@@ -1059,6 +1223,7 @@ __device__ int stored_block(BitIn& br, OutState& o, bool check, const uint32_t* 
 // be allowed bytes.  Huffman blocks are decoded by the whole warp in parallel
 // (par_block); a candidate block start first runs a short serial prefix, so
 // that false candidates fail after a few tokens.
+template <bool PIPE>
 __device__ int one_block(WarpSmem& S, uint32_t* tokbuf, BitIn& br, OutState& o, bool check, uint64_t min_block,
                          uint64_t max_block, bool candidate, uint64_t end_bit, uint32_t& final, int lane) {
     br.refill();
@@ -1089,7 +1254,7 @@ __device__ int one_block(WarpSmem& S, uint32_t* tokbuf, BitIn& br, OutState& o, 
             st = st == CE_MORE ? CE_MORE : (st == CE_OK ? CE_OK + 1000 : st);
         }
         if (st == CE_OK || st == CE_MORE)
-            st = par_block(S, tokbuf, br, o, check, max_block, end_bit, block_n, lane);
+            st = par_block<PIPE>(S, tokbuf, br, o, check, max_block, end_bit, block_n, lane);
         else if (st == CE_OK + 1000)
             st = CE_OK;
     }
@@ -1372,7 +1537,7 @@ __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
         state = CS_EMPTY;
     } else if (o.known || C.given) {          // the member start (empty context) or a known block start
         br.seek(C.lo);
-        const int st = one_block(S, tok, br, o, false, 0, 0, false, F.end_bit, final, lane);
+        const int st = one_block<false>(S, tok, br, o, false, 0, 0, false, F.end_bit, final, lane);
         sync = C.lo;
         resume = br.pos();
         if (st) {
@@ -1390,7 +1555,8 @@ __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
             br.seek(cand);
             o.n = 0;
             o.neg = false;
-            const int st = one_block(S, tok, br, o, true, p.min_block, p.max_block, true, F.end_bit, final, lane);
+            const int st = one_block<false>(S, tok, br, o, true, p.min_block, p.max_block, true, F.end_bit, final,
+                                            lane);
             if (st == CE_OK) {
                 state = CS_FOUND;
                 sync = cand;
@@ -1466,7 +1632,7 @@ __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
             }
             const bool check = !o.known && blocks <= (uint32_t)p.confirm_blocks;
             uint32_t fin = 0;
-            const int st = one_block(S, tok, br, o, check, 0, 0, false, F.end_bit, fin, lane);
+            const int st = one_block<true>(S, tok, br, o, check, 0, 0, false, F.end_bit, fin, lane);
             if (st) {
                 err = (check && st != CE_OVERFLOW) ? (uint32_t)CE_CONFIRM : (uint32_t)st;
                 break;
@@ -1731,9 +1897,6 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // 8 symbols -> 8 bytes (symbols past nv are taken as byte 0)
 __device__ __forceinline__ uint64_t translate8(const uint8_t* T, uint4 q, uint32_t nv, bool ph) {
