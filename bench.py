@@ -45,8 +45,8 @@ PLAIN_PARTS = 1024            # parts per file of the plain one-file-at-a-time f
 METRIC = "decompressed GB/s on 1 GB300 (batched vs plain), %HBM roofline"
 # DRAM bytes (read + write) of pass 1 per decompressed byte: ncu capture of k_sync and k_inflate on this
 # workload's batched run at 64 KiB parts and 4 warps per block (profiles/pass1_translate_crc_fastq256_batched.md:
-# 1.625 + 3.449 GB for 536,870,912 bytes out); None while the kernels differ from the capture
-PASS1_TRAFFIC_PER_OUT_BYTE = None
+# 1.624 + 3.376 GB for 536,870,912 bytes out); None while the kernels differ from the capture
+PASS1_TRAFFIC_PER_OUT_BYTE = 5.000e9 / 536870912
 
 
 def _peaks():
