@@ -203,6 +203,24 @@ int pgz_inspect_window(pgz_ctx* ctx, int part, uint8_t* host_dst /* 32768 bytes 
 int pgz_decompress_noalloc(const uint8_t* gz, uint64_t gz_len, uint8_t* out, uint64_t out_cap,
                            uint64_t* out_len, void* cuda_stream);
 
+/* DNA sequences in decoded symbols that may hold undetermined characters
+   (Appendix "Heuristic extraction of DNA sequences in DEFLATE block"; with
+   pgz_decompress_at this is random access to FASTQ reads, Section
+   "Heuristic determination of sequence-resolved blocks"): the maximal
+   non-overlapping substrings matching T D+ (U+ D+)* T, with T a newline or an
+   undetermined character, D one of A C G T N and U an undetermined character,
+   without the delimiting T's and at least min_len long.  A match needs both
+   delimiters inside the n symbols.
+   sym [device, n u16 symbols as pgz_decompress_at writes them: bit 15 set =
+   undetermined]; spans [device, 2 * max_spans u64]: spans[2k] = start,
+   spans[2k+1] = length | bit 63 if an undetermined symbol lies inside, in no
+   particular order.  *n_spans: spans found (the first max_spans are written);
+   *n_undetermined: those holding an undetermined symbol.  The block is
+   sequence-resolved (the paper's term) when *n_spans reaches the caller's
+   threshold and *n_undetermined is 0.  Stream-ordered; waits for the counts. */
+int pgz_extract_sequences(pgz_ctx* ctx, const uint16_t* sym, uint64_t n, uint32_t min_len, uint64_t* spans,
+                          uint64_t max_spans, uint64_t* n_spans, uint64_t* n_undetermined);
+
 /* One timed configuration of the autotuner. */
 typedef struct pgz_tune_entry {
     uint64_t chunk_bytes;       /* compressed bytes per part */

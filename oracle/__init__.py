@@ -221,3 +221,27 @@ def decompress_at(gz, start_bit: int, fill: int = ord("?"), allowed: np.ndarray 
                                 ctypes.byref(fd))
     return dict(status=e, sym=sym[:n.value].copy(), bytes=byts[:n.value].tobytes(), block_bit=bb.value,
                 first_determined=fd.value)
+
+
+# Appendix "Heuristic extraction of DNA sequences in DEFLATE block": T D+ (U+ D+)* T with T a newline or an
+# undetermined character, D a nucleotide, U an undetermined character; byte 0 stands for U in the mapped text
+# (real byte 0 becomes byte 1, which is neither).
+_SEQ_RE = None
+
+
+def sequences(sym, min_len: int = 0):
+    """The maximal non-overlapping substrings of decoded u16 symbols (bit 15 set: undetermined) that match
+    T D+ (U+ D+)* T, without their delimiting T's, that are at least ``min_len`` long, leftmost first.
+    A match needs its delimiters inside the array.  Returns [(start, length, contains_undetermined)]."""
+    import re
+    global _SEQ_RE
+    if _SEQ_RE is None:
+        _SEQ_RE = re.compile(rb"(?<=[\n\x00])[ACGTN]+(?:\x00+[ACGTN]+)*(?=[\n\x00])")
+    s = np.asarray(sym, dtype=np.uint16)
+    low = (s & 0xFF).astype(np.uint8)
+    txt = np.where((s & 0x8000) != 0, 0, np.where(low == 0, 1, low)).astype(np.uint8).tobytes()
+    out = []
+    for m in _SEQ_RE.finditer(txt):
+        if m.end() - m.start() >= min_len:
+            out.append((m.start(), m.end() - m.start(), b"\x00" in m.group()))
+    return out

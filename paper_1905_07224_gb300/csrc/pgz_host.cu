@@ -1317,6 +1317,26 @@ void pgz_index_free(pgz_index* idx) {
     delete idx;
 }
 
+int pgz_extract_sequences(pgz_ctx* ctx, const uint16_t* sym, uint64_t n, uint32_t min_len, uint64_t* spans,
+                          uint64_t max_spans, uint64_t* n_spans, uint64_t* n_undetermined) {
+    if (!ctx || (!sym && n) || (!spans && max_spans) || !n_spans || !n_undetermined) return PGZ_E_ARG;
+    cudaSetDevice(ctx->cfg.device);
+    *n_spans = *n_undetermined = 0;
+    if (cuda_status(ctx->fill_buf.ensure(std::max<size_t>(kWin, 2 * sizeof(unsigned long long))))) return PGZ_E_NOMEM;
+    unsigned long long* counts = ctx->fill_buf.as<unsigned long long>();
+    launch_sequences(sym, n, min_len, spans, max_spans, counts, ctx->stream);
+    if (cudaPeekAtLastError() != cudaSuccess) return PGZ_E_CUDA;
+    if (cuda_status(ctx->hdr.ensure(2 * sizeof(unsigned long long)))) return PGZ_E_NOMEM;
+    unsigned long long* h = ctx->hdr.as<unsigned long long>();
+    if (cudaMemcpyAsync(h, counts, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+        return PGZ_E_CUDA;
+    *n_spans = h[0];
+    *n_undetermined = h[1];
+    ctx->launches += 1;
+    return PGZ_OK;
+}
+
 int pgz_autotune(pgz_ctx* ctx, pgz_job* jobs, int n_jobs, const uint64_t* chunk_bytes, int n_chunk_bytes,
                  const int* warps_per_block, int n_wpb, int reps, pgz_tune_entry* entries, pgz_tune_entry* best) {
     if (!ctx || !jobs || n_jobs <= 0 || !chunk_bytes || !warps_per_block || n_chunk_bytes <= 0 || n_wpb <= 0 ||

@@ -118,6 +118,10 @@ void launch_translate(const FileDesc* files, ChunkDesc* chunks, int nchunks, uin
 uint64_t crc_segment_bytes();
 void launch_crc(FileDesc* files, int nfiles, uint64_t total_seg, const uint64_t* seg0, cudaStream_t s);
 void launch_finalize(FileDesc* files, int nfiles, cudaStream_t s);
+// DNA sequences among n u16 symbols: spans[2k] = start, spans[2k+1] = length | bit 63 if undetermined
+// symbols lie inside; counts[0] = spans found (may exceed max_spans), counts[1] = those with undetermined
+void launch_sequences(const uint16_t* sym, uint64_t n, uint32_t min_len, uint64_t* spans, uint64_t max_spans,
+                      unsigned long long* counts, cudaStream_t s);
 // ChunkDesc::nph and last_ph from the symbols of every finished part (statistics and inspection only)
 void launch_count_ph(ChunkDesc* chunks, int nchunks, const uint16_t* sym, cudaStream_t s);
 int kernels_per_run();

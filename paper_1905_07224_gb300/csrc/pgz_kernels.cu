@@ -2196,11 +2196,86 @@ __global__ void k_finalize(FileDesc* files, int nfiles) {
     if (crc != F.crc_expect) F.status = PGZ_E_CRC;
 }
 
+// ---------------------------------------------------------------------------
+// DNA sequences in a block with undetermined characters (Appendix "Heuristic
+// extraction of DNA sequences in DEFLATE block"): the maximal non-overlapping
+// substrings matching T D+ (U+ D+)* T, T a newline or an undetermined
+// character, D a nucleotide, U an undetermined character.  Within a maximal
+// run of D/U symbols there is at most one: from the first D preceded by a T
+// to the last D followed by a T (outside the run, only a newline is a T), if
+// the first comes before the last.  Each thread takes the runs that start in
+// its segment of kSeqSeg symbols (following a run past the segment's end).
+// ---------------------------------------------------------------------------
+constexpr uint32_t kSeqSeg = 1024;
+
+__device__ __forceinline__ uint32_t seq_class(uint16_t s) {      // 0 other, 1 D, 2 U, 3 newline
+    if (s & kPH) return 2;
+    const uint32_t b = s & 0xffu;
+    if (b == 'A' || b == 'C' || b == 'G' || b == 'T' || b == 'N') return 1;
+    return b == '\n' ? 3 : 0;
+}
+
+__global__ void __launch_bounds__(256) k_sequences(const uint16_t* __restrict__ sym, uint64_t n, uint32_t min_len,
+                                                   uint64_t* spans, uint64_t max_spans, unsigned long long* counts) {
+    const uint64_t a = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * kSeqSeg;
+    if (a >= n) return;
+    const uint64_t b = a + kSeqSeg < n ? a + kSeqSeg : n;
+    uint64_t p = a;
+    if (a > 0 && seq_class(sym[a - 1]) - 1u < 2u)                  // a run that began in an earlier segment
+        while (p < n && seq_class(sym[p]) - 1u < 2u) ++p;
+    while (p < b) {
+        uint32_t c = seq_class(sym[p]);
+        if (c - 1u >= 2u) {
+            ++p;
+            continue;
+        }
+        const uint64_t r0 = p;
+        const bool open_left = r0 > 0 && seq_class(sym[r0 - 1]) == 3;
+        uint64_t first = ~0ull, last = ~0ull, u_first = 0, u_last = 0, nu = 0;
+        uint32_t prev = 0;
+        for (; p < n; ++p) {
+            c = seq_class(sym[p]);
+            if (c - 1u >= 2u) break;
+            const uint32_t nx = p + 1 < n ? seq_class(sym[p + 1]) : 0u;
+            if (c == 1) {
+                if (first == ~0ull && (p == r0 ? open_left : prev == 2)) {
+                    first = p;
+                    u_first = nu;
+                }
+                if (nx == 2 || nx == 3) {                          // followed by a T
+                    last = p;
+                    u_last = nu;
+                }
+            } else {
+                ++nu;
+            }
+            prev = c;
+        }
+        if (first != ~0ull && last != ~0ull && last >= first && last - first + 1 >= min_len) {
+            const unsigned long long k = atomicAdd(&counts[0], 1ull);
+            const bool und = u_last > u_first;
+            if (und) atomicAdd(&counts[1], 1ull);
+            if (k < max_spans) {
+                spans[2 * k] = first;
+                spans[2 * k + 1] = (last - first + 1) | (und ? (1ull << 63) : 0ull);
+            }
+        }
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
 // host wrappers
 // ---------------------------------------------------------------------------
+void launch_sequences(const uint16_t* sym, uint64_t n, uint32_t min_len, uint64_t* spans, uint64_t max_spans,
+                      unsigned long long* counts, cudaStream_t s) {
+    cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), s);
+    if (n == 0) return;
+    const uint64_t threads = (n + kSeqSeg - 1) / kSeqSeg;
+    k_sequences<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(sym, n, min_len, spans, max_spans, counts);
+}
+
 static size_t warp_smem_bytes() { return sizeof(WarpSmem); }
 
 static int wpb_of(const KParams& p) { return p.wpb == 2 || p.wpb == 8 ? p.wpb : 4; }

@@ -100,6 +100,7 @@ def _load():
         "pgz_server_drain": (ctypes.c_int, [VP]),
         "pgz_server_pending": (ctypes.c_int, [VP]),
         "pgz_server_destroy": (None, [VP]),
+        "pgz_extract_sequences": (ctypes.c_int, [VP, VP, U64, ctypes.c_uint32, VP, U64, P(U64), P(U64)]),
         "pgz_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
@@ -124,7 +125,8 @@ EXPORTED = ["pgz_config_init", "pgz_create", "pgz_destroy", "pgz_decompress", "p
             "pgz_index_build", "pgz_index_info", "pgz_decompress_range", "pgz_index_free", "pgz_inspect_parts",
             "pgz_inspect_symbols", "pgz_inspect_window", "pgz_kernel_launches", "pgz_strerror",
             "pgz_decompress_noalloc", "pgz_autotune", "pgz_server_create", "pgz_server_add_file",
-            "pgz_server_submit", "pgz_server_poll", "pgz_server_drain", "pgz_server_pending", "pgz_server_destroy"]
+            "pgz_server_submit", "pgz_server_poll", "pgz_server_drain", "pgz_server_pending", "pgz_server_destroy",
+            "pgz_extract_sequences"]
 
 
 def pgz_strerror(status: int) -> str:
@@ -283,6 +285,13 @@ class Server:
         if self.h:
             lib().pgz_server_destroy(self.h)
             self.h = None
+
+
+def pgz_extract_sequences(ctx: int, sym_ptr: int, n: int, min_len: int, spans_ptr: int, max_spans: int):
+    """(status, n_spans, n_undetermined); device addresses (spans: 2 * max_spans u64)."""
+    a, b = U64(0), U64(0)
+    r = lib().pgz_extract_sequences(ctx, sym_ptr, n, min_len, spans_ptr, max_spans, ctypes.byref(a), ctypes.byref(b))
+    return r, a.value, b.value
 
 
 def pgz_index_build(ctx: int, gz_ptr: int, gz_len: int) -> int:

@@ -363,3 +363,50 @@ def test_false_block_start_is_caught_by_the_chain_check():
             assert s["false_syncs"] >= 1 and s["retries"] >= 1
         finally:
             ctx.close()
+
+
+def _spans(ctx, sym_np, min_len, max_spans=1 << 16):
+    import torch
+    d = torch.from_numpy(sym_np.astype(np.int16).view(np.int16).copy()).cuda() if sym_np.size else \
+        torch.zeros(1, dtype=torch.int16, device="cuda")
+    sp = torch.zeros(2 * max_spans, dtype=torch.int64, device="cuda")
+    st, n, nu = ctx.pgz.pgz_extract_sequences(ctx.h, d.data_ptr(), sym_np.size, min_len, sp.data_ptr(), max_spans)
+    assert st == 0
+    a = sp[:2 * min(n, max_spans)].cpu().numpy().view(np.uint64).reshape(-1, 2)
+    got = sorted((int(s), int(l & ((1 << 63) - 1)), bool(l >> 63)) for s, l in a)
+    return got, n, nu
+
+
+def test_sequence_heuristic_matches_the_oracle():
+    """Appendix "Heuristic extraction of DNA sequences in DEFLATE block" on the GPU against the oracle: random
+    symbol strings (runs across the kernel's segments included) and the symbols of a random access into FASTQ
+    (with undetermined characters)."""
+    ctx = Ctx()
+    try:
+        rng = np.random.default_rng(11)
+        alphabet = np.array([ord(c) for c in "ACGTN\nx"] + [0x8000 | 5, 0], dtype=np.uint16)
+        for size, weights in [(5000, None), (70000, [8, 8, 8, 8, 1, 2, 3, 4, 1])]:
+            p = None if weights is None else np.array(weights, float) / sum(weights)
+            s = alphabet[rng.choice(alphabet.size, size=size, p=p)]
+            for min_len in (0, 3, 20):
+                want = oracle.sequences(s, min_len)
+                got, n, nu = _spans(ctx, s, min_len)
+                assert got == want and n == len(want) and nu == sum(u for _, _, u in want), (size, min_len)
+        # random access into FASTQ: the paper's use of the heuristic
+        data = synth.fastq(1 << 20, 100, 0.001, 12)
+        gz = synth.gzip_compress(data, 6)
+        for start in (300_000 * 8, 41_234 * 8 + 3):
+            r = oracle.decompress_at(gz, start, cap=len(data) + 4096)
+            assert r["status"] == 0
+            want = oracle.sequences(r["sym"], 50)
+            got, n, nu = _spans(ctx, r["sym"], 50)
+            assert got == want and n == len(want)
+            # reads are found (an undetermined newline can also join a read to quality characters that look
+            # like bases: the heuristic's false positives, as the paper notes)
+            assert n > 100 and any(l == 100 for _, l, _ in want)
+        # fewer slots than spans: the count is still complete
+        s = np.array([ord(c) for c in "\nACGT" * 50 + "\n"], dtype=np.uint16)
+        got, n, nu = _spans(ctx, s, 1, max_spans=7)
+        assert n == 50 and len(got) == 7
+    finally:
+        ctx.close()

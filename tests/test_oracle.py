@@ -371,3 +371,58 @@ def test_window_chain_pieces():
     assert np.array_equal(nw[:32768 - 1000], w[1000:]) and np.array_equal(nw[32768 - 1000:], out)
     long = rng.integers(32, 127, 40000).astype(np.uint16)
     assert np.array_equal(oracle.next_window(w, long), long[-32768:].astype(np.uint8))
+
+
+def _seq_syms(text: str):
+    """'?' stands for an undetermined symbol."""
+    return np.array([0x8000 | 7 if ch == "?" else ord(ch) for ch in text], dtype=np.uint16)
+
+
+def test_sequence_heuristic_on_hand_cases():
+    # Appendix "Heuristic extraction of DNA sequences in DEFLATE block": T D+ (U+ D+)* T, T = newline or U
+    cases = {
+        "\nACGT\n": [(1, 4, False)],
+        "x\nACGT\nIIII": [(2, 4, False)],
+        "\nAC??GT\n": [(1, 6, True)],
+        "?ACG?TTx?GG\n": [(1, 3, False), (9, 2, False)],     # TT is followed by 'x': the match stops at G
+        "+ACGT\n": [],                                       # a quality-like prefix is not a delimiter
+        "\nACGTF\n": [],
+        "\n??ACG\n": [(3, 3, False)],
+        "ACGT\n": [],                                        # no delimiter before the array start
+        "\nACGT": [],                                        # nor after its end
+        "\nA\n\nC?N\n": [(1, 1, False), (4, 3, True)],
+        "\n?\n": [],
+    }
+    for text, want in cases.items():
+        assert oracle.sequences(_seq_syms(text)) == want, text
+    assert oracle.sequences(_seq_syms("\nAC??GT\n\nACGTACGT\n"), min_len=8) == [(9, 8, False)]
+
+
+def test_sequence_heuristic_brute_force():
+    """Against the definition: every substring whose both neighbours are T's and whose text is D+(U+D+)*,
+    keeping the maximal ones left to right without overlap."""
+    rng = np.random.default_rng(5)
+    alphabet = "ACGT?\nx"
+    for _ in range(300):
+        text = "".join(alphabet[k] for k in rng.integers(0, len(alphabet), size=int(rng.integers(1, 40))))
+        n = len(text)
+
+        def body_ok(a, b):
+            seg = text[a:b + 1]
+            if not seg or seg[0] == "?" or seg[-1] == "?":
+                return False
+            return all(c in "ACGTN?" for c in seg)
+
+        def delim(i):
+            return 0 <= i < n and text[i] in "\n?"
+
+        want, i = [], 0
+        while i < n:
+            ends = [b for b in range(i, n) if delim(i - 1) and delim(b + 1) and body_ok(i, b)]
+            if ends:
+                b = max(ends)
+                want.append((i, b - i + 1, "?" in text[i:b + 1]))
+                i = b + 1
+            else:
+                i += 1
+        assert oracle.sequences(_seq_syms(text)) == want, text
