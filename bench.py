@@ -206,16 +206,14 @@ def run_pgz(args, rank, world):
     # and pass-1 CTA shape chosen by the library's autotuner on these files (unless --chunk-bytes fixes them)
     ctx_b = pgz.pgz_create(pgz.pgz_config_init(device=dev, cuda_stream=stream.cuda_stream, n_chunks=0,
                                                chunk_bytes=args.chunk_bytes or CHUNK_BYTES,
-                                               warps_per_block=args.warps_per_block))
+                                               warps_per_block=args.warps_per_block,
+                                               exec_pipelined=args.exec_pipelined))
     tune = None
     if not args.chunk_bytes:
-        st, entries, best = pgz.pgz_autotune(ctx_b, jobs, TUNE_CHUNKS, TUNE_WPB, 2)
-        if st != 0:
-            raise RuntimeError(f"pgz_autotune failed: {pgz.pgz_strerror(st)}")
-        tune = {"best": [best["chunk_bytes"], best["warps_per_block"]],
-                "ms": {f"{e['chunk_bytes'] >> 10}K/{e['warps_per_block']}w": round(e["ms"], 2) for e in entries}}
+        tune = autotune(pgz, ctx_b, jobs, TUNE_CHUNKS, TUNE_WPB)
     chunk_bytes = tune["best"][0] if tune else args.chunk_bytes
     wpb = tune["best"][1] if tune else args.warps_per_block
+    xp = tune["best"][2] if tune else args.exec_pipelined
     batch = pgz.Batch(ctx_b, jobs)
 
     def step_batched():
@@ -279,7 +277,8 @@ def run_pgz(args, rank, world):
     # ---- end to end, pipelined through the library's request loop (pgz_server_*): each file runs in its own
     # slot (stream), so the second file's upload overlaps the first file's decode and each download overlaps
     # what is still decoding; the slots' runs share the GPU as the batch does
-    srv = pgz.Server(pgz.pgz_config_init(device=dev, chunk_bytes=chunk_bytes, warps_per_block=wpb), slots=len(files))
+    srv = pgz.Server(pgz.pgz_config_init(device=dev, chunk_bytes=chunk_bytes, warps_per_block=wpb,
+                                         exec_pipelined=xp), slots=len(files))
     ids = [srv.add_file(gz_dev[k].data_ptr(), len(g)) for k, (_, _, g) in enumerate(files)]
     up, down = torch.cuda.Stream(), torch.cuda.Stream()
 
@@ -358,7 +357,7 @@ def run_pgz(args, rank, world):
         "data": "synthetic",
         "config": {"workload": desc, "form": "batched (all files of the step in one graph-captured run)",
                    "files": len(files), "out_bytes_per_step": total_out, "in_bytes_per_step": total_in,
-                   "chunk_bytes": chunk_bytes, "warps_per_block": wpb, "parts": batch_parts,
+                   "chunk_bytes": chunk_bytes, "warps_per_block": wpb, "exec_pipelined": xp, "parts": batch_parts,
                    "l2": "inputs (%.0f MB) and outputs (%.0f MB) larger than L2" % (total_in / 1e6, total_out / 1e6),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "compressed_MBps": round(world * total_in / (ms * 1e-3) / 1e6, 1),
@@ -401,6 +400,17 @@ def _stage_line(stage, total_in, total_out, window_bytes, hbm):
                              "frac": round(total_out / c / 1e9 / hbm, 4) if c else None}}
 
 
+def autotune(pgz, ctx, jobs, chunks, wpbs):
+    """The library's autotuner over part size x pass-1 CTA shape x pass-1 execution form on these jobs; the
+    context keeps the fastest configuration.  Returns {"best": [chunk, wpb, pipelined], "ms": {...}}."""
+    st, entries, best = pgz.pgz_autotune(ctx, jobs, chunks, wpbs, 2, sweep_exec=True)
+    if st != 0:
+        raise RuntimeError(f"pgz_autotune failed: {pgz.pgz_strerror(st)}")
+    return {"best": [best["chunk_bytes"], best["warps_per_block"], best["exec_pipelined"]],
+            "ms": {f"{e['chunk_bytes'] >> 10}K/{e['warps_per_block']}w/{'p' if e['exec_pipelined'] else 's'}":
+                   round(e["ms"], 2) for e in entries}}
+
+
 def run_tune4g(args):
     """4 GiB FASTQ (150 bp, 1 % N, seed 2) at gzip -6, ISIZE = 0: the autotuner's sweep of part size x pass-1
     CTA shape, then the chosen pair timed."""
@@ -418,10 +428,7 @@ def run_tune4g(args):
     d_in = torch.from_numpy(np.frombuffer(gz, dtype=np.uint8).copy()).cuda()
     d_out = torch.empty(len(raw) + 4096, dtype=torch.uint8, device="cuda")
     chunks = [32 << 10, 64 << 10, 128 << 10, 256 << 10, 512 << 10, 1 << 20, 2 << 20, 4 << 20]
-    st, entries, best = pgz.pgz_autotune(ctx, [(d_in.data_ptr(), len(gz), d_out.data_ptr(), d_out.numel())], chunks,
-                                         [2, 4, 8], 2)
-    if st != 0:
-        raise RuntimeError(f"pgz_autotune failed: {pgz.pgz_strerror(st)}")
+    tune = autotune(pgz, ctx, [(d_in.data_ptr(), len(gz), d_out.data_ptr(), d_out.numel())], chunks, [2, 4, 8])
     ref = torch.from_numpy(np.frombuffer(raw, dtype=np.uint8).copy()).cuda()
     if not torch.equal(d_out[:len(raw)], ref):
         raise RuntimeError("output mismatch")
@@ -442,8 +449,7 @@ def run_tune4g(args):
     hbm = _peaks().get("hbm_gbs") or 6800.0
     line = {"workload": "4 GiB synthetic FASTQ (150 bp, 1 % N, seed 2), gzip -6 (parallel pieces, one member), "
                         "ISIZE 0", "in_bytes": len(gz), "out_bytes": len(raw), "isize": int.from_bytes(gz[-4:], "little"),
-            "make_s": round(t_make, 1), "tune": [{**e, "ms": round(e["ms"], 3)} for e in entries],
-            "best": {**best, "ms": round(best["ms"], 3)}, "parts": s["chunks"],
+            "make_s": round(t_make, 1), "tune": tune["ms"], "best": tune["best"], "parts": s["chunks"],
             "value": round(len(raw) / (ms * 1e-3) / 1e9, 3), "unit": "GB/s", "ms_per_call": round(ms, 3),
             "placeholder_fraction": round(s["placeholders"] / max(1, s["symbols"]), 4),
             "false_syncs": s["false_syncs"], "retries": s["retries"], "empty_parts": s["empty_chunks"]}
@@ -490,7 +496,12 @@ def run_batch512(args):
             d_out[k].zero_()
 
     ctx = pgz.pgz_create(pgz.pgz_config_init(device=0, cuda_stream=stream.cuda_stream,
-                                             chunk_bytes=args.chunk_bytes or CHUNK_BYTES))
+                                             chunk_bytes=args.chunk_bytes or CHUNK_BYTES,
+                                             warps_per_block=args.warps_per_block,
+                                             exec_pipelined=args.exec_pipelined))
+    tune = None
+    if not args.chunk_bytes:
+        tune = autotune(pgz, ctx, jobs, [64 << 10, 128 << 10, 256 << 10], [2, 4])
     batch = pgz.Batch(ctx, jobs)
 
     def step_batched():
@@ -504,23 +515,30 @@ def run_batch512(args):
     r, _, s = pgz.pgz_decompress_batch(ctx, jobs, stats=True)
     batch.free()
 
+    # plain: one call per member on a context of its own at the library's default part size, which suits
+    # one member at a time better than the batch's tuned (larger) parts
+    ctx_p = pgz.pgz_create(pgz.pgz_config_init(device=0, cuda_stream=stream.cuda_stream,
+                                               chunk_bytes=CHUNK_BYTES))
+
     def step_plain():
         for k, (gp, gl, op, oc) in enumerate(jobs):
-            st, n, _ = pgz.pgz_decompress(ctx, gp, gl, op, oc)
+            st, n, _ = pgz.pgz_decompress(ctx_p, gp, gl, op, oc)
             if st != 0:
                 raise RuntimeError(f"pgz_decompress failed: {pgz.pgz_strerror(st)}")
 
     step_plain()
     check()
     ms_p = timed(step_plain)
+    pgz.pgz_destroy(ctx_p)
     pgz.pgz_destroy(ctx)
     return {"workload": "512 synthetic members, log-uniform 64 KiB-64 MiB (seed 3), FASTQ/Markov, gzip -1/-6/-9",
             "in_bytes": total_in, "out_bytes": total_out, "make_s": round(t_make, 1), "parts": s["chunks"],
             "batched": {"value": round(total_out / (ms_b * 1e-3) / 1e9, 3), "ms_per_step": round(ms_b, 3),
                         "form": "one graph-captured run, device work queue"},
             "plain": {"value": round(total_out / (ms_p * 1e-3) / 1e9, 3), "ms_per_step": round(ms_p, 3),
-                      "form": "one pgz_decompress per member"},
-            "unit": "GB/s", "stages_ms_batched": {k: round(v, 3) for k, v in s.items() if k.startswith("ms_")}}
+                      "form": "one pgz_decompress per member", "chunk_bytes": CHUNK_BYTES},
+            "unit": "GB/s", "stages_ms_batched": {k: round(v, 3) for k, v in s.items() if k.startswith("ms_")},
+            "autotune": tune}
 
 
 def run_served(args):
@@ -708,6 +726,8 @@ def main():
     ap.add_argument("--chunk-bytes", type=int, default=0, help="fixed part size (default: autotuned)")
     ap.add_argument("--warps-per-block", type=int, default=4, choices=[2, 4, 8],
                     help="pass-1 CTA shape with a fixed --chunk-bytes or --profile-case")
+    ap.add_argument("--exec-pipelined", type=int, default=0, choices=[0, 1],
+                    help="pass-1 execution form with a fixed --chunk-bytes (default: autotuned)")
     ap.add_argument("--profile-case", default=None, metavar="MIB:LEVEL:CALLS|batch:CALLS",
                     help="run one checked case for an ncu capture and print its stage times: one FASTQ file, or "
                          "the benchmark's two files as one batch")

@@ -72,6 +72,8 @@ typedef struct pgz_config {
     uint64_t dev_mem_budget;    /* upper bound on scratch bytes; 0 = none */
     uint64_t spin_cap;          /* reserved for bounded device waits; 0 = default */
     int warps_per_block;        /* CTA shape of the pass-1 kernels: 2, 4 or 8 warps (one part each); 0 = 4 */
+    int exec_pipelined;         /* 1: pass 1 executes tokens in pipelined passes (faster when sources lie far
+                                   back), 0: one pass at a time (default); pgz_autotune can choose */
 } pgz_config;
 
 /* per-call statistics; the ms_* fields are CUDA-event times of the stages */
@@ -225,27 +227,31 @@ int pgz_extract_sequences(pgz_ctx* ctx, const uint16_t* sym, uint64_t n, uint32_
 typedef struct pgz_tune_entry {
     uint64_t chunk_bytes;       /* compressed bytes per part */
     int warps_per_block;        /* CTA shape of the pass-1 kernels */
+    int exec_pipelined;         /* pass-1 token execution (pgz_config.exec_pipelined) */
     int status;                 /* pgz_status of the calls with this configuration */
-    float ms;                   /* median CUDA-event time of one pgz_decompress call */
+    float ms;                   /* median CUDA-event time of one pgz_decompress_batch call */
 } pgz_tune_entry;
 
 /* Autotuner.  The number of parts n is a free parameter of the method
    (Section "Full file decompression in two passes": n roughly equal parts);
    this picks the part size and the pass-1 CTA shape for the caller's data.
-   For every pair chunk_bytes[a] x warps_per_block[b] it runs
+   For every pair chunk_bytes[a] x warps_per_block[b] -- and, with
+   sweep_exec, both forms of pass-1 token execution -- it runs
    pgz_decompress_batch on the n_jobs jobs (device buffers, the batch rules;
    one job is one member) once untimed and reps times timed (CUDA events on the
-   context's stream), and then sets the context's chunk_bytes and
-   warps_per_block (n_chunks = 0) to the pair with the smallest median time
-   among those whose calls returned PGZ_OK for every job.
-   entries: n_chunk_bytes * n_wpb results, row-major by chunk size (NULL: not
-   returned); best: the chosen pair (NULL: not returned).  The jobs' outputs and
+   context's stream), and then sets the context's chunk_bytes, warps_per_block
+   and exec_pipelined (n_chunks = 0) to the configuration with the smallest
+   median time among those whose calls returned PGZ_OK for every job.
+   entries: n_chunk_bytes * n_wpb * (sweep_exec ? 2 : 1) results, ordered by
+   chunk size, then CTA shape, then execution form (NULL: not returned);
+   best: the chosen configuration (NULL: not returned).  The jobs' outputs and
    statuses are those of the last call.  Returns PGZ_E_ARG for empty lists,
    chunk sizes below 4 KiB, CTA shapes other than 2, 4 or 8 warps, or reps < 1;
    if no pair succeeded, the first failing status (the context is left
    unchanged). */
 int pgz_autotune(pgz_ctx* ctx, pgz_job* jobs, int n_jobs, const uint64_t* chunk_bytes, int n_chunk_bytes,
-                 const int* warps_per_block, int n_wpb, int reps, pgz_tune_entry* entries, pgz_tune_entry* best);
+                 const int* warps_per_block, int n_wpb, int sweep_exec, int reps, pgz_tune_entry* entries,
+                 pgz_tune_entry* best);
 
 /* ---------------------------------------------------------------------------
    Serving: a request loop with continuous batching.  Registered members stay

@@ -903,6 +903,7 @@ void pgz_config_init(pgz_config* cfg) {
     cfg->dev_mem_budget = 0;
     cfg->spin_cap = 0;
     cfg->warps_per_block = 4;
+    cfg->exec_pipelined = 0;
 }
 
 int pgz_create(pgz_ctx** out, const pgz_config* cfg) {
@@ -913,6 +914,7 @@ int pgz_create(pgz_ctx** out, const pgz_config* cfg) {
     if (cfg->warps_per_block != 0 && cfg->warps_per_block != 2 && cfg->warps_per_block != 4 &&
         cfg->warps_per_block != 8)
         return PGZ_E_ARG;
+    if (cfg->exec_pipelined != 0 && cfg->exec_pipelined != 1) return PGZ_E_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) return PGZ_E_CUDA;
     if (cudaSetDevice(cfg->device) != cudaSuccess) return PGZ_E_CUDA;
@@ -927,6 +929,7 @@ int pgz_create(pgz_ctx** out, const pgz_config* cfg) {
     ctx->kp.max_block = cfg->max_block;
     ctx->kp.confirm_blocks = cfg->confirm_blocks;
     ctx->kp.wpb = cfg->warps_per_block ? cfg->warps_per_block : 4;
+    ctx->kp.pipe = cfg->exec_pipelined;
     upload_crc_tables();
     for (int k = 0; k < 8; ++k) cudaEventCreate(&ctx->ev[k]);
     if (cudaGetLastError() != cudaSuccess) {
@@ -1338,7 +1341,8 @@ int pgz_extract_sequences(pgz_ctx* ctx, const uint16_t* sym, uint64_t n, uint32_
 }
 
 int pgz_autotune(pgz_ctx* ctx, pgz_job* jobs, int n_jobs, const uint64_t* chunk_bytes, int n_chunk_bytes,
-                 const int* warps_per_block, int n_wpb, int reps, pgz_tune_entry* entries, pgz_tune_entry* best) {
+                 const int* warps_per_block, int n_wpb, int sweep_exec, int reps, pgz_tune_entry* entries,
+                 pgz_tune_entry* best) {
     if (!ctx || !jobs || n_jobs <= 0 || !chunk_bytes || !warps_per_block || n_chunk_bytes <= 0 || n_wpb <= 0 ||
         reps < 1)
         return PGZ_E_ARG;
@@ -1348,45 +1352,53 @@ int pgz_autotune(pgz_ctx* ctx, pgz_job* jobs, int n_jobs, const uint64_t* chunk_
         if (warps_per_block[b] != 2 && warps_per_block[b] != 4 && warps_per_block[b] != 8) return PGZ_E_ARG;
     cudaSetDevice(ctx->cfg.device);
     const pgz_config saved = ctx->cfg;
-    const int saved_wpb = ctx->kp.wpb;
+    const KParams saved_kp = ctx->kp;
+    const int nx = sweep_exec ? 2 : 1;
     pgz_tune_entry pick{};
     pick.status = PGZ_E_ARG;
     int first_bad = PGZ_OK;
     std::vector<float> t((size_t)reps);
     for (int a = 0; a < n_chunk_bytes; ++a) {
         for (int b = 0; b < n_wpb; ++b) {
-            pgz_tune_entry e{};
-            e.chunk_bytes = chunk_bytes[a];
-            e.warps_per_block = warps_per_block[b];
-            ctx->cfg.n_chunks = 0;
-            ctx->cfg.chunk_bytes = e.chunk_bytes;
-            ctx->cfg.warps_per_block = e.warps_per_block;
-            ctx->kp.wpb = e.warps_per_block;
-            e.status = pgz_decompress_batch(ctx, n_jobs, jobs, nullptr);   // settles buffers and plan
-            for (int r = 0; r < reps && e.status == PGZ_OK; ++r) {
-                cudaEventRecord(ctx->ev[6], ctx->stream);
-                e.status = pgz_decompress_batch(ctx, n_jobs, jobs, nullptr);
-                cudaEventRecord(ctx->ev[7], ctx->stream);
-                if (cudaEventSynchronize(ctx->ev[7]) != cudaSuccess) e.status = PGZ_E_CUDA;
-                else cudaEventElapsedTime(&t[(size_t)r], ctx->ev[6], ctx->ev[7]);
+            for (int x = 0; x < nx; ++x) {
+                pgz_tune_entry e{};
+                e.chunk_bytes = chunk_bytes[a];
+                e.warps_per_block = warps_per_block[b];
+                e.exec_pipelined = sweep_exec ? x : saved.exec_pipelined;
+                ctx->cfg.n_chunks = 0;
+                ctx->cfg.chunk_bytes = e.chunk_bytes;
+                ctx->cfg.warps_per_block = e.warps_per_block;
+                ctx->cfg.exec_pipelined = e.exec_pipelined;
+                ctx->kp.wpb = e.warps_per_block;
+                ctx->kp.pipe = e.exec_pipelined;
+                e.status = pgz_decompress_batch(ctx, n_jobs, jobs, nullptr);   // settles buffers and plan
+                for (int r = 0; r < reps && e.status == PGZ_OK; ++r) {
+                    cudaEventRecord(ctx->ev[6], ctx->stream);
+                    e.status = pgz_decompress_batch(ctx, n_jobs, jobs, nullptr);
+                    cudaEventRecord(ctx->ev[7], ctx->stream);
+                    if (cudaEventSynchronize(ctx->ev[7]) != cudaSuccess) e.status = PGZ_E_CUDA;
+                    else cudaEventElapsedTime(&t[(size_t)r], ctx->ev[6], ctx->ev[7]);
+                }
+                if (e.status == PGZ_OK) {
+                    std::sort(t.begin(), t.end());
+                    e.ms = t[(size_t)reps / 2];
+                    if (pick.status != PGZ_OK || e.ms < pick.ms) pick = e;
+                } else if (first_bad == PGZ_OK) {
+                    first_bad = e.status;
+                }
+                if (entries) entries[((size_t)a * n_wpb + b) * nx + x] = e;
             }
-            if (e.status == PGZ_OK) {
-                std::sort(t.begin(), t.end());
-                e.ms = t[(size_t)reps / 2];
-                if (pick.status != PGZ_OK || e.ms < pick.ms) pick = e;
-            } else if (first_bad == PGZ_OK) {
-                first_bad = e.status;
-            }
-            if (entries) entries[(size_t)a * n_wpb + b] = e;
         }
     }
     ctx->cfg = saved;
-    ctx->kp.wpb = saved_wpb;
+    ctx->kp = saved_kp;
     if (pick.status != PGZ_OK) return first_bad;
     ctx->cfg.n_chunks = 0;
     ctx->cfg.chunk_bytes = pick.chunk_bytes;
     ctx->cfg.warps_per_block = pick.warps_per_block;
+    ctx->cfg.exec_pipelined = pick.exec_pipelined;
     ctx->kp.wpb = pick.warps_per_block;
+    ctx->kp.pipe = pick.exec_pipelined;
     if (best) *best = pick;
     return PGZ_OK;
 }

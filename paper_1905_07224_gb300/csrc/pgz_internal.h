@@ -40,6 +40,8 @@ struct KParams {
     uint32_t max_block;
     int confirm_blocks;
     int wpb;               // warps per block of the pass-1 kernels: 2, 4 or 8 (0: 4)
+    int pipe;              // k_inflate executes tokens in pipelined passes (1) or one pass at a time (0)
+    int pad;
 };
 
 // one gzip member

@@ -871,8 +871,10 @@ __device__ __forceinline__ PassMasks build_pass(uint32_t* masks, const uint32_t*
 // pass is resolved by pointer jumping over the pass's entries in shared memory
 // (overlapping copies included, with no division).
 // PIPE: the passes are pipelined (the next pass's final sources copied
-// asynchronously while a pass resolves; k_inflate); else one pass at a time
-// with direct loads (k_sync, whose block-start search leaves fewer registers).
+// asynchronously while a pass resolves); else one pass at a time with direct
+// loads.  k_sync always takes the second (its block-start search leaves fewer
+// registers); k_inflate takes either (KParams::pipe): which is faster depends
+// on the data (how far back the sources lie), so the autotuner can choose.
 template <bool PIPE>
 __device__ __forceinline__ int exec_range(WarpSmem& S, OutState& o, const uint32_t* tks, uint32_t ntok, bool check,
                                           uint64_t& block_n, int lane) {
@@ -1591,7 +1593,7 @@ __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
 // ---------------------------------------------------------------------------
 // k_inflate: pass 1 of each part up to the next part's block start
 // ---------------------------------------------------------------------------
-template <int WPB>
+template <int WPB, bool PIPE>
 __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
     k_inflate(const FileDesc* __restrict__ files, ChunkDesc* chunks, int nchunks, uint16_t* symbuf, uint32_t* tokbuf,
               uint32_t* queue, KParams p) {
@@ -1632,7 +1634,7 @@ __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
             }
             const bool check = !o.known && blocks <= (uint32_t)p.confirm_blocks;
             uint32_t fin = 0;
-            const int st = one_block<true>(S, tok, br, o, check, 0, 0, false, F.end_bit, fin, lane);
+            const int st = one_block<PIPE>(S, tok, br, o, check, 0, 0, false, F.end_bit, fin, lane);
             if (st) {
                 err = (check && st != CE_OVERFLOW) ? (uint32_t)CE_CONFIRM : (uint32_t)st;
                 break;
@@ -2295,10 +2297,12 @@ static int pass1_resident_blocks_t() {
         int sms = 0, per_sm_sync = 0, per_sm_inflate = 0;
         const bool ok =
             cudaFuncSetAttribute(k_sync<WPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
-            cudaFuncSetAttribute(k_inflate<WPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
+            cudaFuncSetAttribute(k_inflate<WPB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+                cudaSuccess &&
+            cudaFuncSetAttribute(k_inflate<WPB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_sync, k_sync<WPB>, 32 * WPB, smem) == cudaSuccess &&
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_inflate, k_inflate<WPB>, 32 * WPB, smem) ==
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_inflate, k_inflate<WPB, false>, 32 * WPB, smem) ==
                 cudaSuccess;
         const int v = std::max(1, sms) * std::max(1, std::min(per_sm_sync, per_sm_inflate));
         if (!ok) {
@@ -2331,7 +2335,8 @@ static void launch_pass1(bool sync, const FileDesc* files, ChunkDesc* chunks, in
     const int grid = pass1_warps(nchunks, WPB) / WPB;
     const size_t smem = WPB * warp_smem_bytes();
     if (sync) k_sync<WPB><<<grid, 32 * WPB, smem, s>>>(files, chunks, nchunks, sym, tok, queue, p);
-    else k_inflate<WPB><<<grid, 32 * WPB, smem, s>>>(files, chunks, nchunks, sym, tok, queue, p);
+    else if (p.pipe) k_inflate<WPB, true><<<grid, 32 * WPB, smem, s>>>(files, chunks, nchunks, sym, tok, queue, p);
+    else k_inflate<WPB, false><<<grid, 32 * WPB, smem, s>>>(files, chunks, nchunks, sym, tok, queue, p);
 }
 
 static void launch_pass1_any(bool sync, const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym,

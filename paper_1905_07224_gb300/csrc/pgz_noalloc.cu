@@ -169,6 +169,7 @@ extern "C" int pgz_decompress_noalloc(const uint8_t* gz, uint64_t gz_len, uint8_
     kp.max_block = cfg.max_block;
     kp.confirm_blocks = cfg.confirm_blocks;
     kp.wpb = 4;
+    kp.pipe = 0;
 
     const uint64_t csize = gz_len - 8 - s0, end_bit = (gz_len - 8) * 8;
     uint64_t n = (csize + kNaPartBytes - 1) / kNaPartBytes;

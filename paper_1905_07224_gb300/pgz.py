@@ -28,7 +28,8 @@ class pgz_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("cuda_stream", VP), ("chunk_bytes", U64), ("n_chunks", ctypes.c_int),
                 ("threads_per_chunk", ctypes.c_int), ("allowed", ctypes.c_uint8 * 32),
                 ("confirm_blocks", ctypes.c_int), ("min_block", ctypes.c_uint32), ("max_block", ctypes.c_uint32),
-                ("dev_mem_budget", U64), ("spin_cap", U64), ("warps_per_block", ctypes.c_int)]
+                ("dev_mem_budget", U64), ("spin_cap", U64), ("warps_per_block", ctypes.c_int),
+                ("exec_pipelined", ctypes.c_int)]
 
 
 class pgz_stats(ctypes.Structure):
@@ -42,8 +43,8 @@ class pgz_stats(ctypes.Structure):
 
 
 class pgz_tune_entry(ctypes.Structure):
-    _fields_ = [("chunk_bytes", U64), ("warps_per_block", ctypes.c_int), ("status", ctypes.c_int),
-                ("ms", ctypes.c_float)]
+    _fields_ = [("chunk_bytes", U64), ("warps_per_block", ctypes.c_int), ("exec_pipelined", ctypes.c_int),
+                ("status", ctypes.c_int), ("ms", ctypes.c_float)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -92,7 +93,8 @@ def _load():
         "pgz_kernel_launches": (U64, [VP]),
         "pgz_decompress_noalloc": (ctypes.c_int, [VP, U64, VP, U64, P(U64), VP]),
         "pgz_autotune": (ctypes.c_int, [VP, P(pgz_job), ctypes.c_int, P(U64), ctypes.c_int, P(ctypes.c_int),
-                                        ctypes.c_int, ctypes.c_int, P(pgz_tune_entry), P(pgz_tune_entry)]),
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, P(pgz_tune_entry),
+                                        P(pgz_tune_entry)]),
         "pgz_server_create": (ctypes.c_int, [P(VP), P(pgz_config), ctypes.c_int, U64]),
         "pgz_server_add_file": (ctypes.c_int, [VP, VP, U64, P(ctypes.c_int)]),
         "pgz_server_submit": (ctypes.c_int, [VP, P(pgz_request)]),
@@ -223,16 +225,16 @@ class Batch:
             self.h = None
 
 
-def pgz_autotune(ctx: int, jobs, chunk_bytes, warps_per_block, reps: int = 3):
+def pgz_autotune(ctx: int, jobs, chunk_bytes, warps_per_block, reps: int = 3, sweep_exec: bool = False):
     """(status, [entry dicts], best dict); jobs: list of (gz_ptr, gz_len, out_ptr, out_cap) device addresses;
-    sets the context's part size and CTA shape."""
+    sets the context's part size, CTA shape (and, with sweep_exec, the pass-1 execution form)."""
     arr = _jobs(jobs)
     cb = (U64 * len(chunk_bytes))(*chunk_bytes)
     wp = (ctypes.c_int * len(warps_per_block))(*warps_per_block)
-    ent = (pgz_tune_entry * (len(chunk_bytes) * len(warps_per_block)))()
+    ent = (pgz_tune_entry * (len(chunk_bytes) * len(warps_per_block) * (2 if sweep_exec else 1)))()
     best = pgz_tune_entry()
-    r = lib().pgz_autotune(ctx, arr, len(jobs), cb, len(chunk_bytes), wp, len(warps_per_block), reps, ent,
-                           ctypes.byref(best))
+    r = lib().pgz_autotune(ctx, arr, len(jobs), cb, len(chunk_bytes), wp, len(warps_per_block), 1 if sweep_exec else 0,
+                           reps, ent, ctypes.byref(best))
     return r, [e.as_dict() for e in ent], best.as_dict()
 
 

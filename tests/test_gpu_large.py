@@ -68,6 +68,11 @@ def test_autotune_picks_the_fastest_working_pair():
     assert st == 0 and n == len(raw) and _same_on_device(out, raw)
     parts = (len(gz) - 18 + best["chunk_bytes"] - 1) // best["chunk_bytes"]
     assert s["chunks"] == parts
+    # the pass-1 execution form as a third dimension: both forms decode, the context keeps the fastest
+    st, entries, best = ctx.pgz.pgz_autotune(ctx.h, job, [64 << 10], [4], 1, sweep_exec=True)
+    assert st == 0 and [e["exec_pipelined"] for e in entries] == [0, 1]
+    assert all(e["status"] == 0 for e in entries) and best["ms"] == min(e["ms"] for e in entries)
+    assert _same_on_device(out, raw)
     # invalid lists are rejected without running anything
     assert ctx.pgz.pgz_autotune(ctx.h, job, [1024], [4], 1)[0] == ctx.pgz.PGZ_E_ARG
     assert ctx.pgz.pgz_autotune(ctx.h, job, [65536], [3], 1)[0] == ctx.pgz.PGZ_E_ARG

@@ -84,12 +84,13 @@ def test_part_counts(cfg1, nparts):
         ctx.close()
 
 
+@pytest.mark.parametrize("pipe", [0, 1])
 @pytest.mark.parametrize("level", [1, 6, 9])
 @pytest.mark.parametrize("kind", ["fastq", "markov"])
-def test_levels_and_kinds(level, kind):
+def test_levels_and_kinds(level, kind, pipe):
     data = synth.fastq(3 << 20, 150, 0.01, 5) if kind == "fastq" else synth.markov(3 << 20, 6)
     gz = synth.gzip_compress(data, level)
-    ctx = Ctx(n_chunks=24)
+    ctx = Ctx(n_chunks=24, exec_pipelined=pipe)
     try:
         st, out, n, _ = ctx.decompress(gz)
         assert st == 0, ctx.pgz.pgz_strerror(st)
@@ -114,7 +115,8 @@ def _hand(blocks):
     return dw.gzip_wrap(w.tobytes(), text), text
 
 
-def test_edge_inputs():
+@pytest.mark.parametrize("pipe", [0, 1])
+def test_edge_inputs(pipe):
     big = synth.fastq(40000, 100, 0.0, 7)
     cases = {
         "empty": (synth.gzip_compress(b"", 6), b""),
@@ -134,7 +136,7 @@ def test_edge_inputs():
     cases["header_flags"] = (dw.gzip_wrap(raw.compress(txt) + raw.flush(), txt, flags=2 | 4 | 8 | 16,
                                           name=b"x" * 5000, extra=b"e" * 300, comment=b"c"), txt)
     for nparts in [1, 4, 32]:
-        ctx = Ctx(n_chunks=nparts)
+        ctx = Ctx(n_chunks=nparts, exec_pipelined=pipe)
         try:
             for name, (gz, text) in cases.items():
                 st, out, n, _ = ctx.decompress(gz)
