@@ -240,8 +240,10 @@ def run_pgz(args, rank, world):
     _, _, nph_parts = pgz.pgz_inspect_parts(ctx_b)
     window_bytes = int((nph_parts > 0).sum()) * 32768
 
-    # ---- plain: one file at a time through pgz_decompress, PLAIN_PARTS equal parts per file
-    ctx_p = pgz.pgz_create(pgz.pgz_config_init(device=dev, cuda_stream=stream.cuda_stream, n_chunks=PLAIN_PARTS))
+    # ---- plain: one file at a time through pgz_decompress, PLAIN_PARTS equal parts per file, with the
+    # batched form's CTA shape and execution form
+    ctx_p = pgz.pgz_create(pgz.pgz_config_init(device=dev, cuda_stream=stream.cuda_stream, n_chunks=PLAIN_PARTS,
+                                               warps_per_block=wpb, exec_pipelined=xp))
 
     def step_plain(stats=False):
         res = []

@@ -159,6 +159,8 @@ struct pgz_ctx {
     Plan plan;                 // the last call's plan (kept for inspection)
     PBuf hdr;                  // header / trailer staging
     DBuf in_buf, out_buf, fill_buf;
+    DBuf carry_win;            // streaming: the resolved window a segment leaves for the next
+    PBuf stage;                // streaming: pinned output of one segment
     uint64_t launches = 0;
     cudaEvent_t ev[8] = {};
 };
@@ -377,6 +379,12 @@ int count_and_read_chunks(pgz_ctx* ctx, Plan& P) {
 //    false (merge); an error in the first part is final.
 bool recover(Plan& P, int f, const ChunkDesc* res, uint64_t* false_syncs) {
     FileDesc& F = P.files[f];
+    // a streamed segment whose probe found no block start: its last part ran to the end of the segment's
+    // bytes; only a longer look-ahead helps (the caller's decision)
+    if (F.mode == 3 && !F.last_seg) {
+        const int pr = F.chunk0 + F.nchunks - 1;
+        if (res[pr].state == CS_EMPTY) return false;
+    }
     for (int c = F.chunk0; c < F.chunk0 + F.nchunks; ++c) {
         const ChunkDesc& R = res[c];
         if (R.state != CS_ERROR) continue;
@@ -393,6 +401,12 @@ bool recover(Plan& P, int f, const ChunkDesc* res, uint64_t* false_syncs) {
                 if (res[j].state == CS_ERROR && res[j].err == CE_OVERFLOW) {
                     if (P.chunks[j].cap >= kMaxPartSymbols) return false;
                     P.chunks[j].cap = std::min<uint64_t>(P.chunks[j].cap * 2, kMaxPartSymbols);
+                    return true;
+                }
+                if (P.chunks[j].probe) {         // a false block start at the segment's end: search on after it
+                    if (res[j].sync == kNone) return false;
+                    P.chunks[j].lo = res[j].sync + 1;
+                    ++*false_syncs;
                     return true;
                 }
                 P.chunks[j].disabled = 1;
@@ -565,6 +579,76 @@ void copy_range_windows(Plan& P, const pgz_index* idx, const std::vector<std::pa
     for (const auto& w : wins)
         cudaMemcpyAsync(P.d_windows.as<uint8_t>() + w.first * kWin, idx->windows.as<uint8_t>() + w.second * kWin, kWin,
                         cudaMemcpyDeviceToDevice, s);
+}
+
+// One segment of a streamed member as a mode-3 member of P.  The device holds the member's bytes
+// [win_lo, win_lo + win_len) at win; bit positions are relative to win_lo.  Part 0 starts at the known
+// block start b (the member's first block when first); parts 1.. search equal shares of [b, seg_end);
+// unless the segment is the last, a probe part searches [seg_end, probe_hi) for the block start where the
+// next segment begins, and the last part stops there.  The last segment's bytes end with the trailer.
+void plan_segment(pgz_ctx* ctx, Plan& P, const uint8_t* win, uint64_t win_len, uint64_t b, uint64_t seg_end,
+                  uint64_t probe_hi, bool first, bool last, const uint8_t* win0, uint64_t out_before,
+                  uint32_t crc_in, uint32_t crc_expect, uint32_t isize, uint64_t cap_mul) {
+    FileDesc F{};
+    F.gz = win;
+    F.gz_len = win_len;
+    F.s0_bit = b;
+    F.end_bit = last ? (win_len - 8) * 8 : win_len * 8;
+    F.crc_expect = crc_expect;
+    F.isize_expect = isize;
+    F.mode = 3;
+    F.out_hi = kNone;
+    F.win0 = first ? nullptr : win0;
+    F.out_before = out_before;
+    F.crc_in = crc_in;
+    F.last_seg = last ? 1u : 0u;
+    const uint64_t stop = last ? F.end_bit : seg_end;
+    const uint64_t csize = (stop - b + 7) / 8;
+    uint64_t n;
+    if (ctx->cfg.n_chunks > 0) n = (uint64_t)ctx->cfg.n_chunks;
+    else n = std::max<uint64_t>(1, (csize + ctx->cfg.chunk_bytes - 1) / ctx->cfg.chunk_bytes);
+    n = std::max<uint64_t>(1, std::min<uint64_t>(n, std::max<uint64_t>(1, csize / 64)));
+    const uint64_t per = (stop - b + n - 1) / n;     // bits
+    // symbols per part: 2x the compressed size bounds text; an overflow doubles the part's capacity
+    const uint64_t cap = std::min<uint64_t>(round_up(cap_mul * (4 * csize / n + 65536), 8), kMaxPartSymbols);
+    F.chunk0 = (int32_t)P.chunks.size();
+    const uint64_t np = n + (last ? 0 : 1);
+    F.nchunks = (int32_t)np;
+    uint64_t cap_sum = 0;
+    for (uint64_t i = 0; i < np; ++i) {
+        ChunkDesc C{};
+        if (i < n) {
+            C.lo = b + i * per;
+            C.hi = std::min<uint64_t>(b + (i + 1) * per, stop);
+            C.disabled = (i > 0 && C.lo >= stop) ? 1u : 0u;
+        } else {
+            C.lo = seg_end;
+            C.hi = probe_hi;
+            C.probe = 1;
+        }
+        if (i == 0) {
+            C.hi = b + 1;
+            C.given = first ? 0u : 1u;
+        }
+        C.file = (int32_t)P.files.size();
+        C.index = (int32_t)(i + (first ? 0 : 1));     // part 0 of the member only in the first segment
+        C.cap = cap;
+        C.stop_hint = kNone;
+        C.sync = kNone;
+        cap_sum += cap;
+        P.chunks.push_back(C);
+    }
+    F.out_cap = cap_sum;                              // the caller sizes the output buffer to it
+    const uint64_t gsz = std::max<uint64_t>(1, (uint64_t)std::ceil(std::sqrt((double)np)));
+    F.group0 = (int32_t)P.g0.size();
+    F.ngroups = 0;
+    for (uint64_t a = 0; a < np; a += gsz) {
+        P.g0.push_back(F.chunk0 + (int32_t)a);
+        P.gn.push_back((int32_t)std::min<uint64_t>(gsz, np - a));
+        P.gfile.push_back((int32_t)P.files.size());
+        F.ngroups++;
+    }
+    P.files.push_back(F);
 }
 
 // BGZF (SAM/BAM specification): a member whose FEXTRA holds the subfield
@@ -945,6 +1029,8 @@ void pgz_destroy(pgz_ctx* ctx) {
     cudaSetDevice(ctx->cfg.device);
     cudaStreamSynchronize(ctx->stream);
     ctx->plan.release();
+    ctx->carry_win.release();
+    ctx->stage.release();
     ctx->hdr.release();
     ctx->in_buf.release();
     ctx->out_buf.release();
@@ -1229,6 +1315,101 @@ int pgz_inspect_window(pgz_ctx* ctx, int part, uint8_t* host_dst) {
 }
 
 uint64_t pgz_kernel_launches(const pgz_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+// --------------------------------------------------------------------------- streaming
+int pgz_decompress_stream(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, uint64_t segment_bytes,
+                          pgz_sink sink, void* user, uint64_t* out_len, pgz_stats* st) {
+    if (!ctx || !gz || !sink || !out_len) return PGZ_E_ARG;
+    if (segment_bytes == 0) segment_bytes = 256ull << 20;
+    if (segment_bytes < (1ull << 20)) return PGZ_E_ARG;
+    cudaSetDevice(ctx->cfg.device);
+    *out_len = 0;
+    if (st) memset(st, 0, sizeof *st);
+    if (gz_len < 18) return PGZ_E_HEADER;
+    uint64_t s0 = 0;
+    if (parse_header(gz, gz_len, gz_len, &s0) != PGZ_OK) return PGZ_E_HEADER;
+    const uint8_t* t = gz + gz_len - 8;
+    const uint32_t crc_expect = t[0] | ((uint32_t)t[1] << 8) | ((uint32_t)t[2] << 16) | ((uint32_t)t[3] << 24);
+    const uint32_t isize = t[4] | ((uint32_t)t[5] << 8) | ((uint32_t)t[6] << 16) | ((uint32_t)t[7] << 24);
+    const uint64_t data_end = gz_len - 8;                  // bytes: the trailer follows the DEFLATE data
+    if (s0 >= data_end) return PGZ_E_DATA;
+    Plan& P = ctx->plan;
+    P.wpb = ctx->kp.wpb;
+    uint64_t b = s0 * 8;                                   // absolute bit of the next segment's first block
+    uint32_t reg = 0xffffffffu;                            // CRC-32 register after the output so far
+    uint64_t done = 0;
+    bool first = true;
+    uint64_t look = std::max<uint64_t>(segment_bytes / 8, 1ull << 20);
+    uint64_t cap_mul = 1;
+    if (cuda_status(ctx->carry_win.ensure(kWin))) return PGZ_E_NOMEM;
+    for (;;) {
+        // the segment's bytes: from the 4 KiB boundary at or before its first block (the block-start scan
+        // reads from 128-byte boundaries) to the look-ahead past its nominal end, or to the member's end
+        const uint64_t bb = b >> 3;
+        const uint64_t win_lo = bb & ~4095ull;
+        const uint64_t seg_end = bb + segment_bytes;
+        const bool last = seg_end + look + 65536 >= data_end;
+        const uint64_t win_hi = last ? gz_len : seg_end + look;
+        const uint64_t win_len = win_hi - win_lo;
+        if (cuda_status(ctx->in_buf.ensure(win_len))) return PGZ_E_NOMEM;
+        if (cudaMemcpyAsync(ctx->in_buf.p, gz + win_lo, win_len, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+            return PGZ_E_CUDA;
+        begin_plan(P);
+        plan_segment(ctx, P, ctx->in_buf.as<uint8_t>(), win_len, b - win_lo * 8, (seg_end - win_lo) * 8,
+                     (seg_end + look / 2 - win_lo) * 8, first, last, ctx->carry_win.as<uint8_t>(), done, reg,
+                     crc_expect, isize, cap_mul);
+        FileDesc& F = P.files[0];
+        if (cuda_status(ctx->out_buf.ensure(F.out_cap))) return PGZ_E_NOMEM;
+        F.out = ctx->out_buf.as<uint8_t>();
+        pgz_stats s1;
+        const int e = execute(ctx, P, st ? &s1 : nullptr);
+        if (st) add_stats(st, s1);
+        const FileDesc& R = P.h_files.as<FileDesc>()[0];
+        if (e == PGZ_E_CAPACITY && cap_mul < 64) {            // more output than the capacities allowed
+            cap_mul *= 2;
+            continue;
+        }
+        if (e != PGZ_OK) {
+            // a segment whose end found no block start in its look-ahead: retry with a longer one
+            ChunkDesc pc{};
+            if (!last && cudaMemcpy(&pc, P.d_chunks.as<ChunkDesc>() + F.chunk0 + F.nchunks - 1, sizeof pc,
+                                    cudaMemcpyDeviceToHost) == cudaSuccess &&
+                pc.state == CS_EMPTY && look < 4 * segment_bytes) {
+                look *= 2;
+                continue;
+            }
+            *out_len = done;
+            return e;
+        }
+        const uint64_t n = R.total;
+        if (n) {
+            if (cuda_status(ctx->stage.ensure(n))) return PGZ_E_NOMEM;
+            if (cudaMemcpyAsync(ctx->stage.p, ctx->out_buf.p, n, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+                return PGZ_E_CUDA;
+        }
+        ChunkDesc pc{};
+        if (!last) {
+            // the block start where the next segment begins, and the window the segment leaves before it
+            const int pr = F.chunk0 + F.nchunks - 1;
+            cudaMemcpyAsync(&pc, P.d_chunks.as<ChunkDesc>() + pr, sizeof pc, cudaMemcpyDeviceToHost, ctx->stream);
+            cudaMemcpyAsync(ctx->carry_win.p, P.d_windows.as<uint8_t>() + (uint64_t)pr * kWin, kWin,
+                            cudaMemcpyDeviceToDevice, ctx->stream);
+        }
+        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return PGZ_E_CUDA;
+        if (n && sink(user, ctx->stage.as<uint8_t>(), n) != 0) {
+            *out_len = done;
+            return PGZ_E_ABORTED;
+        }
+        done += n;
+        reg = R.crc;
+        *out_len = done;
+        if (last) return PGZ_OK;
+        if (pc.state != CS_DONE || pc.sync == kNone) return PGZ_E_DATA;
+        b = win_lo * 8 + pc.sync;
+        first = false;
+        cap_mul = 1;
+    }
+}
 
 // --------------------------------------------------------------------------- index / range
 int pgz_index_build(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, pgz_index** idx) {
@@ -1554,6 +1735,7 @@ const char* pgz_strerror(int status) {
         case PGZ_E_TIMEOUT: return "device wait timed out";
         case PGZ_E_CUDA: return "CUDA error";
         case PGZ_E_NOMEM: return "out of device memory";
+        case PGZ_E_ABORTED: return "stopped by the caller's sink";
         default: return "unknown status";
     }
 }

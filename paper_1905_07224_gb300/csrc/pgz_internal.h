@@ -57,7 +57,8 @@ struct FileDesc {
     int32_t chunk0, nchunks;
     int32_t group0, ngroups;
     uint64_t seg0, nseg;   // 4 KiB CRC segments of the output
-    uint32_t mode;         // 0 whole member; 1 from a bit offset (no CRC/ISIZE); 2 byte range of the output
+    uint32_t mode;         // 0 whole member; 1 from a bit offset (no CRC/ISIZE); 2 byte range of the output;
+                           // 3 one segment of a streamed member (bit positions relative to the segment's bytes)
     uint32_t open_end;     // mode 0: more members may follow; the member ends after its final block, and its
                            // trailer (CRC-32, ISIZE) is read there
     uint64_t out_base;     // output offset of the first part (mode 2: from the index)
@@ -71,6 +72,11 @@ struct FileDesc {
     uint32_t bad_err;
     uint32_t pad1;
     uint64_t member_end;   // mode 0: one past the member's trailer, in bytes of gz
+    // mode 3 (streamed member): what the earlier segments left
+    const uint8_t* win0;   // resolved 32 KiB window before the segment's first part (null: the member start)
+    uint64_t out_before;   // output bytes of the member before the segment
+    uint32_t crc_in;       // CRC-32 register after those bytes (all-ones start, not inverted)
+    uint32_t last_seg;     // the segment reaches the member's end: its final block and trailer are in it
 };
 
 // one part of a member
@@ -97,7 +103,7 @@ struct ChunkDesc {
     uint32_t blocks;
     uint32_t final;        // the part decoded the member's final block
     uint32_t anyph;        // pass 1 produced at least one placeholder
-    uint32_t pad2;
+    uint32_t probe;        // 1: only the block start is searched (the end of a streamed segment); no output
 };
 
 // host-side launch wrappers (pgz_kernels.cu)

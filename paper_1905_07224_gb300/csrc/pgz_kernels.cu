@@ -1605,6 +1605,17 @@ __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
     if (c >= nchunks) return;
     ChunkDesc& C = chunks[c];
     if (C.state != CS_FOUND) continue;
+    if (C.probe) {                    // a streamed segment's end: the block start found is all it gives
+        if (lane == 0) {
+            C.state = CS_DONE;
+            C.n = 0;
+            C.anyph = 0;
+            C.blocks = 0;
+            C.final = 0;
+            C.end = C.sync;
+        }
+        continue;
+    }
     const FileDesc& F = files[C.file];
     // the next part that holds a block start.  `sync` is final after k_sync
     // and never written here (other warps of this kernel rewrite `state`).
@@ -1736,13 +1747,13 @@ __global__ void __launch_bounds__(1024) k_plan(FileDesc* files, ChunkDesc* chunk
             if (bad != 0xffffffffu) {
                 F.bad_err = chunks[F.chunk0 + bad].err;
                 st = F.bad_err == CE_TRAIL ? PGZ_E_UNSUPPORTED : PGZ_E_DATA;
-            } else if (!any_final && F.mode != 2) {
+            } else if (!any_final && (F.mode == 0 || F.mode == 1 || (F.mode == 3 && F.last_seg))) {
                 st = PGZ_E_DATA;
-            } else if (F.mode == 0 && total > F.out_cap) {
-                st = PGZ_E_CAPACITY;
-            } else if (F.mode == 1 && total > F.out_cap) {
+            } else if (F.mode != 2 && total > F.out_cap) {
                 st = PGZ_E_CAPACITY;
             } else if (F.mode == 0 && (uint32_t)total != F.isize_expect) {
+                st = PGZ_E_ISIZE;
+            } else if (F.mode == 3 && F.last_seg && (uint32_t)(F.out_before + total) != F.isize_expect) {
                 st = PGZ_E_ISIZE;
             }
         }
@@ -1806,7 +1817,7 @@ __global__ void __launch_bounds__(1024) k_chain_walk(const FileDesc* __restrict_
     const FileDesc& F = files[blockIdx.x];
     if (F.status != PGZ_OK) return;
     const uint32_t tid = threadIdx.x;
-    for (uint32_t k = tid; k < kWin; k += 1024) W[k] = 0;   // before the member: never referenced
+    for (uint32_t k = tid; k < kWin; k += 1024) W[k] = F.win0 ? F.win0[k] : 0;   // before the member: never referenced
     __syncthreads();
     for (int g = F.group0; g < F.group0 + F.ngroups; ++g) {
         uint8_t* ws = wstart + (uint64_t)g * kWin;
@@ -2168,7 +2179,7 @@ __global__ void __launch_bounds__(kCrcThreads, 1) k_crc(FileDesc* files, int nfi
             run_end = 0;
         }
         FileDesc& F = files[f];
-        if (F.status != PGZ_OK || F.mode != 0) continue;
+        if (F.status != PGZ_OK || (F.mode != 0 && F.mode != 3)) continue;
         const uint64_t D = F.total;
         const uint64_t a = (sg - seg0[f]) * kCrcSeg;
         if (a >= D) continue;
@@ -2191,7 +2202,15 @@ __global__ void k_finalize(FileDesc* files, int nfiles) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nfiles) return;
     FileDesc& F = files[f];
-    if (F.status != PGZ_OK || F.mode != 0) return;
+    if (F.status != PGZ_OK) return;
+    if (F.mode == 3) {
+        // register after the segment, from the register the earlier segments left (R_I(M) = I x^(8|M|) + R_0(M))
+        const uint32_t reg = F.crc_acc ^ gf2_mul(F.crc_in, xpow8(F.total));
+        F.crc = reg;
+        if (F.last_seg && (reg ^ 0xffffffffu) != F.crc_expect) F.status = PGZ_E_CRC;
+        return;
+    }
+    if (F.mode != 0) return;
     // register after D bytes from the initial all-ones register, then inverted
     const uint32_t crc = F.crc_acc ^ gf2_mul(0xffffffffu, xpow8(F.total)) ^ 0xffffffffu;
     F.crc = crc;
