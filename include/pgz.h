@@ -54,7 +54,8 @@ typedef enum pgz_status {
     PGZ_E_UNSUPPORTED = 8,  /* data after a member that is not a gzip member; a batch job with several members */
     PGZ_E_TIMEOUT = 9,      /* a bounded device wait gave up */
     PGZ_E_CUDA = 10,        /* a CUDA runtime call failed */
-    PGZ_E_NOMEM = 11        /* scratch allocation failed or exceeds the budget */
+    PGZ_E_NOMEM = 11,       /* scratch allocation failed or exceeds the budget */
+    PGZ_E_ABORTED = 12      /* the caller's sink stopped a streamed decode */
 } pgz_status;
 
 typedef struct pgz_ctx pgz_ctx;
@@ -133,6 +134,40 @@ int pgz_decompress(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len,
    output back to `out`, both inside the call. */
 int pgz_decompress_host(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len,
                         uint8_t* out, uint64_t out_cap, uint64_t* out_len, pgz_stats* st);
+
+/* Receives the output of a streamed decode in order: n bytes at `bytes`
+   (pinned host memory, valid only during the call).  A non-zero return
+   stops the decode with PGZ_E_ABORTED. */
+typedef int (*pgz_sink)(void* user, const uint8_t* bytes, uint64_t n);
+
+/* Memory-bounded streaming of one gzip member held in HOST memory (Section
+   "Full file decompression in two passes", run over consecutive segments of
+   the compressed data).  Each segment of about segment_bytes compressed
+   bytes is one run of the pass kernels:
+   - its first part starts at a known block start, with the resolved 32 KiB
+     window the previous segment left (the member's start and an empty
+     window for the first segment);
+   - its other parts search their block starts as in pgz_decompress;
+   - a probe part past its nominal end finds the block start where the next
+     segment begins (within a look-ahead of max(segment_bytes / 8, 1 MiB),
+     doubled when nothing is found there), and the segment's last part must
+     end exactly on it.
+   The CRC-32 register and the output length are carried from segment to
+   segment on the device, and the last segment checks them against the
+   trailer.  Output reaches sink(user, bytes, n) segment by segment, in
+   order; when a later segment fails, the bytes already delivered stay
+   delivered and the status says why the rest could not be decoded.
+   Device memory in use is bounded by the segment, not by the member: about
+   17 bytes per compressed byte of a segment at 64 KiB parts for data that
+   expands at most 2x (input, symbol scratch, output, windows); more where a
+   segment expands further, its capacities doubling on demand.  segment_bytes: 0 for 256 MiB, else at least 1 MiB
+   (PGZ_E_ARG otherwise).  *out_len: bytes delivered to the sink.
+   st (nullable): statistics summed over the segments' runs.
+   Errors: PGZ_E_HEADER, PGZ_E_DATA, PGZ_E_CRC, PGZ_E_ISIZE and
+   PGZ_E_UNSUPPORTED (data after the member) as for pgz_decompress;
+   PGZ_E_ABORTED when the sink returns non-zero. */
+int pgz_decompress_stream(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, uint64_t segment_bytes,
+                          pgz_sink sink, void* user, uint64_t* out_len, pgz_stats* st);
 
 /* Problem "Random access in DEFLATE stream" (Section "Feasibility of random
    access"): from compressed BIT offset start_bit of a gzip member, find the

@@ -17,7 +17,9 @@ LIB_PATH = os.path.join(_HERE, "libpgz.so")
 
 PGZ_OK = 0
 PGZ_E_ARG, PGZ_E_HEADER, PGZ_E_DATA, PGZ_E_CRC, PGZ_E_ISIZE, PGZ_E_CAPACITY = 1, 2, 3, 4, 5, 6
-PGZ_E_NOSYNC, PGZ_E_UNSUPPORTED, PGZ_E_TIMEOUT, PGZ_E_CUDA, PGZ_E_NOMEM = 7, 8, 9, 10, 11
+PGZ_E_NOSYNC, PGZ_E_UNSUPPORTED, PGZ_E_TIMEOUT, PGZ_E_CUDA, PGZ_E_NOMEM, PGZ_E_ABORTED = 7, 8, 9, 10, 11, 12
+# int sink(void* user, const uint8_t* bytes, uint64_t n)
+PGZ_SINK = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64)
 NONE = (1 << 64) - 1
 
 U64 = ctypes.c_uint64
@@ -78,6 +80,7 @@ def _load():
         "pgz_destroy": (None, [VP]),
         "pgz_decompress": (ctypes.c_int, [VP, VP, U64, VP, U64, P(U64), P(pgz_stats)]),
         "pgz_decompress_host": (ctypes.c_int, [VP, VP, U64, VP, U64, P(U64), P(pgz_stats)]),
+        "pgz_decompress_stream": (ctypes.c_int, [VP, VP, U64, U64, PGZ_SINK, VP, P(U64), P(pgz_stats)]),
         "pgz_decompress_at": (ctypes.c_int, [VP, VP, U64, U64, VP, VP, ctypes.c_uint8, U64, P(U64), P(U64), P(U64)]),
         "pgz_decompress_batch": (ctypes.c_int, [VP, ctypes.c_int, P(pgz_job), P(pgz_stats)]),
         "pgz_batch_prepare": (ctypes.c_int, [VP, ctypes.c_int, P(pgz_job), P(VP)]),
@@ -128,7 +131,7 @@ EXPORTED = ["pgz_config_init", "pgz_create", "pgz_destroy", "pgz_decompress", "p
             "pgz_inspect_symbols", "pgz_inspect_window", "pgz_kernel_launches", "pgz_strerror",
             "pgz_decompress_noalloc", "pgz_autotune", "pgz_server_create", "pgz_server_add_file",
             "pgz_server_submit", "pgz_server_poll", "pgz_server_drain", "pgz_server_pending", "pgz_server_destroy",
-            "pgz_extract_sequences"]
+            "pgz_extract_sequences", "pgz_decompress_stream"]
 
 
 def pgz_strerror(status: int) -> str:
@@ -176,6 +179,28 @@ def pgz_decompress_host(ctx: int, gz, out: np.ndarray, stats: bool = False):
     r = lib().pgz_decompress_host(ctx, a.ctypes.data, a.size, out.ctypes.data, out.size, ctypes.byref(n),
                                   ctypes.byref(st) if st is not None else None)
     return r, n.value, (st.as_dict() if st is not None else None)
+
+
+def pgz_decompress_stream(ctx: int, gz, segment_bytes: int = 0, sink=None, stats: bool = False):
+    """(status, out_len, stats, out); gz: bytes/uint8 array in host memory.  sink(memoryview) receives the
+    output segment by segment (a truthy return stops the decode); without a sink the output is collected
+    and returned as bytes in `out`."""
+    a = np.frombuffer(gz, dtype=np.uint8) if isinstance(gz, (bytes, bytearray)) else np.ascontiguousarray(gz)
+    parts = []
+
+    def _cb(_user, p, n):
+        view = (ctypes.c_uint8 * n).from_address(p)
+        if sink is None:
+            parts.append(bytes(view))
+            return 0
+        return 1 if sink(memoryview(view)) else 0
+
+    cb = PGZ_SINK(_cb)
+    n = U64(0)
+    st = pgz_stats() if stats else None
+    r = lib().pgz_decompress_stream(ctx, a.ctypes.data, a.size, segment_bytes, cb, None, ctypes.byref(n),
+                                    ctypes.byref(st) if st is not None else None)
+    return r, n.value, (st.as_dict() if st is not None else None), (b"".join(parts) if sink is None else None)
 
 
 def pgz_decompress_at(ctx: int, gz_ptr: int, gz_len: int, start_bit: int, sym_ptr: int | None,
