@@ -160,7 +160,8 @@ struct pgz_ctx {
     PBuf hdr;                  // header / trailer staging
     DBuf in_buf, out_buf, fill_buf;
     DBuf carry_win;            // streaming: the resolved window a segment leaves for the next
-    PBuf stage;                // streaming: pinned output of one segment
+    DBuf sin[2], sout[2];      // streaming: compressed bytes and output of two segments in flight
+    PBuf stage[2];             // streaming: pinned output of two segments
     uint64_t launches = 0;
     cudaEvent_t ev[8] = {};
 };
@@ -474,19 +475,24 @@ void fill_stats(pgz_ctx* ctx, const Plan& P, pgz_stats* st, uint64_t retries, ui
     }
 }
 
-// runs a plan to completion, with recovery re-runs
-int execute(pgz_ctx* ctx, Plan& P, pgz_stats* st) {
+// the first half of a run of a plan: buffers, uploads and every launch, all asynchronous on the context's
+// stream
+int start_run(pgz_ctx* ctx, Plan& P, bool timed) {
+    P.wpb = ctx->kp.wpb;
+    reset_results(P);
+    int e = layout(P);
+    if (e) return e;
+    upload_static(P, ctx->stream);
+    return enqueue(ctx, P, ctx->stream, timed);
+}
+
+// the second half: waits for the run, then re-runs with recovery until the plan succeeds or cannot
+int finish_run(pgz_ctx* ctx, Plan& P, pgz_stats* st) {
     uint64_t retries = 0, false_syncs = 0;
     const bool timed = st != nullptr;
     int status = PGZ_OK;
-    P.wpb = ctx->kp.wpb;
     for (;;) {
-        reset_results(P);
-        int e = layout(P);
-        if (e) return e;
-        upload_static(P, ctx->stream);
-        e = enqueue(ctx, P, ctx->stream, timed);
-        if (e) return e;
+        int e = PGZ_OK;
         if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return PGZ_E_CUDA;
         const FileDesc* hf = P.h_files.as<FileDesc>();
         bool again = false;
@@ -514,6 +520,8 @@ int execute(pgz_ctx* ctx, Plan& P, pgz_stats* st) {
         }
         if (again) {
             ++retries;
+            e = start_run(ctx, P, timed);
+            if (e) return e;
             continue;
         }
         if (need_chunks || st) {
@@ -529,6 +537,13 @@ int execute(pgz_ctx* ctx, Plan& P, pgz_stats* st) {
         fill_stats(ctx, P, st, retries, false_syncs, timed, (need_chunks || st) ? res : nullptr);
         return status;
     }
+}
+
+// runs a plan to completion, with recovery re-runs
+int execute(pgz_ctx* ctx, Plan& P, pgz_stats* st) {
+    const int e = start_run(ctx, P, st != nullptr);
+    if (e) return e;
+    return finish_run(ctx, P, st);
 }
 
 // a byte range [d_off, d_off + len) of an indexed member as a mode-2 member of P:
@@ -1030,7 +1045,11 @@ void pgz_destroy(pgz_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     ctx->plan.release();
     ctx->carry_win.release();
-    ctx->stage.release();
+    for (int k = 0; k < 2; ++k) {
+        ctx->sin[k].release();
+        ctx->sout[k].release();
+        ctx->stage[k].release();
+    }
     ctx->hdr.release();
     ctx->in_buf.release();
     ctx->out_buf.release();
@@ -1317,6 +1336,71 @@ int pgz_inspect_window(pgz_ctx* ctx, int part, uint8_t* host_dst) {
 uint64_t pgz_kernel_launches(const pgz_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 // --------------------------------------------------------------------------- streaming
+namespace {
+
+// a streamed segment's place in the member: its first block (bit), its bytes on the device, its nominal end
+struct SegGeom {
+    uint64_t b, win_lo, win_hi, seg_end;
+    bool last;
+};
+
+SegGeom seg_geom(uint64_t b, uint64_t segment_bytes, uint64_t look, uint64_t gz_len) {
+    SegGeom g;
+    const uint64_t data_end = gz_len - 8;
+    const uint64_t bb = b >> 3;
+    g.b = b;
+    g.win_lo = bb & ~4095ull;            // the block-start scan reads from 128-byte boundaries
+    g.seg_end = bb + segment_bytes;
+    g.last = g.seg_end + look + 65536 >= data_end;
+    g.win_hi = g.last ? gz_len : g.seg_end + look;
+    return g;
+}
+
+// host -> device copies of member bytes into a streaming input buffer, on the upload stream
+struct Upload {
+    uint64_t lo = 0, hi = 0;             // member bytes [lo, hi) held
+    cudaEvent_t done = nullptr;
+};
+
+int upload_bytes(DBuf& buf, Upload& u, const uint8_t* gz, uint64_t lo, uint64_t hi, cudaStream_t up) {
+    if (cuda_status(buf.ensure(hi - lo))) return PGZ_E_NOMEM;
+    if (cudaMemcpyAsync(buf.p, gz + lo, hi - lo, cudaMemcpyHostToDevice, up) != cudaSuccess) return PGZ_E_CUDA;
+    if (cudaEventRecord(u.done, up) != cudaSuccess) return PGZ_E_CUDA;
+    u.lo = lo;
+    u.hi = hi;
+    return PGZ_OK;
+}
+
+struct StreamRes {                       // per-call streams and events, released on every return
+    cudaStream_t up = nullptr, down = nullptr;
+    cudaEvent_t ev_dn[2] = {};
+    Upload upl[2];
+    int init() {
+        if (cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking) != cudaSuccess) return PGZ_E_CUDA;
+        if (cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking) != cudaSuccess) return PGZ_E_CUDA;
+        for (int k = 0; k < 2; ++k) {
+            if (cudaEventCreateWithFlags(&ev_dn[k], cudaEventDisableTiming) != cudaSuccess) return PGZ_E_CUDA;
+            if (cudaEventCreateWithFlags(&upl[k].done, cudaEventDisableTiming) != cudaSuccess) return PGZ_E_CUDA;
+        }
+        return PGZ_OK;
+    }
+    ~StreamRes() {
+        if (up) cudaStreamSynchronize(up);
+        if (down) cudaStreamSynchronize(down);
+        for (int k = 0; k < 2; ++k) {
+            if (ev_dn[k]) cudaEventDestroy(ev_dn[k]);
+            if (upl[k].done) cudaEventDestroy(upl[k].done);
+        }
+        if (up) cudaStreamDestroy(up);
+        if (down) cudaStreamDestroy(down);
+    }
+};
+
+}  // namespace
+
+// Segments alternate between two input and two output buffers.  While segment k runs on the context's
+// stream, the bytes segment k + 1 can need (its first block lies in segment k's probe range) go up on an
+// upload stream, and segment k - 1's output comes down on a download stream and is handed to the sink.
 int pgz_decompress_stream(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, uint64_t segment_bytes,
                           pgz_sink sink, void* user, uint64_t* out_len, pgz_stats* st) {
     if (!ctx || !gz || !sink || !out_len) return PGZ_E_ARG;
@@ -1331,83 +1415,108 @@ int pgz_decompress_stream(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, uint
     const uint8_t* t = gz + gz_len - 8;
     const uint32_t crc_expect = t[0] | ((uint32_t)t[1] << 8) | ((uint32_t)t[2] << 16) | ((uint32_t)t[3] << 24);
     const uint32_t isize = t[4] | ((uint32_t)t[5] << 8) | ((uint32_t)t[6] << 16) | ((uint32_t)t[7] << 24);
-    const uint64_t data_end = gz_len - 8;                  // bytes: the trailer follows the DEFLATE data
-    if (s0 >= data_end) return PGZ_E_DATA;
+    if (s0 >= gz_len - 8) return PGZ_E_DATA;
+    StreamRes R;
+    if (R.init() != PGZ_OK) return PGZ_E_CUDA;
+    if (cuda_status(ctx->carry_win.ensure(kWin))) return PGZ_E_NOMEM;
     Plan& P = ctx->plan;
-    P.wpb = ctx->kp.wpb;
-    uint64_t b = s0 * 8;                                   // absolute bit of the next segment's first block
-    uint32_t reg = 0xffffffffu;                            // CRC-32 register after the output so far
-    uint64_t done = 0;
-    bool first = true;
+    uint32_t reg = 0xffffffffu;          // CRC-32 register after the output so far
+    uint64_t produced = 0;               // output bytes of the segments decoded so far
     uint64_t look = std::max<uint64_t>(segment_bytes / 8, 1ull << 20);
     uint64_t cap_mul = 1;
-    if (cuda_status(ctx->carry_win.ensure(kWin))) return PGZ_E_NOMEM;
+    bool first = true;
+    int i = 0;                           // buffers of the current segment
+    int pend = -1;                       // buffers of the output still to deliver, and its size
+    uint64_t pend_n = 0;
+    // hands the pending output to the sink; false if the sink stopped the decode
+    auto deliver = [&]() -> int {
+        if (pend < 0) return PGZ_OK;
+        const int k = pend;
+        pend = -1;
+        if (cudaEventSynchronize(R.ev_dn[k]) != cudaSuccess) return PGZ_E_CUDA;
+        if (pend_n && sink(user, ctx->stage[k].as<uint8_t>(), pend_n) != 0) return PGZ_E_ABORTED;
+        *out_len += pend_n;
+        return PGZ_OK;
+    };
+    // the caller's sink may stop the decode while a run is in flight: wait for it before returning
+    auto quit = [&](int status) -> int {
+        cudaStreamSynchronize(ctx->stream);
+        return status;
+    };
+    SegGeom g = seg_geom(s0 * 8, segment_bytes, look, gz_len);
     for (;;) {
-        // the segment's bytes: from the 4 KiB boundary at or before its first block (the block-start scan
-        // reads from 128-byte boundaries) to the look-ahead past its nominal end, or to the member's end
-        const uint64_t bb = b >> 3;
-        const uint64_t win_lo = bb & ~4095ull;
-        const uint64_t seg_end = bb + segment_bytes;
-        const bool last = seg_end + look + 65536 >= data_end;
-        const uint64_t win_hi = last ? gz_len : seg_end + look;
-        const uint64_t win_len = win_hi - win_lo;
-        if (cuda_status(ctx->in_buf.ensure(win_len))) return PGZ_E_NOMEM;
-        if (cudaMemcpyAsync(ctx->in_buf.p, gz + win_lo, win_len, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
-            return PGZ_E_CUDA;
+        // the segment's bytes: from the upload made while the previous segment ran, else now
+        Upload& u = R.upl[i];
+        if (!(u.lo <= g.win_lo && g.win_hi <= u.hi)) {
+            const int e = upload_bytes(ctx->sin[i], u, gz, g.win_lo, g.win_hi, R.up);
+            if (e) return quit(e);
+        }
+        if (cudaStreamWaitEvent(ctx->stream, u.done, 0) != cudaSuccess) return quit(PGZ_E_CUDA);
         begin_plan(P);
-        plan_segment(ctx, P, ctx->in_buf.as<uint8_t>(), win_len, b - win_lo * 8, (seg_end - win_lo) * 8,
-                     (seg_end + look / 2 - win_lo) * 8, first, last, ctx->carry_win.as<uint8_t>(), done, reg,
-                     crc_expect, isize, cap_mul);
+        plan_segment(ctx, P, ctx->sin[i].as<uint8_t>() + (g.win_lo - u.lo), g.win_hi - g.win_lo, g.b - g.win_lo * 8,
+                     (g.seg_end - g.win_lo) * 8, (g.seg_end + look / 2 - g.win_lo) * 8, first, g.last,
+                     ctx->carry_win.as<uint8_t>(), produced, reg, crc_expect, isize, cap_mul);
         FileDesc& F = P.files[0];
-        if (cuda_status(ctx->out_buf.ensure(F.out_cap))) return PGZ_E_NOMEM;
-        F.out = ctx->out_buf.as<uint8_t>();
+        if (cuda_status(ctx->sout[i].ensure(F.out_cap))) return quit(PGZ_E_NOMEM);
+        F.out = ctx->sout[i].as<uint8_t>();
+        int e = start_run(ctx, P, st != nullptr);
+        if (e) return quit(e);
+        // while it runs: the bytes the next segment can need, and the previous segment's output
+        if (!g.last) {
+            Upload& v = R.upl[i ^ 1];
+            const uint64_t lo = g.seg_end & ~4095ull;
+            const uint64_t hi = std::min<uint64_t>(gz_len, g.seg_end + look / 2 + segment_bytes + look + 65544);
+            if (!(v.lo <= lo && hi <= v.hi)) {
+                e = upload_bytes(ctx->sin[i ^ 1], v, gz, lo, hi, R.up);
+                if (e) return quit(e);
+            }
+        }
+        e = deliver();
+        if (e) return quit(e);
         pgz_stats s1;
-        const int e = execute(ctx, P, st ? &s1 : nullptr);
+        e = finish_run(ctx, P, st ? &s1 : nullptr);
         if (st) add_stats(st, s1);
-        const FileDesc& R = P.h_files.as<FileDesc>()[0];
-        if (e == PGZ_E_CAPACITY && cap_mul < 64) {            // more output than the capacities allowed
+        if (e == PGZ_E_CAPACITY && cap_mul < 64) {        // more output than the capacities allowed
             cap_mul *= 2;
             continue;
         }
         if (e != PGZ_OK) {
             // a segment whose end found no block start in its look-ahead: retry with a longer one
             ChunkDesc pc{};
-            if (!last && cudaMemcpy(&pc, P.d_chunks.as<ChunkDesc>() + F.chunk0 + F.nchunks - 1, sizeof pc,
-                                    cudaMemcpyDeviceToHost) == cudaSuccess &&
+            if (!g.last && cudaMemcpy(&pc, P.d_chunks.as<ChunkDesc>() + F.chunk0 + F.nchunks - 1, sizeof pc,
+                                      cudaMemcpyDeviceToHost) == cudaSuccess &&
                 pc.state == CS_EMPTY && look < 4 * segment_bytes) {
                 look *= 2;
+                g = seg_geom(g.b, segment_bytes, look, gz_len);
                 continue;
             }
-            *out_len = done;
             return e;
         }
-        const uint64_t n = R.total;
+        const FileDesc& H = P.h_files.as<FileDesc>()[0];
+        const uint64_t n = H.total;
         if (n) {
-            if (cuda_status(ctx->stage.ensure(n))) return PGZ_E_NOMEM;
-            if (cudaMemcpyAsync(ctx->stage.p, ctx->out_buf.p, n, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+            if (cuda_status(ctx->stage[i].ensure(n))) return PGZ_E_NOMEM;
+            if (cudaMemcpyAsync(ctx->stage[i].p, ctx->sout[i].p, n, cudaMemcpyDeviceToHost, R.down) != cudaSuccess)
                 return PGZ_E_CUDA;
         }
+        if (cudaEventRecord(R.ev_dn[i], R.down) != cudaSuccess) return PGZ_E_CUDA;
+        pend = i;
+        pend_n = n;
+        produced += n;
+        reg = H.crc;
+        if (g.last) return deliver();
+        // the block start where the next segment begins, and the window this segment leaves before it
         ChunkDesc pc{};
-        if (!last) {
-            // the block start where the next segment begins, and the window the segment leaves before it
-            const int pr = F.chunk0 + F.nchunks - 1;
-            cudaMemcpyAsync(&pc, P.d_chunks.as<ChunkDesc>() + pr, sizeof pc, cudaMemcpyDeviceToHost, ctx->stream);
-            cudaMemcpyAsync(ctx->carry_win.p, P.d_windows.as<uint8_t>() + (uint64_t)pr * kWin, kWin,
-                            cudaMemcpyDeviceToDevice, ctx->stream);
-        }
+        const int pr = F.chunk0 + F.nchunks - 1;
+        cudaMemcpyAsync(&pc, P.d_chunks.as<ChunkDesc>() + pr, sizeof pc, cudaMemcpyDeviceToHost, ctx->stream);
+        cudaMemcpyAsync(ctx->carry_win.p, P.d_windows.as<uint8_t>() + (uint64_t)pr * kWin, kWin,
+                        cudaMemcpyDeviceToDevice, ctx->stream);
         if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return PGZ_E_CUDA;
-        if (n && sink(user, ctx->stage.as<uint8_t>(), n) != 0) {
-            *out_len = done;
-            return PGZ_E_ABORTED;
-        }
-        done += n;
-        reg = R.crc;
-        *out_len = done;
-        if (last) return PGZ_OK;
         if (pc.state != CS_DONE || pc.sync == kNone) return PGZ_E_DATA;
-        b = win_lo * 8 + pc.sync;
+        g = seg_geom(g.win_lo * 8 + pc.sync, segment_bytes, look, gz_len);
         first = false;
         cap_mul = 1;
+        i ^= 1;
     }
 }
 
