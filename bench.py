@@ -43,10 +43,19 @@ TUNE_CHUNKS = [32 << 10, 64 << 10, 128 << 10, 256 << 10, 512 << 10]   # the auto
 TUNE_WPB = [2, 4, 8]                                                # ... and pass-1 CTA shapes (warps)
 PLAIN_PARTS = 1024            # parts per file of the plain one-file-at-a-time form
 METRIC = "decompressed GB/s on 1 GB300 (batched vs plain), %HBM roofline"
-# DRAM bytes (read + write) of pass 1 per decompressed byte: ncu capture of k_sync and k_inflate on this
-# workload's batched run at 64 KiB parts and 4 warps per block (profiles/pass1_translate_crc_fastq256_batched.md:
-# 1.624 + 3.376 GB for 536,870,912 bytes out); None while the kernels differ from the capture
-PASS1_TRAFFIC_PER_OUT_BYTE = 5.000e9 / 536870912
+# DRAM bytes (read + write) of pass 1 (k_sync + k_inflate) per decompressed byte on this workload's batched
+# run, by (part size, warps per block, pipelined execution): ncu captures of the configurations the autotuner
+# picks here (profiles/pass1_traffic_fastq256_batched.md).  A configuration without a capture reports null.
+PASS1_TRAFFIC_PER_OUT_BYTE = {
+    (65536, 2, 0): 5.0866e9 / 536870912,
+    (65536, 2, 1): 5.0049e9 / 536870912,
+    (65536, 4, 0): 5.0821e9 / 536870912,
+    (65536, 4, 1): 5.0035e9 / 536870912,
+    (131072, 4, 0): 4.4942e9 / 536870912,
+    (131072, 4, 1): 4.3808e9 / 536870912,
+    (131072, 8, 0): 4.4814e9 / 536870912,
+    (131072, 8, 1): 4.3636e9 / 536870912,
+}
 
 
 def _peaks():
@@ -343,7 +352,8 @@ def run_pgz(args, rank, world):
     ach4 = alg4 / (stage["ms_translate"] * 1e-3) / 1e9 if stage["ms_translate"] > 0 else None
     alg5 = total_out                                 # bytes read by the CRC
     ach5 = alg5 / (stage["ms_crc"] * 1e-3) / 1e9 if stage["ms_crc"] > 0 else None
-    traffic1 = PASS1_TRAFFIC_PER_OUT_BYTE * total_out if PASS1_TRAFFIC_PER_OUT_BYTE else None
+    tpb = PASS1_TRAFFIC_PER_OUT_BYTE.get((chunk_bytes, wpb, xp))
+    traffic1 = tpb * total_out if tpb else None
     line = {
         "metric": METRIC,
         "value": round(gbs, 3),
@@ -755,6 +765,8 @@ def run_profile_case(spec: str, chunk_bytes: int, wpb: int = 4):
     from paper_1905_07224_gb300 import build, pgz, synth
     if spec.startswith("batch:"):
         return run_profile_batch(int(spec.split(":")[1]), chunk_bytes, wpb)
+    if spec.startswith("batchsweep:"):
+        return run_profile_sweep(spec.split(":", 1)[1])
     mib, level, calls = (int(x) for x in spec.split(":"))
     build.build()
     raw = synth.fastq(mib << 20, 150, 0.001, 1)
@@ -803,6 +815,41 @@ def run_profile_batch(calls: int, chunk_bytes: int, wpb: int):
             **{k: (round(v, 3) if isinstance(v, float) else v) for k, v in s.items()}}
 
 
+def run_profile_sweep(spec: str):
+    """--profile-case batchsweep:CHUNK/WPB/PIPE,... -- the benchmark's two files decoded together by one
+    pgz_decompress_batch call per configuration (part size, warps per block, pipelined execution), in the order
+    given, on one context each; outputs checked.  An ncu capture of k_sync / k_inflate then gives each
+    configuration's pass-1 traffic in launch order."""
+    import numpy as np
+    import torch
+    from paper_1905_07224_gb300 import build, pgz
+    build.build()
+    files, desc = make_workload("fastq256")
+    stream = torch.cuda.current_stream()
+    d_in = [torch.from_numpy(np.frombuffer(g, dtype=np.uint8).copy()).cuda() for _, _, g in files]
+    d_out = [torch.empty(len(r) + 4096, dtype=torch.uint8, device="cuda") for _, r, _ in files]
+    jobs = [(d_in[k].data_ptr(), len(g), d_out[k].data_ptr(), d_out[k].numel()) for k, (_, _, g) in enumerate(files)]
+    refs = [torch.from_numpy(np.frombuffer(r, dtype=np.uint8).copy()).cuda() for _, r, _ in files]
+    rows = []
+    for item in spec.split(","):
+        cb, w, x = (int(v) for v in item.split("/"))
+        ctx = pgz.pgz_create(pgz.pgz_config_init(device=0, cuda_stream=stream.cuda_stream, n_chunks=0,
+                                                 chunk_bytes=cb, warps_per_block=w, exec_pipelined=x))
+        r, res, s = pgz.pgz_decompress_batch(ctx, jobs, stats=True)
+        torch.cuda.synchronize()
+        if r != 0:
+            raise RuntimeError(f"pgz_decompress_batch failed: {pgz.pgz_strerror(r)}")
+        for k, (_, raw, _) in enumerate(files):
+            if not torch.equal(d_out[k][:len(raw)], refs[k]):
+                raise RuntimeError("output mismatch")
+            d_out[k].zero_()
+        pgz.pgz_destroy(ctx)
+        rows.append({"chunk_bytes": cb, "warps_per_block": w, "exec_pipelined": x, "parts": s["chunks"],
+                     "ms_sync": round(s["ms_sync"], 3), "ms_inflate": round(s["ms_inflate"], 3)})
+    return {"case": desc + " (batched, one call per configuration)", "out_bytes": sum(len(r) for _, r, _ in files),
+            "configs": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -819,7 +866,7 @@ def main():
                     help="pass-1 CTA shape with a fixed --chunk-bytes or --profile-case")
     ap.add_argument("--exec-pipelined", type=int, default=0, choices=[0, 1],
                     help="pass-1 execution form with a fixed --chunk-bytes (default: autotuned)")
-    ap.add_argument("--profile-case", default=None, metavar="MIB:LEVEL:CALLS|batch:CALLS",
+    ap.add_argument("--profile-case", default=None, metavar="MIB:LEVEL:CALLS|batch:CALLS|batchsweep:C/W/P,...",
                     help="run one checked case for an ncu capture and print its stage times: one FASTQ file, or "
                          "the benchmark's two files as one batch")
     args = ap.parse_args()
