@@ -543,6 +543,7 @@ def run_batch512(args):
     ms_p = timed(step_plain)
     pgz.pgz_destroy(ctx_p)
     pgz.pgz_destroy(ctx)
+    cpu, zl = cpu_baseline_parallel(files)
     return {"workload": "512 synthetic members, log-uniform 64 KiB-64 MiB (seed 3), FASTQ/Markov, gzip -1/-6/-9",
             "in_bytes": total_in, "out_bytes": total_out, "make_s": round(t_make, 1), "parts": s["chunks"],
             "batched": {"value": round(total_out / (ms_b * 1e-3) / 1e9, 3), "ms_per_step": round(ms_b, 3),
@@ -550,7 +551,7 @@ def run_batch512(args):
             "plain": {"value": round(total_out / (ms_p * 1e-3) / 1e9, 3), "ms_per_step": round(ms_p, 3),
                       "form": "one pgz_decompress per member", "chunk_bytes": CHUNK_BYTES},
             "unit": "GB/s", "stages_ms_batched": {k: round(v, 3) for k, v in s.items() if k.startswith("ms_")},
-            "autotune": tune}
+            "autotune": tune, "cpu_baseline": cpu, "zlib_context": zl}
 
 
 def run_stream(args):
@@ -725,6 +726,46 @@ def cpu_baseline(files, budget_s: float = 20.0):
         sample.append(label)
     return {"value": round(done_out / t_used / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
             "sample": f"oracle.gunzip (one thread) over {', '.join(sample)} ({done_out >> 20} MiB out, {t_used:.1f} s)"}
+
+
+def cpu_baseline_parallel(members, target_s: float = 10.0):
+    """The oracle file-parallel on all host cores over a bounded sample of the members (list of (raw, gz)),
+    and host zlib on one core over the same sample as context.  The sample is the first members, in order,
+    up to about target_s seconds of the oracle's work per core (at 60 MB/s per core)."""
+    import zlib
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle
+    oracle.build()
+    cores = len(os.sched_getaffinity(0))
+    want = target_s * 60e6 * cores
+    sample, out = [], 0
+    for raw, gz in members:
+        if out >= want:
+            break
+        sample.append((raw, gz))
+        out += len(raw)
+
+    def one(m):
+        raw, gz = m
+        e, o, _, _ = oracle.gunzip(gz, cap=len(raw) + 1024)    # the C oracle releases the GIL
+        if e != 0 or len(o) != len(raw):
+            raise RuntimeError("oracle failed")
+        return len(raw)
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        done = sum(ex.map(one, sample))
+    t_or = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for raw, gz in sample:
+        if len(zlib.decompress(gz, 31)) != len(raw):
+            raise RuntimeError("zlib failed")
+    t_z = time.perf_counter() - t0
+    desc = f"the first {len(sample)} members ({done >> 20} MiB out)"
+    return ({"value": round(done / t_or / 1e9, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
+             "sample": f"oracle.gunzip, one member per thread on {cores} threads, over {desc}, {t_or:.1f} s"},
+            {"value": round(done / t_z / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "host zlib (context)",
+             "sample": f"zlib.decompress, one thread, over {desc}, {t_z:.1f} s"})
 
 
 def run_reference(args):
