@@ -58,3 +58,27 @@ def test_create_fails_cleanly_without_gpu(pgz):
     with pytest.raises(pgz.PgzError) as e:
         pgz.pgz_create(bad)
     assert e.value.status == pgz.PGZ_E_ARG
+
+
+def test_new_config_fields_and_their_validation(pgz):
+    cfg = pgz.pgz_config_init()
+    assert cfg.warps_per_block == 4 and cfg.exec_pipelined == 0
+    # invalid CTA shapes and execution forms are rejected before any device is touched
+    for bad in (pgz.pgz_config_init(warps_per_block=3), pgz.pgz_config_init(exec_pipelined=2)):
+        with pytest.raises(pgz.PgzError) as e:
+            pgz.pgz_create(bad)
+        assert e.value.status == pgz.PGZ_E_ARG
+    assert "sink" in pgz.pgz_strerror(pgz.PGZ_E_ABORTED)
+
+
+def test_calls_without_a_context_are_argument_errors(pgz):
+    L = pgz.lib()
+    n = ctypes.c_uint64(0)
+    sink = pgz.PGZ_SINK(lambda u, p, k: 0)
+    data = (ctypes.c_uint8 * 64)()
+    assert L.pgz_decompress_stream(None, data, 64, 1 << 20, sink, None, ctypes.byref(n), None) == pgz.PGZ_E_ARG
+    assert L.pgz_decompress_host(None, data, 64, data, 64, ctypes.byref(n), None) == pgz.PGZ_E_ARG
+    assert L.pgz_decompress(None, data, 64, data, 64, ctypes.byref(n), None) == pgz.PGZ_E_ARG
+    cb = (ctypes.c_uint64 * 1)(65536)
+    wp = (ctypes.c_int * 1)(4)
+    assert L.pgz_autotune(None, None, 1, cb, 1, wp, 1, 1, 1, None, None) == pgz.PGZ_E_ARG
