@@ -288,6 +288,13 @@ int pgz_autotune(pgz_ctx* ctx, pgz_job* jobs, int n_jobs, const uint64_t* chunk_
                  const int* warps_per_block, int n_wpb, int sweep_exec, int reps, pgz_tune_entry* entries,
                  pgz_tune_entry* best);
 
+/* Sets the context's part size (n_chunks = 0), pass-1 CTA shape and pass-1
+   execution form, as pgz_autotune does with its choice: for a configuration
+   chosen earlier (a tuning cache) without timing anything.  No device call.
+   PGZ_E_ARG for a NULL context, chunk_bytes < 4096, warps_per_block not 2, 4
+   or 8, or exec_pipelined not 0 or 1 (the context is then unchanged). */
+int pgz_set_tuning(pgz_ctx* ctx, uint64_t chunk_bytes, int warps_per_block, int exec_pipelined);
+
 /* ---------------------------------------------------------------------------
    Serving: a request loop with continuous batching.  Registered members stay
    resident (compressed input; for byte ranges also the index of part starts

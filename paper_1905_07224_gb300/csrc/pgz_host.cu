@@ -1335,6 +1335,19 @@ int pgz_inspect_window(pgz_ctx* ctx, int part, uint8_t* host_dst) {
 
 uint64_t pgz_kernel_launches(const pgz_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+int pgz_set_tuning(pgz_ctx* ctx, uint64_t chunk_bytes, int warps_per_block, int exec_pipelined) {
+    if (!ctx || chunk_bytes < 4096 || (warps_per_block != 2 && warps_per_block != 4 && warps_per_block != 8) ||
+        (exec_pipelined != 0 && exec_pipelined != 1))
+        return PGZ_E_ARG;
+    ctx->cfg.n_chunks = 0;
+    ctx->cfg.chunk_bytes = chunk_bytes;
+    ctx->cfg.warps_per_block = warps_per_block;
+    ctx->cfg.exec_pipelined = exec_pipelined;
+    ctx->kp.wpb = warps_per_block;
+    ctx->kp.pipe = exec_pipelined;
+    return PGZ_OK;
+}
+
 // --------------------------------------------------------------------------- streaming
 namespace {
 

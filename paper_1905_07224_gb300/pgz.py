@@ -81,6 +81,7 @@ def _load():
         "pgz_decompress": (ctypes.c_int, [VP, VP, U64, VP, U64, P(U64), P(pgz_stats)]),
         "pgz_decompress_host": (ctypes.c_int, [VP, VP, U64, VP, U64, P(U64), P(pgz_stats)]),
         "pgz_decompress_stream": (ctypes.c_int, [VP, VP, U64, U64, PGZ_SINK, VP, P(U64), P(pgz_stats)]),
+        "pgz_set_tuning": (ctypes.c_int, [VP, U64, ctypes.c_int, ctypes.c_int]),
         "pgz_decompress_at": (ctypes.c_int, [VP, VP, U64, U64, VP, VP, ctypes.c_uint8, U64, P(U64), P(U64), P(U64)]),
         "pgz_decompress_batch": (ctypes.c_int, [VP, ctypes.c_int, P(pgz_job), P(pgz_stats)]),
         "pgz_batch_prepare": (ctypes.c_int, [VP, ctypes.c_int, P(pgz_job), P(VP)]),
@@ -131,7 +132,7 @@ EXPORTED = ["pgz_config_init", "pgz_create", "pgz_destroy", "pgz_decompress", "p
             "pgz_inspect_symbols", "pgz_inspect_window", "pgz_kernel_launches", "pgz_strerror",
             "pgz_decompress_noalloc", "pgz_autotune", "pgz_server_create", "pgz_server_add_file",
             "pgz_server_submit", "pgz_server_poll", "pgz_server_drain", "pgz_server_pending", "pgz_server_destroy",
-            "pgz_extract_sequences", "pgz_decompress_stream"]
+            "pgz_extract_sequences", "pgz_decompress_stream", "pgz_set_tuning"]
 
 
 def pgz_strerror(status: int) -> str:
@@ -179,6 +180,11 @@ def pgz_decompress_host(ctx: int, gz, out: np.ndarray, stats: bool = False):
     r = lib().pgz_decompress_host(ctx, a.ctypes.data, a.size, out.ctypes.data, out.size, ctypes.byref(n),
                                   ctypes.byref(st) if st is not None else None)
     return r, n.value, (st.as_dict() if st is not None else None)
+
+
+def pgz_set_tuning(ctx: int, chunk_bytes: int, warps_per_block: int, exec_pipelined: int) -> int:
+    """Applies a part size, CTA shape and execution form chosen earlier; returns the status."""
+    return lib().pgz_set_tuning(ctx, chunk_bytes, warps_per_block, exec_pipelined)
 
 
 def pgz_decompress_stream(ctx: int, gz, segment_bytes: int = 0, sink=None, stats: bool = False):

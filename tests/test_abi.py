@@ -82,3 +82,7 @@ def test_calls_without_a_context_are_argument_errors(pgz):
     cb = (ctypes.c_uint64 * 1)(65536)
     wp = (ctypes.c_int * 1)(4)
     assert L.pgz_autotune(None, None, 1, cb, 1, wp, 1, 1, 1, None, None) == pgz.PGZ_E_ARG
+
+
+def test_set_tuning_without_a_context(pgz):
+    assert pgz.pgz_set_tuning(None, 65536, 4, 0) == pgz.PGZ_E_ARG

@@ -79,6 +79,35 @@ def test_autotune_picks_the_fastest_working_pair():
     ctx.close()
 
 
+def test_a_cached_tuning_is_applied_without_timing(tmp_path):
+    from paper_1905_07224_gb300 import tune_cache as tc
+    raw = synth.fastq(8 << 20, 150, 0.01, 3)
+    gz = synth.gzip_compress(raw, 1)
+    d = to_device(gz)
+    out = empty(len(raw) + 4096)
+    job = [(d.data_ptr(), len(gz), out.data_ptr(), out.numel())]
+    key = tc.cache_key("test-gpu", gz[8], len(gz))
+    path = str(tmp_path / "tune.json")
+    ctx = Ctx()
+    st, e, hit = tc.autotune_cached(ctx.pgz, ctx.h, job, key, tc.TuneCache(path), [32 << 10, 128 << 10], [4, 8], 1)
+    assert st == 0 and not hit
+    ctx.close()
+    ctx = Ctx()                                           # a new context: the stored choice, no timing
+    st, e, hit = tc.autotune_cached(ctx.pgz, ctx.h, job, key, tc.TuneCache(path), [32 << 10], [4], 1)
+    assert st == 0 and hit
+    out.zero_()
+    st, n, s = ctx.pgz.pgz_decompress(ctx.h, d.data_ptr(), len(gz), out.data_ptr(), out.numel(), True)
+    assert st == 0 and n == len(raw) and _same_on_device(out, raw)
+    assert s["chunks"] == (len(gz) - 18 + e["chunk_bytes"] - 1) // e["chunk_bytes"]
+    # invalid values leave the context as it was
+    assert ctx.pgz.pgz_set_tuning(ctx.h, 1024, 4, 0) == ctx.pgz.PGZ_E_ARG
+    assert ctx.pgz.pgz_set_tuning(ctx.h, 65536, 5, 0) == ctx.pgz.PGZ_E_ARG
+    assert ctx.pgz.pgz_set_tuning(ctx.h, 65536, 4, 7) == ctx.pgz.PGZ_E_ARG
+    st, n, s = ctx.pgz.pgz_decompress(ctx.h, d.data_ptr(), len(gz), out.data_ptr(), out.numel(), True)
+    assert st == 0 and s["chunks"] == (len(gz) - 18 + e["chunk_bytes"] - 1) // e["chunk_bytes"]
+    ctx.close()
+
+
 @pytest.mark.parametrize("wpb", [2, 8])
 def test_cta_shapes_match_the_oracle(wpb):
     data = synth.fastq(1 << 20, 100, 0.001, 0)
