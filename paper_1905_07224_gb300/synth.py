@@ -158,6 +158,18 @@ def markov(n_bytes: int, seed: int = 0) -> bytes:
 # ---------------------------------------------------------------------------
 # compression (host zlib, called as a library) and the paper's workloads
 # ---------------------------------------------------------------------------
+def binary_records(n_bytes: int, seed: int = 0) -> bytes:
+    """Structured binary data (bytes of every value): little-endian 14-byte records of a counter (u32, step
+    3), six small integers (u8, 0..11) and a normal float32 rounded to 0.01; exactly n_bytes."""
+    rng = np.random.default_rng(seed)
+    n = n_bytes // 14 + 1
+    rec = np.zeros(n, dtype=[("id", "<u4"), ("q", "u1", 6), ("x", "<f4")])
+    rec["id"] = np.arange(n, dtype=np.uint32) * 3 + 1000
+    rec["q"] = rng.integers(0, 12, size=(n, 6))
+    rec["x"] = np.round(rng.normal(0, 1, n), 2).astype(np.float32)
+    return rec.tobytes()[:n_bytes]
+
+
 def gzip_compress(data: bytes, level: int = 6) -> bytes:
     """Single-member gzip (10-byte header) via host zlib at ``level``."""
     c = zlib.compressobj(level, zlib.DEFLATED, 31)

@@ -100,6 +100,39 @@ def test_levels_and_kinds(level, kind, pipe):
         ctx.close()
 
 
+@pytest.mark.parametrize("level", [1, 9])
+def test_binary_data_with_every_byte_allowed(level):
+    """Bytes of every value: with the allowed-byte mask opened to all 256 values, the block-start predicate
+    rests on the block structure alone.  The output must be exact.  Every part start the run kept must be a
+    true block start of the member (false ones are rejected by the chain check), and the member must really
+    be split.  With the default ASCII mask no part start passes, and the first part decodes everything,
+    exactly."""
+    raw = synth.binary_records(1 << 20, 7)
+    gz = synth.gzip_compress(raw, level)
+    e, ref, blocks, _ = oracle.gunzip(gz, max_blocks=4096)
+    assert e == 0 and ref == raw
+    true_starts = {int(b) for b in blocks}
+    every = np.full(32, 0xFF, dtype=np.uint8)
+    ctx = Ctx(n_chunks=32, allowed=every)
+    try:
+        st, out, n, s = ctx.decompress(gz, stats=True)
+        assert st == 0, ctx.pgz.pgz_strerror(st)
+        assert out == raw
+        sb, ns, _ = ctx.pgz.pgz_inspect_parts(ctx.h)
+        kept = [int(b) for b, k in zip(sb, ns) if k > 0]
+        assert set(kept) <= true_starts
+        assert len(kept) >= 8
+    finally:
+        ctx.close()
+    ctx = Ctx(n_chunks=32)
+    try:
+        st, out, n, s = ctx.decompress(gz, stats=True)
+        assert st == 0 and out == raw
+        assert s["empty_chunks"] == 31
+    finally:
+        ctx.close()
+
+
 def _hand(blocks):
     w = dw.BitWriter()
     text = b""

@@ -426,3 +426,21 @@ def test_sequence_heuristic_brute_force():
             else:
                 i += 1
         assert oracle.sequences(_seq_syms(text)) == want, text
+
+
+@pytest.mark.parametrize("level", [1, 6, 9])
+def test_binary_safe_block_start_predicate(level):
+    """Data with bytes of every value: with every byte allowed, the predicate rests on the block structure
+    alone (complete codes, block size, distances) and the two passes split the member into parts and stay
+    exact; with the ASCII mask no start passes and everything is decoded from the first block, still
+    exactly.  Pinned by zlib's output."""
+    raw = synth.binary_records(1 << 20, 7)
+    assert len(set(raw)) == 256 or max(raw) > 126
+    gz = synth.gzip_compress(raw, level)
+    every = np.full(32, 0xFF, dtype=np.uint8)
+    r = oracle.two_pass(gz, 32, allowed=every)
+    assert r["status"] == 0 and r["out"] == raw == zlib.decompress(gz, 31)
+    assert int((r["part_len"] > 0).sum()) >= 16
+    r = oracle.two_pass(gz, 32)
+    assert r["status"] == 0 and r["out"] == raw
+    assert int((r["part_len"] > 0).sum()) == 1
