@@ -398,6 +398,7 @@ def run_pgz(args, rank, world):
     }
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(files)
+        line["zlib_context"] = zlib_context(files)
     return line
 
 
@@ -726,6 +727,20 @@ def cpu_baseline(files, budget_s: float = 20.0):
         sample.append(label)
     return {"value": round(done_out / t_used / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
             "sample": f"oracle.gunzip (one thread) over {', '.join(sample)} ({done_out >> 20} MiB out, {t_used:.1f} s)"}
+
+
+def zlib_context(files):
+    """Host zlib inflate, one thread, on the same files: context beside the oracle, not a target."""
+    import zlib
+    t0 = time.perf_counter()
+    done = 0
+    for _, raw, gz in files:
+        if len(zlib.decompress(gz, 31)) != len(raw):
+            raise RuntimeError("zlib failed")
+        done += len(raw)
+    dt = time.perf_counter() - t0
+    return {"value": round(done / dt / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "host zlib (context)",
+            "sample": f"zlib.decompress (one thread) over the step's files ({done >> 20} MiB out, {dt:.1f} s)"}
 
 
 def cpu_baseline_parallel(members, target_s: float = 10.0):
