@@ -193,19 +193,26 @@ def pgz_decompress_stream(ctx: int, gz, segment_bytes: int = 0, sink=None, stats
     and returned as bytes in `out`."""
     a = np.frombuffer(gz, dtype=np.uint8) if isinstance(gz, (bytes, bytearray)) else np.ascontiguousarray(gz)
     parts = []
+    raised = []
 
     def _cb(_user, p, n):
         view = (ctypes.c_uint8 * n).from_address(p)
         if sink is None:
             parts.append(bytes(view))
             return 0
-        return 1 if sink(memoryview(view)) else 0
+        try:
+            return 1 if sink(memoryview(view)) else 0
+        except BaseException as exc:                 # stop the decode; re-raised after the call returns
+            raised.append(exc)
+            return 1
 
     cb = PGZ_SINK(_cb)
     n = U64(0)
     st = pgz_stats() if stats else None
     r = lib().pgz_decompress_stream(ctx, a.ctypes.data, a.size, segment_bytes, cb, None, ctypes.byref(n),
                                     ctypes.byref(st) if st is not None else None)
+    if raised:
+        raise raised[0]
     return r, n.value, (st.as_dict() if st is not None else None), (b"".join(parts) if sink is None else None)
 
 

@@ -129,6 +129,11 @@ def test_stream_errors():
             return len(seen) >= 2
         st, n, _, _ = pgz.pgz_decompress_stream(ctx.h, gz, MIB, sink=stop_after_one)
         assert st == pgz.PGZ_E_ABORTED and n == seen[0] and len(seen) == 2
+        # an exception in the sink stops the decode and reaches the caller
+        def boom(v):
+            raise KeyError("sink failed")
+        with pytest.raises(KeyError):
+            pgz.pgz_decompress_stream(ctx.h, gz, MIB, sink=boom)
         # the context still decodes after every failure
         st, n, _, out = pgz.pgz_decompress_stream(ctx.h, gz, MIB)
         assert st == 0 and out == raw
