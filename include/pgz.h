@@ -20,13 +20,15 @@
  *
  * Conventions for every call:
  *  - Pointers named "device" must point to memory of the context's device
- *    (cudaMalloc / torch tensors); "host" pointers to host memory.  The
- *    compressed input must be 4-byte aligned; otherwise PGZ_E_ARG.
+ *    (cudaMalloc / torch tensors); "host" pointers to host memory.  Compressed
+ *    input in device memory must be 4-byte aligned; otherwise PGZ_E_ARG.
  *  - The caller owns every input and output buffer.  The context owns its
  *    scratch memory, which grows on demand and is kept between calls.
  *  - Work is issued on the context's CUDA stream (pgz_config.cuda_stream);
  *    calls return after their final status has been read back, i.e. they
- *    synchronise that stream once or twice.
+ *    synchronise that stream once or twice.  pgz_decompress_stream also
+ *    copies on two streams of its own, and each server slot has its own
+ *    context and stream.
  *  - Return values are pgz_status codes; pgz_strerror() names them.  No call
  *    aborts the process or faults the GPU on malformed input: every device
  *    read is bounds-checked against the buffer sizes given here.
@@ -73,8 +75,9 @@ typedef struct pgz_config {
     uint64_t dev_mem_budget;    /* upper bound on scratch bytes; 0 = none */
     uint64_t spin_cap;          /* reserved for bounded device waits; 0 = default */
     int warps_per_block;        /* CTA shape of the pass-1 kernels: 2, 4 or 8 warps (one part each); 0 = 4 */
-    int exec_pipelined;         /* 1: pass 1 executes tokens in pipelined passes (faster when sources lie far
-                                   back), 0: one pass at a time (default); pgz_autotune can choose */
+    int exec_pipelined;         /* 1: pass 1 executes tokens in pipelined passes, 0: one pass at a time
+                                   (default); which is faster depends on the data and the part size, and
+                                   pgz_autotune can choose */
 } pgz_config;
 
 /* per-call statistics; the ms_* fields are CUDA-event times of the stages */
@@ -160,8 +163,10 @@ typedef int (*pgz_sink)(void* user, const uint8_t* bytes, uint64_t n);
    Device memory in use is bounded by the segment, not by the member: about
    17 bytes per compressed byte of a segment at 64 KiB parts for data that
    expands at most 2x (input, symbol scratch, output, windows); more where a
-   segment expands further, its capacities doubling on demand.  segment_bytes: 0 for 256 MiB, else at least 1 MiB
-   (PGZ_E_ARG otherwise).  *out_len: bytes delivered to the sink.
+   segment expands further, its capacities doubling on demand.
+   gz [host, gz_len bytes]: one gzip member.  segment_bytes: 0 for 256 MiB,
+   else at least 1 MiB (PGZ_E_ARG otherwise).  *out_len: bytes delivered to
+   the sink.
    st (nullable): statistics summed over the segments' runs.
    Errors: PGZ_E_HEADER, PGZ_E_DATA, PGZ_E_CRC, PGZ_E_ISIZE and
    PGZ_E_UNSUPPORTED (data after the member) as for pgz_decompress;
