@@ -832,7 +832,7 @@ def run_reference(args, budget_s: float = 150.0, oracle_gbs: float = 0.06):
             "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def run_profile_case(spec: str, chunk_bytes: int, wpb: int = 4):
+def run_profile_case(spec: str, chunk_bytes: int, wpb: int = 4, xp: int = 0):
     """--profile-case MIB:LEVEL:CALLS -- a small fixed case for ncu captures: one synthetic FASTQ file
     (150 bp, seed 1) of MIB MiB at gzip LEVEL, decompressed CALLS times through pgz_decompress on device
     buffers; the output of the last call is checked byte for byte and its stage times printed."""
@@ -840,7 +840,7 @@ def run_profile_case(spec: str, chunk_bytes: int, wpb: int = 4):
     import torch
     from paper_1905_07224_gb300 import build, pgz, synth
     if spec.startswith("batch:"):
-        return run_profile_batch(int(spec.split(":")[1]), chunk_bytes, wpb)
+        return run_profile_batch(int(spec.split(":")[1]), chunk_bytes, wpb, xp)
     if spec.startswith("batchsweep:"):
         return run_profile_sweep(spec.split(":", 1)[1])
     mib, level, calls = (int(x) for x in spec.split(":"))
@@ -849,7 +849,7 @@ def run_profile_case(spec: str, chunk_bytes: int, wpb: int = 4):
     gz = synth.gzip_compress(raw, level)
     stream = torch.cuda.current_stream()
     ctx = pgz.pgz_create(pgz.pgz_config_init(device=0, cuda_stream=stream.cuda_stream, n_chunks=0,
-                                             chunk_bytes=chunk_bytes, warps_per_block=wpb))
+                                             chunk_bytes=chunk_bytes, warps_per_block=wpb, exec_pipelined=xp))
     d_in = torch.from_numpy(np.frombuffer(gz, dtype=np.uint8).copy()).cuda()
     d_out = torch.empty(len(raw) + 4096, dtype=torch.uint8, device="cuda")
     for _ in range(calls):
@@ -864,7 +864,7 @@ def run_profile_case(spec: str, chunk_bytes: int, wpb: int = 4):
             **{k: (round(v, 3) if isinstance(v, float) else v) for k, v in s.items()}}
 
 
-def run_profile_batch(calls: int, chunk_bytes: int, wpb: int):
+def run_profile_batch(calls: int, chunk_bytes: int, wpb: int, xp: int = 0):
     """--profile-case batch:CALLS -- the benchmark's two files decoded together by pgz_decompress_batch (the
     batched form without the graph), CALLS times; outputs checked."""
     import numpy as np
@@ -874,7 +874,7 @@ def run_profile_batch(calls: int, chunk_bytes: int, wpb: int):
     files, desc = make_workload("fastq256")
     stream = torch.cuda.current_stream()
     ctx = pgz.pgz_create(pgz.pgz_config_init(device=0, cuda_stream=stream.cuda_stream, n_chunks=0,
-                                             chunk_bytes=chunk_bytes, warps_per_block=wpb))
+                                             chunk_bytes=chunk_bytes, warps_per_block=wpb, exec_pipelined=xp))
     d_in = [torch.from_numpy(np.frombuffer(g, dtype=np.uint8).copy()).cuda() for _, _, g in files]
     d_out = [torch.empty(len(r) + 4096, dtype=torch.uint8, device="cuda") for _, r, _ in files]
     jobs = [(d_in[k].data_ptr(), len(g), d_out[k].data_ptr(), d_out[k].numel()) for k, (_, _, g) in enumerate(files)]
@@ -887,7 +887,7 @@ def run_profile_batch(calls: int, chunk_bytes: int, wpb: int):
         if d_out[k][:len(raw)].cpu().numpy().tobytes() != raw:
             raise RuntimeError("output mismatch")
     pgz.pgz_destroy(ctx)
-    return {"case": desc + " (batched)", "chunk_bytes": chunk_bytes, "warps_per_block": wpb,
+    return {"case": desc + " (batched)", "chunk_bytes": chunk_bytes, "warps_per_block": wpb, "exec_pipelined": xp,
             **{k: (round(v, 3) if isinstance(v, float) else v) for k, v in s.items()}}
 
 
@@ -947,8 +947,8 @@ def main():
                          "the benchmark's two files as one batch")
     args = ap.parse_args()
     if args.profile_case:
-        print(json.dumps(run_profile_case(args.profile_case, args.chunk_bytes or CHUNK_BYTES, args.warps_per_block)),
-              flush=True)
+        print(json.dumps(run_profile_case(args.profile_case, args.chunk_bytes or CHUNK_BYTES, args.warps_per_block,
+                                          args.exec_pipelined)), flush=True)
         return
     args.warmup = max(3, args.warmup)
     if args.workload in ("fastq4g", "batch512", "served", "stream") and args.impl == "pgz":
