@@ -444,3 +444,34 @@ def test_binary_safe_block_start_predicate(level):
     r = oracle.two_pass(gz, 32)
     assert r["status"] == 0 and r["out"] == raw
     assert int((r["part_len"] > 0).sum()) == 1
+
+
+def test_fuzz_against_zlib_every_window_size_and_strategy():
+    """Seeded fuzz: inputs mixing text, binary records, long runs and random bytes, compressed by zlib with
+    every window size (wbits 9..15), memLevel, strategy and level; the oracle's gunzip and its two passes
+    must give zlib's output exactly (a smaller window is a special case of the 32 KiB one)."""
+    rng = np.random.default_rng(11)
+    strategies = [zlib.Z_DEFAULT_STRATEGY, zlib.Z_FILTERED, zlib.Z_HUFFMAN_ONLY, zlib.Z_RLE, zlib.Z_FIXED]
+    every = np.full(32, 0xFF, dtype=np.uint8)
+    for case in range(40):
+        pieces = []
+        for _ in range(int(rng.integers(1, 5))):
+            kind = int(rng.integers(0, 4))
+            n = int(rng.integers(1, 60000))
+            if kind == 0:
+                pieces.append(synth.fastq(n, 100, 0.01, int(rng.integers(1 << 30))))
+            elif kind == 1:
+                pieces.append(synth.binary_records(n, int(rng.integers(1 << 30))))
+            elif kind == 2:
+                pieces.append(bytes([int(rng.integers(256))]) * n)
+            else:
+                pieces.append(rng.integers(0, 256, n, dtype=np.uint8).tobytes())
+        raw = b"".join(pieces)
+        c = zlib.compressobj(int(rng.integers(0, 10)), zlib.DEFLATED, 16 + int(rng.integers(9, 16)),
+                             int(rng.integers(1, 10)), strategies[int(rng.integers(len(strategies)))])
+        gz = c.compress(raw) + c.flush()
+        e, out, _, _ = oracle.gunzip(gz)
+        assert e == 0 and out == raw, case
+        for nparts in (3, 8):
+            r = oracle.two_pass(gz, nparts, allowed=every)
+            assert r["status"] == 0 and r["out"] == raw, (case, nparts)
