@@ -197,6 +197,20 @@ int pgz_decompress_at(pgz_ctx* ctx, const uint8_t* gz, uint64_t gz_len, uint64_t
    job's status; each job's own status and out_len are filled in. */
 int pgz_decompress_batch(pgz_ctx* ctx, int n, pgz_job* jobs, pgz_stats* st);
 
+/* The same method over many members held in HOST memory (Section "Full
+   file decompression in two passes", over a batch): jobs [host array of n],
+   each job's gz and out are HOST pointers (page-locked memory lets the copies
+   overlap the decoding; pageable memory works but copies synchronously).  The
+   jobs are cut into up to 4 groups of consecutive jobs with about equal
+   compressed bytes (groups of at least 96 MiB).  Every group is copied to
+   device memory owned by the context, decoded by one run of the pass kernels
+   as soon as its own copy has arrived, and its output copied back to the
+   jobs' `out` while the next group decodes.  Statuses, out_len and the return
+   value as for pgz_decompress_batch; st (nullable) receives in_bytes,
+   out_bytes and chunks (the ms_* fields are not timed here).  The call returns
+   when every output is in host memory. */
+int pgz_decompress_batch_host(pgz_ctx* ctx, int n, pgz_job* jobs, pgz_stats* st);
+
 /* A batch planned once and replayed as one CUDA graph: pgz_batch_prepare
    reads the jobs' headers, sizes the scratch and captures the stage
    launches; pgz_batch_run replays them on the context's stream and reads the
@@ -240,8 +254,15 @@ int pgz_inspect_window(pgz_ctx* ctx, int part, uint8_t* host_dst /* 32768 bytes 
    header <= 4 KiB; larger inputs return PGZ_E_ARG.  The first call on a device
    sets up the array's address there; make it before any stream capture.
    Calls share the array: calls that overlap on the GPU (other streams or
-   threads) race and must be serialised by the caller.  Default configuration
-   (pgz_config_init).  *out_len as for pgz_decompress. */
+   threads) race and must be serialised by the caller.
+   One gzip member per call: data after the member's trailer returns
+   PGZ_E_UNSUPPORTED (pgz_decompress accepts several members).  The
+   configuration is pgz_config_init's (allowed bytes, confirmation, block
+   bounds, 4 warps per pass-1 block, one execution pass at a time), except the
+   part size: 32 KiB of compressed data, at most 64 parts; when a part needs
+   more symbols than its share of the array, the call is re-planned with half
+   as many parts.  Recovery from false block starts is that of
+   pgz_decompress.  *out_len: bytes written. */
 int pgz_decompress_noalloc(const uint8_t* gz, uint64_t gz_len, uint8_t* out, uint64_t out_cap,
                            uint64_t* out_len, void* cuda_stream);
 

@@ -18,6 +18,118 @@
 
 using namespace pgz;
 
+namespace pgz {
+
+namespace {
+
+// a part whose block start was searched (not the member start, not a known start, not a segment-end probe)
+bool searched_start(const FileDesc& F, const ChunkDesc& C, const ChunkDesc& R) {
+    return !C.given && !C.probe && !C.disabled && R.sync != kNone && !(C.index == 0 && C.lo <= F.s0_bit);
+}
+
+// the part that holds the next block start after part c (the part k_inflate stopped at), or -1
+int next_start(const FileDesc& F, const ChunkDesc* res, int c) {
+    for (int j = c + 1; j < F.chunk0 + F.nchunks; ++j)
+        if (res[j].sync != kNone) return j;
+    return -1;
+}
+
+// The confirmation of part c's start: its block and the confirm_blocks blocks after it must decode with the
+// checks (Section "Detection of DEFLATE block start positions").  A part checks the blocks it decodes itself;
+// when it ends exactly on the next part's start before the window is complete, the blocks of that part are
+// the same chain's next blocks, and their checks (made by that part) continue the window.  Returns the
+// 1-based position of the first failing block in the window, 0 if the window passed, -1 if the run's results
+// do not settle it.
+int confirm_failure(const FileDesc& F, const ChunkDesc* res, int c, int confirm_blocks) {
+    const int window = confirm_blocks + 1;
+    int before = 0;                                  // blocks of the window decoded by earlier parts
+    for (;;) {
+        const ChunkDesc& R = res[c];
+        if (R.confirmed) return 0;
+        if (R.state == CS_ERROR && R.err == CE_CONFIRM) {
+            const int k = before + (int)R.blocks + 1;
+            return k <= window ? k : 0;
+        }
+        if (R.state != CS_DONE) return -1;
+        before += (int)R.blocks;
+        if (before >= window) return 0;
+        const int j = next_start(F, res, c);
+        if (j < 0 || res[j].sync != R.end) return -1;
+        c = j;
+    }
+}
+
+}  // namespace
+
+int recover_member(const FileDesc& F, ChunkDesc* plan, const ChunkDesc* res, int confirm_blocks,
+                   uint64_t* false_syncs, int* grow) {
+    const int c0 = F.chunk0, c1 = F.chunk0 + F.nchunks;
+    // a streamed segment whose probe found no block start: its last part ran to the end of the segment's
+    // bytes; only a longer look-ahead helps (the caller's decision)
+    if (F.mode == 3 && !F.last_seg && res[c1 - 1].state == CS_EMPTY) return kRecoverStop;
+    // 1. starts that failed their confirmation: the search goes on from the bit after each
+    bool again = false;
+    if (confirm_blocks > 0)
+        for (int c = c0; c < c1; ++c) {
+            if (!searched_start(F, plan[c], res[c])) continue;
+            if (confirm_failure(F, res, c, confirm_blocks) > 0) {
+                plan[c].lo = res[c].sync + 1;
+                plan[c].confirm_ext = 0;
+                again = true;
+            }
+        }
+    if (again) return kRecoverRerun;
+    // 2. the first failing part, in order: every part before it ended on the next start, so its own start
+    // lies on the member's chain of blocks
+    for (int c = c0; c < c1; ++c) {
+        const ChunkDesc& R = res[c];
+        if (R.state != CS_ERROR) continue;
+        ChunkDesc& C = plan[c];
+        if (R.err == CE_OVERFLOW) {
+            *grow = c;
+            return kRecoverGrow;
+        }
+        if (R.err == CE_TRAIL) return kRecoverStop;
+        if (R.err == CE_CHAIN) {
+            const int j = next_start(F, res, c);
+            if (j < 0) return kRecoverStop;
+            if (res[j].state == CS_ERROR && res[j].err == CE_OVERFLOW) {
+                *grow = j;
+                return kRecoverGrow;
+            }
+            if (plan[j].probe) {                  // a false block start at the segment's end: search on after it
+                plan[j].lo = res[j].sync + 1;
+                ++*false_syncs;
+                return kRecoverRerun;
+            }
+            // the start of part j is not on the chain.  Its confirmation decides between the next start of
+            // its search (failed, handled above) and no start in its range (passed: merge); when the run left
+            // it open, part j first decodes past its stop to settle it
+            if (confirm_blocks > 0 && searched_start(F, plan[j], res[j]) && !plan[j].confirm_ext &&
+                confirm_failure(F, res, j, confirm_blocks) < 0) {
+                plan[j].confirm_ext = 1;
+                return kRecoverRerun;
+            }
+            plan[j].disabled = 1;
+            ++*false_syncs;
+            return kRecoverRerun;
+        }
+        if (C.index == 0 && C.lo <= F.s0_bit) return kRecoverStop;
+        if (C.given) return kRecoverStop;
+        if (R.err == CE_CONFIRM && R.sync != kNone) {
+            C.lo = R.sync + 1;
+            C.confirm_ext = 0;
+            return kRecoverRerun;
+        }
+        C.disabled = 1;
+        ++*false_syncs;
+        return kRecoverRerun;
+    }
+    return kRecoverStop;
+}
+
+}  // namespace pgz
+
 namespace {
 
 constexpr uint64_t kMaxPartSymbols = (1ull << 31) - 256;   // part positions are 32-bit in the kernels
@@ -164,6 +276,12 @@ struct pgz_ctx {
     PBuf stage[2];             // streaming: pinned output of two segments
     uint64_t launches = 0;
     cudaEvent_t ev[8] = {};
+    // host-buffer batches: device copies of the jobs, and one plan per group of jobs in flight
+    static constexpr int kHostGroups = 4;
+    DBuf hb_in, hb_out;
+    Plan hb_plan[kHostGroups];
+    cudaStream_t hb_up = nullptr, hb_down = nullptr;
+    cudaEvent_t hb_ev_up[kHostGroups] = {}, hb_ev_run[kHostGroups] = {};
 };
 
 struct pgz_batch {
@@ -370,63 +488,18 @@ int count_and_read_chunks(pgz_ctx* ctx, Plan& P) {
     return read_chunks(ctx, P);
 }
 
-// Adjusts the plan after a failed run; returns true if a re-run may succeed.
-//  - a part that overflowed its symbol capacity gets twice the capacity;
-//  - a part that did not end exactly on the next accepted block start shows
-//    that start was false: that part is merged into its predecessor;
-//  - a part whose confirmation blocks failed searches again from the bit
-//    after its start (Section "Detection of DEFLATE block start positions");
-//  - any other decoding error of a part after the first marks its start as
-//    false (merge); an error in the first part is final.
-bool recover(Plan& P, int f, const ChunkDesc* res, uint64_t* false_syncs) {
-    FileDesc& F = P.files[f];
-    // a streamed segment whose probe found no block start: its last part ran to the end of the segment's
-    // bytes; only a longer look-ahead helps (the caller's decision)
-    if (F.mode == 3 && !F.last_seg) {
-        const int pr = F.chunk0 + F.nchunks - 1;
-        if (res[pr].state == CS_EMPTY) return false;
-    }
-    for (int c = F.chunk0; c < F.chunk0 + F.nchunks; ++c) {
-        const ChunkDesc& R = res[c];
-        if (R.state != CS_ERROR) continue;
-        ChunkDesc& C = P.chunks[c];
-        if (R.err == CE_OVERFLOW) {
-            if (C.cap >= kMaxPartSymbols) return false;
-            C.cap = std::min<uint64_t>(C.cap * 2, kMaxPartSymbols);
-            return true;
-        }
-        if (R.err == CE_TRAIL) return false;
-        if (R.err == CE_CHAIN) {
-            for (int j = c + 1; j < F.chunk0 + F.nchunks; ++j) {
-                if (res[j].state == CS_EMPTY || P.chunks[j].disabled) continue;
-                if (res[j].state == CS_ERROR && res[j].err == CE_OVERFLOW) {
-                    if (P.chunks[j].cap >= kMaxPartSymbols) return false;
-                    P.chunks[j].cap = std::min<uint64_t>(P.chunks[j].cap * 2, kMaxPartSymbols);
-                    return true;
-                }
-                if (P.chunks[j].probe) {         // a false block start at the segment's end: search on after it
-                    if (res[j].sync == kNone) return false;
-                    P.chunks[j].lo = res[j].sync + 1;
-                    ++*false_syncs;
-                    return true;
-                }
-                P.chunks[j].disabled = 1;
-                ++*false_syncs;
-                return true;
-            }
-            return false;
-        }
-        if (C.index == 0 && C.lo == F.s0_bit) return false;
-        if (C.given) return false;
-        if (R.err == CE_CONFIRM && R.sync != kNone) {
-            C.lo = R.sync + 1;
-            return true;
-        }
-        C.disabled = 1;
-        ++*false_syncs;
+// Adjusts the plan after a failed run; returns true if a re-run may succeed (an overflowing part gets twice
+// its symbol capacity; the rest is recover_member's).
+bool recover(pgz_ctx* ctx, Plan& P, int f, const ChunkDesc* res, uint64_t* false_syncs) {
+    int grow = -1;
+    const int a = recover_member(P.files[f], P.chunks.data(), res, ctx->kp.confirm_blocks, false_syncs, &grow);
+    if (a == kRecoverGrow) {
+        ChunkDesc& C = P.chunks[grow];
+        if (C.cap >= kMaxPartSymbols) return false;
+        C.cap = std::min<uint64_t>(C.cap * 2, kMaxPartSymbols);
         return true;
     }
-    return false;
+    return a == kRecoverRerun;
 }
 
 void reset_results(Plan& P) {
@@ -512,7 +585,7 @@ int finish_run(pgz_ctx* ctx, Plan& P, pgz_stats* st) {
             P.files[f].status = hf[f].status;
             if (hf[f].status == PGZ_OK) continue;
             if (hf[f].bad_chunk != 0xffffffffu && retries < (uint64_t)kMaxRetries &&
-                recover(P, (int)f, res, &false_syncs)) {
+                recover(ctx, P, (int)f, res, &false_syncs)) {
                 again = true;
             } else if (status == PGZ_OK) {
                 status = (int)hf[f].status;
@@ -1056,6 +1129,17 @@ void pgz_destroy(pgz_ctx* ctx) {
     ctx->fill_buf.release();
     for (int k = 0; k < 8; ++k)
         if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
+    if (ctx->hb_up) cudaStreamSynchronize(ctx->hb_up);
+    if (ctx->hb_down) cudaStreamSynchronize(ctx->hb_down);
+    for (int g = 0; g < pgz_ctx::kHostGroups; ++g) {
+        ctx->hb_plan[g].release();
+        if (ctx->hb_ev_up[g]) cudaEventDestroy(ctx->hb_ev_up[g]);
+        if (ctx->hb_ev_run[g]) cudaEventDestroy(ctx->hb_ev_run[g]);
+    }
+    ctx->hb_in.release();
+    ctx->hb_out.release();
+    if (ctx->hb_up) cudaStreamDestroy(ctx->hb_up);
+    if (ctx->hb_down) cudaStreamDestroy(ctx->hb_down);
     delete ctx;
 }
 
@@ -1187,6 +1271,147 @@ int pgz_decompress_batch(pgz_ctx* ctx, int n, pgz_job* jobs, pgz_stats* st) {
     for (int k = 0; k < n; ++k)
         if (jobs[k].status != PGZ_OK && first_bad == PGZ_OK) first_bad = jobs[k].status;
     return first_bad;
+}
+
+// Jobs in host memory.  The jobs are cut into up to kHostGroups groups of consecutive jobs with about equal
+// compressed bytes.  All uploads are issued at once on an upload stream; each group's run of the pass
+// kernels waits only for its own upload, and the runs follow each other on the context's stream with no
+// host wait between them; each group's output goes down on a download stream as soon as its run ends.
+// The host then collects the results group by group; a group that needs recovery (a false block start, a
+// capacity) is re-run with recovery and its output copied again.
+int pgz_decompress_batch_host(pgz_ctx* ctx, int n, pgz_job* jobs, pgz_stats* st) {
+    if (!ctx || n < 0 || (n && !jobs)) return PGZ_E_ARG;
+    cudaSetDevice(ctx->cfg.device);
+    if (st) memset(st, 0, sizeof *st);
+    if (n == 0) return PGZ_OK;
+    constexpr int G = pgz_ctx::kHostGroups;
+    if (!ctx->hb_up) {
+        if (cudaStreamCreateWithFlags(&ctx->hb_up, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&ctx->hb_down, cudaStreamNonBlocking) != cudaSuccess)
+            return PGZ_E_CUDA;
+        for (int g = 0; g < G; ++g)
+            if (cudaEventCreateWithFlags(&ctx->hb_ev_up[g], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ctx->hb_ev_run[g], cudaEventDisableTiming) != cudaSuccess)
+                return PGZ_E_CUDA;
+    }
+    // headers and trailers from the host copies; device offsets (16-byte aligned) of every job
+    std::vector<MemberInfo> mi((size_t)n);
+    std::vector<uint64_t> in_off((size_t)n), out_off((size_t)n), down((size_t)n, 0);
+    std::vector<char> valid((size_t)n, 0);
+    uint64_t in_total = 0, out_total = 0;
+    for (int k = 0; k < n; ++k) {
+        pgz_job& J = jobs[k];
+        J.out_len = 0;
+        J.status = PGZ_OK;
+        if (!J.gz || (!J.out && J.out_cap)) {
+            J.status = PGZ_E_ARG;
+            continue;
+        }
+        uint64_t s0 = 0;
+        if (J.gz_len < 18 || parse_header(J.gz, J.gz_len, J.gz_len, &s0) != PGZ_OK) {
+            J.status = PGZ_E_HEADER;
+            continue;
+        }
+        const uint8_t* t = J.gz + J.gz_len - 8;
+        mi[k].s0 = s0;
+        mi[k].crc = t[0] | ((uint32_t)t[1] << 8) | ((uint32_t)t[2] << 16) | ((uint32_t)t[3] << 24);
+        mi[k].isize = t[4] | ((uint32_t)t[5] << 8) | ((uint32_t)t[6] << 16) | ((uint32_t)t[7] << 24);
+        in_off[k] = in_total;
+        out_off[k] = out_total;
+        in_total += round_up(J.gz_len, 16);
+        out_total += round_up(J.out_cap, 16);
+        valid[k] = 1;
+    }
+    if (cuda_status(ctx->hb_in.ensure(in_total)) || cuda_status(ctx->hb_out.ensure(out_total))) return PGZ_E_NOMEM;
+    uint8_t* din = ctx->hb_in.as<uint8_t>();
+    uint8_t* dout = ctx->hb_out.as<uint8_t>();
+    // groups: consecutive jobs, about in_total / ng compressed bytes each
+    const int ng = (int)std::max<uint64_t>(1, std::min<uint64_t>({(uint64_t)G, (uint64_t)n, in_total / (96ull << 20)}));
+    std::vector<int> gfirst((size_t)ng + 1, n);
+    {
+        uint64_t acc = 0;
+        int g = 0;
+        gfirst[0] = 0;
+        for (int k = 0; k < n && g + 1 < ng; ++k) {
+            acc += valid[k] ? round_up(jobs[k].gz_len, 16) : 0;
+            if (acc * (uint64_t)ng >= in_total * (uint64_t)(g + 1)) gfirst[++g] = k + 1;
+        }
+        for (int h = g + 1; h <= ng; ++h) gfirst[h] = n;
+    }
+    // every upload at once, one event per group
+    for (int g = 0; g < ng; ++g) {
+        for (int k = gfirst[g]; k < gfirst[g + 1]; ++k)
+            if (valid[k] && cudaMemcpyAsync(din + in_off[k], jobs[k].gz, jobs[k].gz_len, cudaMemcpyHostToDevice,
+                                            ctx->hb_up) != cudaSuccess)
+                return PGZ_E_CUDA;
+        if (cudaEventRecord(ctx->hb_ev_up[g], ctx->hb_up) != cudaSuccess) return PGZ_E_CUDA;
+    }
+    // the groups' runs back to back; each group's output down as its run ends (ISIZE bytes: the length of
+    // a good member below 4 GiB, corrected below when the run says otherwise)
+    int status = PGZ_OK;
+    std::vector<char> started((size_t)ng, 0);
+    for (int g = 0; g < ng; ++g) {
+        Plan& P = ctx->hb_plan[g];
+        begin_plan(P);
+        for (int k = gfirst[g]; k < gfirst[g + 1]; ++k)
+            if (valid[k])
+                plan_member(ctx, P, din + in_off[k], jobs[k].gz_len, dout + out_off[k], jobs[k].out_cap, mi[k], 0);
+        if (P.files.empty()) continue;
+        if (cudaStreamWaitEvent(ctx->stream, ctx->hb_ev_up[g], 0) != cudaSuccess) return PGZ_E_CUDA;
+        const int e = start_run(ctx, P, false);
+        if (e) {
+            status = e;
+            break;
+        }
+        started[g] = 1;
+        if (cudaEventRecord(ctx->hb_ev_run[g], ctx->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(ctx->hb_down, ctx->hb_ev_run[g], 0) != cudaSuccess)
+            return PGZ_E_CUDA;
+        for (int k = gfirst[g]; k < gfirst[g + 1]; ++k) {
+            if (!valid[k]) continue;
+            down[k] = std::min<uint64_t>(jobs[k].out_cap, mi[k].isize);
+            if (down[k] && cudaMemcpyAsync(jobs[k].out, dout + out_off[k], down[k], cudaMemcpyDeviceToHost,
+                                           ctx->hb_down) != cudaSuccess)
+                return PGZ_E_CUDA;
+        }
+    }
+    // results, group by group (recovery re-runs a group and copies its output again)
+    for (int g = 0; g < ng; ++g) {
+        if (!started[g]) continue;
+        Plan& P = ctx->hb_plan[g];
+        uint64_t again = 0;
+        {
+            if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return PGZ_E_CUDA;
+            const FileDesc* hf = P.h_files.as<FileDesc>();
+            for (size_t f = 0; f < P.files.size(); ++f) again |= hf[f].bad_chunk != 0xffffffffu;
+        }
+        const int e = finish_run(ctx, P, nullptr);
+        if (e == PGZ_E_CUDA || e == PGZ_E_NOMEM) return e;
+        const FileDesc* hf = P.h_files.as<FileDesc>();
+        size_t f = 0;
+        for (int k = gfirst[g]; k < gfirst[g + 1]; ++k) {
+            if (!valid[k]) continue;
+            jobs[k].status = (int)hf[f].status;
+            jobs[k].out_len = hf[f].total;
+            if (st) {
+                st->in_bytes += jobs[k].gz_len;
+                st->out_bytes += hf[f].total;
+            }
+            const uint64_t want = jobs[k].status == PGZ_OK ? hf[f].total : 0;
+            if (jobs[k].status == PGZ_OK && (again || want != down[k])) {
+                if (cudaMemcpyAsync(jobs[k].out, dout + out_off[k], want, cudaMemcpyDeviceToHost, ctx->hb_down) !=
+                    cudaSuccess)
+                    return PGZ_E_CUDA;
+            }
+            ++f;
+        }
+        if (st) st->chunks += P.chunks.size();
+    }
+    if (cudaStreamSynchronize(ctx->hb_down) != cudaSuccess) return PGZ_E_CUDA;
+    if (status != PGZ_OK) return status;
+    for (int k = 0; k < n; ++k)
+        if (jobs[k].status != PGZ_OK) return jobs[k].status;
+    return PGZ_OK;
 }
 
 int pgz_batch_prepare(pgz_ctx* ctx, int n, const pgz_job* jobs, pgz_batch** out) {

@@ -104,6 +104,10 @@ struct ChunkDesc {
     uint32_t final;        // the part decoded the member's final block
     uint32_t anyph;        // pass 1 produced at least one placeholder
     uint32_t probe;        // 1: only the block start is searched (the end of a streamed segment); no output
+    uint32_t confirm_ext;  // plan: when the part reaches the next part's start before its confirmation blocks
+                           // are all decoded, it decodes on past that start until they are (output unchanged)
+    uint32_t confirmed;    // result: the start's block and the confirm_blocks blocks after it (or up to a
+                           // final block) decoded with the checks; always 1 for a known start
 };
 
 // host-side launch wrappers (pgz_kernels.cu)
@@ -134,5 +138,20 @@ void launch_sequences(const uint16_t* sym, uint64_t n, uint32_t min_len, uint64_
 void launch_count_ph(ChunkDesc* chunks, int nchunks, const uint16_t* sym, cudaStream_t s);
 int kernels_per_run();
 void upload_crc_tables();
+
+// Recovery after a failed run (pgz_host.cu), shared by every entry point.  For the member F whose parts are
+// plan[F.chunk0 .. F.chunk0 + F.nchunks) with the run's results res[...], it changes the plan for a re-run:
+//  - every searched start whose confirmation failed is searched again from the bit after it (Section
+//    "Detection of DEFLATE block start positions"): the lowest start that passes both the block checks and
+//    the confirmation is the one taken;
+//  - then the first failing part, in order, decides: a part that did not end exactly on the next part's
+//    start shows that start is not on the member's chain of blocks, and that part is merged into its
+//    predecessor (if its confirmation is not settled yet, it first decodes past its stop to settle it);
+//    another decoding error of a searched start merges its part too.
+// Returns kRecoverRerun, kRecoverGrow (*grow = a part that needs more symbol capacity; the caller decides
+// how to give it) or kRecoverStop (the error is final).
+constexpr int kRecoverStop = 0, kRecoverRerun = 1, kRecoverGrow = 2;
+int recover_member(const FileDesc& F, ChunkDesc* plan, const ChunkDesc* res, int confirm_blocks,
+                   uint64_t* false_syncs, int* grow);
 
 }  // namespace pgz

@@ -1585,6 +1585,7 @@ __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
         C.anyph = neg && state == CS_FOUND;
         C.blocks = state == CS_FOUND ? 1u : 0u;
         C.final = final && state == CS_FOUND;
+        C.confirmed = (state == CS_FOUND && (o.known || C.given || final || p.confirm_blocks == 0)) ? 1u : 0u;
         C.end = resume;
     }
     }
@@ -1612,6 +1613,7 @@ __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
             C.anyph = 0;
             C.blocks = 0;
             C.final = 0;
+            C.confirmed = 0;
             C.end = C.sync;
         }
         continue;
@@ -1628,22 +1630,37 @@ __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
         }
     }
     OutState o{symbuf + C.sym_base, C.cap, C.n, C.index == 0 && C.sync == F.s0_bit, false};
-    uint32_t blocks = C.blocks, final = C.final, err = CE_OK;
+    uint32_t blocks = C.blocks, final = C.final, err = CE_OK, confirmed = C.confirmed;
     uint64_t end = C.resume;
+    // the confirmation (Section "Detection of DEFLATE block start positions") covers the start's block and
+    // the confirm_blocks blocks after it; they are decoded with the literal checks
+    const uint32_t window = (uint32_t)p.confirm_blocks + 1u;
     if (final) {
         if (stop != kNone && !F.open_end) err = CE_CHAIN;
-    } else if (!(stop != kNone && C.resume == stop)) {
+    } else if (!(stop != kNone && C.resume == stop) || (C.confirm_ext && !confirmed)) {
         init_smem(S, p, lane);
         BitIn br;
         br.setup(F.gz, F.gz_len);
         br.seek(C.resume);
+        // past the stop (confirm_ext): blocks decoded only to finish the confirmation; the part's own
+        // output, end and status are those at the stop
+        bool past = false;
+        uint32_t err_stop = CE_OK;
+        uint64_t n_stop = 0, end_stop = 0;
         for (;;) {
             const uint64_t pos = br.pos();
-            if (stop != kNone && pos >= stop) {
-                if (pos != stop) err = CE_CHAIN;
-                break;
+            if (!past && stop != kNone && pos >= stop) {
+                err_stop = pos != stop ? (uint32_t)CE_CHAIN : (uint32_t)CE_OK;
+                if (!C.confirm_ext || blocks >= window) {
+                    err = err_stop;
+                    break;
+                }
+                past = true;
+                n_stop = o.n;
+                end_stop = pos;
             }
-            const bool check = !o.known && blocks <= (uint32_t)p.confirm_blocks;
+            if (past && blocks >= window) break;
+            const bool check = !o.known && blocks < window;
             uint32_t fin = 0;
             const int st = one_block<PIPE>(S, tok, br, o, check, 0, 0, false, F.end_bit, fin, lane);
             if (st) {
@@ -1652,12 +1669,22 @@ __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
             }
             ++blocks;
             if (fin) {
+                if (blocks <= window) confirmed = 1;
+                if (past) break;
                 final = 1;
                 if (stop != kNone && !F.open_end) err = CE_CHAIN;   // an open member may end before the next part
                 break;
             }
         }
         end = br.pos();
+        if (blocks >= window && err != CE_CONFIRM) confirmed = 1;
+        if (past) {
+            if (err == CE_OK) err = err_stop;
+            if (err != CE_CONFIRM && err != CE_OVERFLOW) {
+                o.n = n_stop;
+                end = end_stop;
+            }
+        }
     }
     if (err == CE_OK && final && F.mode != 2 && !F.open_end) {   // the trailer must follow the final block
         if (((end + 7) >> 3) + 8 != F.gz_len) err = CE_TRAIL;
@@ -1670,6 +1697,7 @@ __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
         C.anyph = C.anyph | (neg ? 1u : 0u);
         C.blocks = blocks;
         C.final = final;
+        C.confirmed = confirmed;
         C.end = end;
     }
     }
@@ -2390,12 +2418,16 @@ void launch_chain(const FileDesc* files, const ChunkDesc* chunks, int nfiles, in
                   const int32_t* g0, const int32_t* gn, const int32_t* gfile, const uint16_t* sym,
                   uint16_t* gmaps, uint8_t* wstart, uint8_t* windows, cudaStream_t s) {
     if (ngroups <= 0) return;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_chain_compose, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kWin);
-        cudaFuncSetAttribute(k_chain_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kWin);
-        cudaFuncSetAttribute(k_chain_expand, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kWin);
-        attr = true;
+    static bool attr[64] = {};                            // the shared-memory limits are raised per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int slot = dev >= 0 && dev < 64 ? dev : 0;
+    if (!attr[slot]) {
+        attr[slot] =
+            cudaFuncSetAttribute(k_chain_compose, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kWin) ==
+                cudaSuccess &&
+            cudaFuncSetAttribute(k_chain_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kWin) == cudaSuccess &&
+            cudaFuncSetAttribute(k_chain_expand, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kWin) == cudaSuccess;
     }
     k_chain_compose<<<ngroups, 1024, 4 * kWin, s>>>(files, chunks, g0, gn, gfile, sym, gmaps);
     k_chain_walk<<<nfiles, 1024, 2 * kWin, s>>>(files, gmaps, wstart);

@@ -41,7 +41,7 @@ constexpr int kNaMaxParts = 64;
 constexpr int kNaMaxGroups = 8;
 constexpr uint64_t kNaSymbols = 2 * kNaMaxOut;       // u16 symbols shared by the parts
 constexpr uint64_t kNaPartBytes = 32 << 10;          // compressed bytes per part
-constexpr int kNaMaxRetries = 16;
+constexpr int kNaMaxRetries = 32;
 
 constexpr size_t a256(size_t x) { return (x + 255) / 256 * 256; }
 constexpr size_t kOffFiles = 0;
@@ -177,6 +177,7 @@ extern "C" int pgz_decompress_noalloc(const uint8_t* gz, uint64_t gz_len, uint8_
     ChunkDesc plan[kNaMaxParts], res[kNaMaxParts];
     FileDesc F, R;
     bool replan = true;
+    uint64_t false_syncs = 0;
     for (int attempt = 0; attempt <= kNaMaxRetries; ++attempt) {
         if (replan) {                                  // n parts of equal compressed size
             const uint64_t per = (csize + n - 1) / n;
@@ -246,36 +247,18 @@ extern "C" int pgz_decompress_noalloc(const uint8_t* gz, uint64_t gz_len, uint8_
         if (cudaMemcpyAsync(res, d_chunks, n * sizeof(ChunkDesc), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return PGZ_E_CUDA;
-        bool fixed = false;
-        for (uint64_t c = 0; c < n && !fixed; ++c) {
-            const ChunkDesc& X = res[c];
-            if (X.state != CS_ERROR) continue;
-            if (X.err == CE_OVERFLOW) {                 // fewer parts, each with more of the symbol scratch
-                if (n == 1) return PGZ_E_CAPACITY;
-                n = (n + 1) / 2;
-                replan = true;
-                fixed = true;
-            } else if (X.err == CE_TRAIL) {
-                return PGZ_E_UNSUPPORTED;
-            } else if (X.err == CE_CHAIN) {
-                for (uint64_t j = c + 1; j < n; ++j) {
-                    if (res[j].state == CS_EMPTY || plan[j].disabled) continue;
-                    plan[j].disabled = 1;
-                    fixed = true;
-                    break;
-                }
-                if (!fixed) return PGZ_E_DATA;
-            } else if (c == 0) {
-                return (int)R.status;
-            } else if (X.err == CE_CONFIRM && X.sync != kNone) {
-                plan[c].lo = X.sync + 1;
-                fixed = true;
-            } else {
-                plan[c].disabled = 1;
-                fixed = true;
-            }
+        // the same recovery as pgz_decompress, within the fixed scratch: a part that needs more symbol
+        // capacity makes the plan use fewer parts, each with a larger share of the symbol array
+        F.nchunks = (int32_t)n;
+        int grow = -1;
+        const int a = recover_member(F, plan, res, kp.confirm_blocks, &false_syncs, &grow);
+        if (a == kRecoverGrow) {
+            if (n == 1) return PGZ_E_CAPACITY;
+            n = (n + 1) / 2;
+            replan = true;
+        } else if (a != kRecoverRerun) {
+            return (int)R.status;
         }
-        if (!fixed) return (int)R.status;
     }
     return PGZ_E_DATA;
 }

@@ -84,6 +84,7 @@ def _load():
         "pgz_set_tuning": (ctypes.c_int, [VP, U64, ctypes.c_int, ctypes.c_int]),
         "pgz_decompress_at": (ctypes.c_int, [VP, VP, U64, U64, VP, VP, ctypes.c_uint8, U64, P(U64), P(U64), P(U64)]),
         "pgz_decompress_batch": (ctypes.c_int, [VP, ctypes.c_int, P(pgz_job), P(pgz_stats)]),
+        "pgz_decompress_batch_host": (ctypes.c_int, [VP, ctypes.c_int, P(pgz_job), P(pgz_stats)]),
         "pgz_batch_prepare": (ctypes.c_int, [VP, ctypes.c_int, P(pgz_job), P(VP)]),
         "pgz_batch_run": (ctypes.c_int, [VP, P(pgz_job), P(pgz_stats)]),
         "pgz_batch_free": (None, [VP]),
@@ -127,7 +128,7 @@ def lib():
 
 
 EXPORTED = ["pgz_config_init", "pgz_create", "pgz_destroy", "pgz_decompress", "pgz_decompress_host",
-            "pgz_decompress_at", "pgz_decompress_batch", "pgz_batch_prepare", "pgz_batch_run", "pgz_batch_free",
+            "pgz_decompress_at", "pgz_decompress_batch", "pgz_decompress_batch_host", "pgz_batch_prepare", "pgz_batch_run", "pgz_batch_free",
             "pgz_index_build", "pgz_index_info", "pgz_decompress_range", "pgz_index_free", "pgz_inspect_parts",
             "pgz_inspect_symbols", "pgz_inspect_window", "pgz_kernel_launches", "pgz_strerror",
             "pgz_decompress_noalloc", "pgz_autotune", "pgz_server_create", "pgz_server_add_file",
@@ -237,6 +238,15 @@ def pgz_decompress_batch(ctx: int, jobs, stats: bool = False):
     arr = _jobs(jobs)
     st = pgz_stats() if stats else None
     r = lib().pgz_decompress_batch(ctx, len(jobs), arr, ctypes.byref(st) if st is not None else None)
+    return r, [(arr[k].status, arr[k].out_len) for k in range(len(jobs))], (st.as_dict() if st is not None else None)
+
+
+def pgz_decompress_batch_host(ctx: int, jobs, stats: bool = False):
+    """jobs: list of (gz_ptr, gz_len, out_ptr, out_cap) with HOST addresses; returns (status,
+    [(status, out_len)], stats)."""
+    arr = _jobs(jobs)
+    st = pgz_stats() if stats else None
+    r = lib().pgz_decompress_batch_host(ctx, len(jobs), arr, ctypes.byref(st) if st is not None else None)
     return r, [(arr[k].status, arr[k].out_len) for k in range(len(jobs))], (st.as_dict() if st is not None else None)
 
 

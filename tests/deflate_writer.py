@@ -164,7 +164,7 @@ def fixed_lit_lengths():
     return [8] * 144 + [9] * 112 + [7] * 24 + [8] * 8
 
 
-def _emit_tokens(w: BitWriter, tokens, lcodes, llen, dcodes, dlen):
+def _emit_tokens(w: BitWriter, tokens, lcodes, llen, dcodes, dlen, eob: bool = True):
     for t in tokens:
         if t[0] == "lit":
             w.put_code(lcodes[t[1]], llen[t[1]])
@@ -176,7 +176,8 @@ def _emit_tokens(w: BitWriter, tokens, lcodes, llen, dcodes, dlen):
             c, ev, eb = dist_code(d)
             w.put_code(dcodes[c], dlen[c])
             w.put(ev, eb)
-    w.put_code(lcodes[256], llen[256])
+    if eob:
+        w.put_code(lcodes[256], llen[256])
 
 
 def write_fixed(w: BitWriter, tokens, final: bool):
@@ -187,8 +188,10 @@ def write_fixed(w: BitWriter, tokens, final: bool):
     _emit_tokens(w, tokens, canonical(llen), llen, canonical(dlen), dlen)
 
 
-def write_dynamic(w: BitWriter, tokens, final: bool, llen=None, dlen=None, use_rle: bool = True):
-    """A dynamic-Huffman block; code lengths default to Huffman codes of the tokens."""
+def write_dynamic(w: BitWriter, tokens, final: bool, llen=None, dlen=None, use_rle: bool = True,
+                  eob: bool = True):
+    """A dynamic-Huffman block; code lengths default to Huffman codes of the tokens.  eob=False leaves out
+    the end-of-block code, so a decoder reads on into whatever bits follow."""
     lf: dict[int, int] = {256: 1}
     df: dict[int, int] = {}
     for t in tokens:
@@ -221,7 +224,7 @@ def write_dynamic(w: BitWriter, tokens, final: bool, llen=None, dlen=None, use_r
     for s, ev, eb in cl_syms:
         w.put_code(clc[s], cl_len[s])
         w.put(ev, eb)
-    _emit_tokens(w, tokens, canonical(llen), llen, canonical(dlen), dlen)
+    _emit_tokens(w, tokens, canonical(llen), llen, canonical(dlen), dlen, eob)
 
 
 def expand(tokens, prefix: bytes = b"") -> bytes:

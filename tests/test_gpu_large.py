@@ -152,6 +152,29 @@ def test_batch_of_512_members_in_one_graph():
     ctx.close()
 
 
+def _scan_ranges(gz: bytes, nparts: int = 0, chunk_bytes: int = 0):
+    """Scan ranges [lo_i, hi_i) of a member's parts of equal compressed size, as the library plans them:
+    nparts parts, or one per chunk_bytes of compressed data (at most one per 64 bytes)."""
+    s0 = oracle.gzip_header(gz)
+    csize = len(gz) - 8 - s0
+    end = (len(gz) - 8) * 8
+    n = nparts or max(1, -(-csize // chunk_bytes))
+    n = max(1, min(n, max(1, csize // 64)))
+    per = -(-csize // n)
+    return [((s0 + i * per) * 8, min((s0 + (i + 1) * per) * 8, end)) for i in range(n)]
+
+
+def _oracle_start(gz: bytes, lo: int, hi: int) -> int:
+    """The oracle's block start of a part: the lowest bit of [lo, hi) passing the block checks and the
+    five-block confirmation (none: the library's NONE)."""
+    b = oracle.sync_scan(gz, (len(gz) - 8) * 8, lo, hi, oracle.default_allowed(), confirm_blocks=5)
+    return b if b >= 0 else pgz_none()
+
+
+def pgz_none() -> int:
+    return (1 << 64) - 1
+
+
 @pytest.mark.slow
 def test_two_256mib_files_full_size():
     """The benchmark's workload: 2 x 256 MiB FASTQ (150 bp, seed 1) at gzip -1 and -9, batched (graph, 64 KiB
@@ -170,6 +193,19 @@ def test_two_256mib_files_full_size():
     for k, (raw, _) in enumerate(files):
         assert res[k] == (0, len(raw)) and _same_on_device(d_out[k], raw)
     b.free()
+    # the same batch without the graph, for its part starts: sampled parts of each file against the
+    # oracle's own search over the part's scan range (the lowest bit passing the block checks and the
+    # confirmation)
+    r, _, _ = pgz.pgz_decompress_batch(ctx.h, jobs)
+    assert r == 0
+    sb, _, _ = pgz.pgz_inspect_parts(ctx.h)
+    base = 0
+    for raw, gz in files:
+        ranges = _scan_ranges(gz, chunk_bytes=65536)
+        for i in (1, len(ranges) // 2, len(ranges) - 1):
+            assert int(sb[base + i]) == _oracle_start(gz, *ranges[i]), i
+        base += len(ranges)
+    assert base == len(sb)
     ctx.close()
     plain = Ctx(n_chunks=1024)
     try:
@@ -180,7 +216,9 @@ def test_two_256mib_files_full_size():
             assert s["chunks"] == 1024 and s["empty_chunks"] == 0
             sb, ns, nph = pgz.pgz_inspect_parts(plain.h)
             end = (len(gz) - 8) * 8
+            ranges = _scan_ranges(gz, nparts=1024)
             for i in (1, 511, 1023):
+                assert int(sb[i]) == _oracle_start(gz, *ranges[i]), i
                 stop = int(sb[i + 1]) if i + 1 < len(sb) else 0
                 ref = oracle.inflate_from(gz, end, int(sb[i]), stop, known=False, cap=int(ns[i]) + 4096)
                 assert ref["status"] == 0

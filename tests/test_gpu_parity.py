@@ -299,6 +299,46 @@ def test_host_entry_point(cfg1):
         ctx.close()
 
 
+def test_host_batch_entry_point():
+    """pgz_decompress_batch_host: members in host memory (page-locked and pageable), cut into groups whose
+    copies overlap the decoding.  Four 64 MiB members of Markov text make the batch span more than one
+    group; a member with a hidden false block start needs recovery inside its group; a member with a wrong
+    trailer CRC fails alone.  Every other output is exact."""
+    import torch
+    import confirm_streams as cs
+    m = cs.find("invalid", 2)
+    raws = [synth.markov(64 << 20, 30 + k) for k in range(4)] + [synth.fastq(3 << 20, 150, 0.001, 34), m.data]
+    gzs = [synth.gzip_compress(r, 1) for r in raws[:5]] + [m.gz]
+    bad = bytearray(synth.gzip_compress(raws[4], 6))
+    bad[-8] ^= 1
+    raws.insert(2, raws[4])
+    gzs.insert(2, bytes(bad))
+    ctx = Ctx(n_chunks=0, chunk_bytes=64 << 10)
+    try:
+        P = ctx.pgz
+        for pinned in (True, False):
+            ins = [torch.from_numpy(np.frombuffer(g, dtype=np.uint8).copy()) for g in gzs]
+            outs = [torch.zeros(len(r) + 4096, dtype=torch.uint8) for r in raws]
+            if pinned:
+                ins = [t.pin_memory() for t in ins]
+                outs = [t.pin_memory() for t in outs]
+            jobs = [(ins[k].data_ptr(), len(gzs[k]), outs[k].data_ptr(), outs[k].numel()) for k in range(len(gzs))]
+            for _ in range(2):
+                for o in outs:
+                    o.zero_()
+                st, res, s = P.pgz_decompress_batch_host(ctx.h, jobs, stats=True)
+                assert st == P.PGZ_E_CRC
+                for k, raw in enumerate(raws):
+                    if k == 2:
+                        assert res[k][0] == P.PGZ_E_CRC
+                        continue
+                    assert res[k] == (0, len(raw)), (k, P.pgz_strerror(res[k][0]))
+                    assert outs[k][:len(raw)].numpy().tobytes() == raw, k
+                assert s["out_bytes"] >= sum(len(r) for k, r in enumerate(raws) if k != 2)
+    finally:
+        ctx.close()
+
+
 def test_multi_member_files():
     """RFC 1952 2.2: a gzip file is a series of members; the output is their concatenation (the oracle decodes
     every member)."""
@@ -396,6 +436,9 @@ def test_false_block_start_is_caught_by_the_chain_check():
             assert st == 0, ctx.pgz.pgz_strerror(st)
             assert out == data
             assert s["false_syncs"] >= 1 and s["retries"] >= 1
+            assert s["false_syncs"] == ref["false_syncs"]
+            sb, _, _ = ctx.pgz.pgz_inspect_parts(ctx.h)
+            assert np.array_equal(sb, ref["part_bits"].astype(np.uint64))
         finally:
             ctx.close()
 
