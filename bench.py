@@ -1,27 +1,35 @@
 #!/usr/bin/env python3
 """Benchmark of the GB300 two-pass parallel gzip decompression (libpgz).
 
-Default workload (one GPU): two 256 MiB synthetic FASTQ files (150 bp reads,
-seed 1), gzip level 1 and level 9 via host zlib.  One step decompresses both
-files (block-start search, pass 1, window chain, translation, CRC-32/ISIZE
-check) with inputs and outputs resident in device memory, in two forms:
+Default workload (one GPU): 512 independent synthetic gzip members (seed 3)
+with log-uniform uncompressed sizes 64 KiB .. 64 MiB, half FASTQ (150 bp
+reads) and half order-2 Markov text, gzip levels 1/6/9 (host zlib); about
+2.9 GB compressed and 4.5 GB decompressed.  One step decompresses all of them
+(block-start search, pass 1, window chain, translation, CRC-32/ISIZE check)
+with inputs and outputs resident in device memory, in two forms:
 
-  batched (the reported value): both files in one run of the pass kernels,
+  batched (the reported value): every member in one run of the pass kernels,
       parts taken from a device work queue, captured once in a CUDA graph
-      (pgz_batch_prepare / pgz_batch_run); part size and pass-1 CTA shape
-      are chosen by the library's autotuner (pgz_autotune) on the same files
-      unless --chunk-bytes fixes the size;
-  plain: one file at a time through pgz_decompress with 1024 equal parts per
-      file, with sync-failure and placeholder statistics per level.
+      (pgz_batch_prepare / pgz_batch_run); part size, pass-1 CTA shape and
+      execution form chosen by the library's autotuner (pgz_autotune) on the
+      same members unless --chunk-bytes fixes them;
+  plain: one pgz_decompress call per member (the library's default parts).
+
+e2e times the same members through pgz_decompress_batch_host: pinned host
+input and output, the copies inside the call.  Extra keys of the same line:
+the two 256 MiB FASTQ files at gzip -1 and -9 (batched and plain, per-level
+block-start and placeholder statistics) and the served request loop (p50 and
+p99 latency at offered loads of 1, 4 and 16 GB/s, a reduced request count).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pgz|reference]
-                  [--workload fastq256|fastq1m|fastq4g|batch512|served] [--chunk-bytes B]
-                  [--profile-case MIB:LEVEL:CALLS]
+                  [--workload batch512|fastq256|fastq1m|fastq4g|served|stream]
+                  [--chunk-bytes B] [--served-requests R] [--profile-case SPEC]
 
 Prints one JSON line.  --impl reference times the CPU oracle (the plain
-bit-at-a-time RFC 1951 inflater under oracle/) on the same files.  Under
-torchrun every rank decodes its own copy of the workload (independent files,
-no collective: weak scaling) and rank 0 prints the whole-job throughput.
+bit-at-a-time RFC 1951 inflater under oracle/), member-parallel on the host's
+cores, on the same members.  Under torchrun every rank decodes its own copy of
+the workload (independent members, no collective: weak scaling) and rank 0
+prints the whole-job throughput.
 """
 from __future__ import annotations
 
@@ -42,10 +50,17 @@ CHUNK_BYTES = 64 << 10        # compressed bytes per part when the autotuner is 
 TUNE_CHUNKS = [32 << 10, 64 << 10, 128 << 10, 256 << 10, 512 << 10]   # the autotuner's part sizes ...
 TUNE_WPB = [2, 4, 8]                                                # ... and pass-1 CTA shapes (warps)
 PLAIN_PARTS = 1024            # parts per file of the plain one-file-at-a-time form
-METRIC = "decompressed GB/s on 1 GB300 (batched vs plain), %HBM roofline"
+METRIC = "decompressed GB/s on 1 GB300 (batched vs plain), %HBM roofline; served p50/p99 ms"
+HEADLINE_DESC = ("512 synthetic gzip members, log-uniform 64 KiB-64 MiB (seed 3), FASTQ 150 bp / order-2 Markov "
+                 "text, gzip -1/-6/-9")
+TUNE_CHUNKS_BATCH = [64 << 10, 128 << 10, 256 << 10, 512 << 10]   # the autotuner's part sizes on the 512 members
+TUNE_WPB_BATCH = [2, 4]
+SERVED_REQUESTS = 240         # requests per offered load in the default run (the full served run uses 2000)
 # DRAM bytes (read + write) of pass 1 (k_sync + k_inflate) per decompressed byte on this workload's batched
 # run, by (part size, warps per block, pipelined execution): ncu captures of the configurations the autotuner
 # picks here (profiles/pass1_traffic_fastq256_batched.md).  A configuration without a capture reports null.
+# The same for the 512-member batch, by the configuration the autotuner picks there (empty: no capture yet).
+PASS1_TRAFFIC_PER_OUT_BYTE_BATCH512 = {}
 PASS1_TRAFFIC_PER_OUT_BYTE = {
     (65536, 2, 0): 5.0866e9 / 536870912,
     (65536, 2, 1): 5.0049e9 / 536870912,
@@ -402,6 +417,144 @@ def run_pgz(args, rank, world):
     return line
 
 
+def timed_steps(step, steps: int, warmup: int, stream, dist: bool = False, mark=None):
+    """W untimed steps, then K steps between barriers and synchronisations, timed by CUDA events on the
+    launching stream: one event before the first step and one after each step.  Returns the mean ms per step
+    over the K steps and the list of per-step times.  mark(0) / mark(1), if given, run just before and just
+    after the timed steps."""
+    import torch
+    for _ in range(warmup):
+        step()
+    if dist:
+        import torch.distributed as tdist
+        tdist.barrier()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    if mark:
+        mark(0)
+    ev[0].record(stream)
+    for k in range(steps):
+        step()
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    if mark:
+        mark(1)
+    if dist:
+        import torch.distributed as tdist
+        tdist.barrier()
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    return ev[0].elapsed_time(ev[steps]) / steps, per
+
+
+def stage_means(pgz, ctx, jobs, reps: int = 3):
+    """Per-stage CUDA-event times of one run of the pass kernels over `jobs` (pgz_decompress_batch, the same
+    launches as the captured graph), mean of reps runs, and the run's part count."""
+    stage = {k: 0.0 for k in ("ms_sync", "ms_inflate", "ms_chain", "ms_translate", "ms_crc", "ms_total")}
+    s = None
+    for _ in range(reps):
+        r, _, s = pgz.pgz_decompress_batch(ctx, jobs, stats=True)
+        if r != 0:
+            raise RuntimeError(f"pgz_decompress_batch failed: {pgz.pgz_strerror(r)}")
+        for k in stage:
+            stage[k] += s[k] / reps
+    return stage, s["chunks"]
+
+
+def rooflines(stage, total_in, total_out, window_bytes, hbm, traffic_per_out_byte=None):
+    """The pass-1 pair against HBM (its algorithmic bytes: compressed input read + u16 symbols written), and
+    the two HBM-bound stages: translation (u16 symbols and windows read, bytes written) and CRC (bytes read)."""
+    pass1_ms = stage["ms_sync"] + stage["ms_inflate"]
+    alg1 = total_in + 2 * total_out
+    ach1 = alg1 / (pass1_ms * 1e-3) / 1e9
+    alg4 = 3 * total_out + window_bytes
+    ach4 = alg4 / (stage["ms_translate"] * 1e-3) / 1e9 if stage["ms_translate"] > 0 else None
+    ach5 = total_out / (stage["ms_crc"] * 1e-3) / 1e9 if stage["ms_crc"] > 0 else None
+    traffic = round(traffic_per_out_byte * total_out) if traffic_per_out_byte else None
+    return ({"bound": "hbm", "kernel": "pass 1 (k_sync + k_inflate)", "achieved": round(ach1, 2), "peak": hbm,
+             "unit": "GB/s", "frac": round(ach1 / hbm, 5), "traffic": traffic, "algorithmic_bytes": alg1,
+             "ms": round(pass1_ms, 3)},
+            {"bound": "hbm", "kernel": "k_translate", "achieved": round(ach4, 1) if ach4 else None, "peak": hbm,
+             "unit": "GB/s", "frac": round(ach4 / hbm, 4) if ach4 else None, "bytes": alg4,
+             "window_bytes": window_bytes},
+            {"bound": "hbm", "kernel": "k_crc", "achieved": round(ach5, 1) if ach5 else None, "peak": hbm,
+             "unit": "GB/s", "frac": round(ach5 / hbm, 4) if ach5 else None, "bytes": total_out})
+
+
+def config2_legs(pgz, files, dev, stream, steps: int, warmup: int, hbm: float):
+    """The two 256 MiB FASTQ files (150 bp, seed 1) at gzip -1 and -9: batched (autotuned, graph) and plain
+    (one pgz_decompress per file, 1024 equal parts), per-level block-start and placeholder statistics."""
+    import numpy as np
+    import torch
+    labels = ["fastq-L1", "fastq-L9"]
+    gz_dev = [torch.from_numpy(np.frombuffer(g, dtype=np.uint8).copy()).cuda() for _, g in files]
+    outs = [torch.empty(len(r) + 4096, dtype=torch.uint8, device="cuda") for r, _ in files]
+    refs = [torch.from_numpy(np.frombuffer(r, dtype=np.uint8).copy()).cuda() for r, _ in files]
+    jobs = [(gz_dev[k].data_ptr(), len(g), outs[k].data_ptr(), outs[k].numel()) for k, (_, g) in enumerate(files)]
+    total_out = sum(len(r) for r, _ in files)
+    total_in = sum(len(g) for _, g in files)
+
+    def check(what):
+        torch.cuda.synchronize()
+        for k, (r, _) in enumerate(files):
+            if not torch.equal(outs[k][:len(r)], refs[k]):
+                raise RuntimeError(f"output mismatch ({what}, {labels[k]})")
+            outs[k].zero_()
+
+    ctx = pgz.pgz_create(pgz.pgz_config_init(device=dev, cuda_stream=stream.cuda_stream))
+    tune = autotune(pgz, ctx, jobs, TUNE_CHUNKS, TUNE_WPB)
+    chunk, wpb, xp = tune["best"]
+    batch = pgz.Batch(ctx, jobs)
+
+    def step_batched():
+        r, res, _ = batch.run()
+        if r != 0:
+            raise RuntimeError(f"pgz_batch_run failed: {pgz.pgz_strerror(r)}")
+
+    step_batched()
+    check("batched")
+    ms_b, per_b = timed_steps(step_batched, steps, warmup, stream)
+    stage, parts = stage_means(pgz, ctx, jobs)
+    _, _, nph_parts = pgz.pgz_inspect_parts(ctx)
+    window_bytes = int((nph_parts > 0).sum()) * 32768
+    batch.free()
+    pgz.pgz_destroy(ctx)
+    ctx_p = pgz.pgz_create(pgz.pgz_config_init(device=dev, cuda_stream=stream.cuda_stream, n_chunks=PLAIN_PARTS,
+                                               warps_per_block=wpb, exec_pipelined=xp))
+
+    def step_plain(stats=False):
+        res = []
+        for k, (r, _) in enumerate(files):
+            st, n, s = pgz.pgz_decompress(ctx_p, *jobs[k], stats)
+            if st != 0 or n != len(r):
+                raise RuntimeError(f"pgz_decompress failed: {pgz.pgz_strerror(st)}")
+            res.append(s)
+        return res
+
+    step_plain()
+    check("plain")
+    ms_p, _ = timed_steps(step_plain, steps, warmup, stream)
+    per_level = {}
+    for label, (r, g), s in zip(labels, files, step_plain(stats=True)):
+        per_level[label] = {"parts": s["chunks"], "empty_parts": s["empty_chunks"], "false_syncs": s["false_syncs"],
+                            "retries": s["retries"],
+                            "placeholder_fraction": round(s["placeholders"] / max(1, s["symbols"]), 4),
+                            "in_bytes": len(g), "ms": round(s["ms_total"], 3)}
+    pgz.pgz_destroy(ctx_p)
+    r1, r4, r5 = rooflines(stage, total_in, total_out, window_bytes, hbm,
+                           PASS1_TRAFFIC_PER_OUT_BYTE.get((chunk, wpb, xp)))
+    return {"workload": "2 x 256 MiB synthetic FASTQ (150 bp, seed 1), gzip -1 and -9",
+            "out_bytes_per_step": total_out, "in_bytes_per_step": total_in,
+            "batched": {"value": round(total_out / (ms_b * 1e-3) / 1e9, 3), "unit": "GB/s", "ms_per_step": round(ms_b, 3),
+                        "step_ms": {"median": round(statistics.median(per_b), 3), "min": round(min(per_b), 3),
+                                    "max": round(max(per_b), 3)},
+                        "chunk_bytes": chunk, "warps_per_block": wpb, "exec_pipelined": xp, "parts": parts},
+            "plain": {"value": round(total_out / (ms_p * 1e-3) / 1e9, 3), "unit": "GB/s", "ms_per_step": round(ms_p, 3),
+                      "parts_per_file": PLAIN_PARTS, "form": "one file at a time through pgz_decompress",
+                      "per_level": per_level},
+            "stages_ms": {k: round(v, 3) for k, v in stage.items()},
+            "roofline_pass1": r1, "roofline_translate": r4, "roofline_crc": r5, "autotune": tune}
+
+
 def _stage_line(stage, total_in, total_out, window_bytes, hbm):
     stage = {k: v for k, v in stage.items() if k.startswith("ms_")}
     t = stage["ms_translate"] * 1e-3
@@ -470,51 +623,47 @@ def run_tune4g(args):
     return line
 
 
-def run_batch512(args):
-    """512 members, log-uniform 64 KiB .. 64 MiB (seed 3), FASTQ and Markov text, levels 1/6/9: one
-    graph-captured batched run against one pgz_decompress call per member."""
+def run_headline(args, rank, world):
+    """The 512 members: batched (autotuned, one graph-captured run) against plain (one pgz_decompress per
+    member); e2e through pgz_decompress_batch_host; on rank 0 also the config-2 files, the served loop and the
+    oracle on the host's cores."""
     import numpy as np
     import torch
     from paper_1905_07224_gb300 import build, pgz, synth
     build.build()
-    torch.cuda.set_device(0)
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    dist = world > 1
+    extras = rank == 0 and not args.headline_only
     t0 = time.perf_counter()
-    files = synth.make_files(synth.batch_manifest(512, 3))
+    man4 = synth.batch_manifest(512, 3)
+    man2 = [("fastq", 256 << 20, 1, 1), ("fastq", 256 << 20, 9, 1)] if extras else []
+    man5, rng5 = served_manifest() if extras and args.served_requests > 0 else ([], None)
+    allf = synth.make_files(man4 + man2 + man5)
+    files, files2, files5 = allf[:512], allf[512:512 + len(man2)], allf[512 + len(man2):]
     t_make = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
     total_out = sum(len(r) for r, _ in files)
     total_in = sum(len(g) for _, g in files)
     d_in = [torch.from_numpy(np.frombuffer(g, dtype=np.uint8).copy()).cuda() for _, g in files]
     d_out = [torch.empty(len(r) + 4096, dtype=torch.uint8, device="cuda") for r, _ in files]
+    refs = [torch.from_numpy(np.frombuffer(r, dtype=np.uint8).copy()).cuda() for r, _ in files]
     jobs = [(d_in[k].data_ptr(), len(g), d_out[k].data_ptr(), d_out[k].numel()) for k, (_, g) in enumerate(files)]
 
-    def timed(step):
-        for _ in range(args.warmup):
-            step()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    def check(what):
         torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(args.steps):
-            step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / args.steps
-
-    def check():
-        torch.cuda.synchronize()
-        for k, (raw, _) in enumerate(files):
-            ref = torch.from_numpy(np.frombuffer(raw, dtype=np.uint8).copy()).cuda()
-            if not torch.equal(d_out[k][:len(raw)], ref):
-                raise RuntimeError(f"output mismatch (member {k})")
+        for k, (r, _) in enumerate(files):
+            if not torch.equal(d_out[k][:len(r)], refs[k]):
+                raise RuntimeError(f"output mismatch ({what}, member {k})")
             d_out[k].zero_()
 
-    ctx = pgz.pgz_create(pgz.pgz_config_init(device=0, cuda_stream=stream.cuda_stream,
-                                             chunk_bytes=args.chunk_bytes or CHUNK_BYTES,
+    # ---- batched: every member in one graph-captured run, the configuration chosen by the autotuner
+    ctx = pgz.pgz_create(pgz.pgz_config_init(device=dev, cuda_stream=stream.cuda_stream,
+                                             chunk_bytes=args.chunk_bytes or (256 << 10),
                                              warps_per_block=args.warps_per_block,
                                              exec_pipelined=args.exec_pipelined))
-    tune = None
-    if not args.chunk_bytes:
-        tune = autotune(pgz, ctx, jobs, [64 << 10, 128 << 10, 256 << 10], [2, 4])
+    tune = None if args.chunk_bytes else autotune(pgz, ctx, jobs, TUNE_CHUNKS_BATCH, TUNE_WPB_BATCH)
+    chunk, wpb, xp = tune["best"] if tune else (args.chunk_bytes, args.warps_per_block, args.exec_pipelined)
     batch = pgz.Batch(ctx, jobs)
 
     def step_batched():
@@ -523,36 +672,120 @@ def run_batch512(args):
             raise RuntimeError(f"pgz_batch_run failed: {pgz.pgz_strerror(r)}")
 
     step_batched()
-    check()
-    ms_b = timed(step_batched)
-    r, _, s = pgz.pgz_decompress_batch(ctx, jobs, stats=True)
+    check("batched")
+    count = [0, 0]
+
+    def mark(k):
+        count[k] = pgz.pgz_kernel_launches(ctx)
+
+    with Clocks(dev) as clk:
+        ms, per = timed_steps(step_batched, args.steps, args.warmup, stream, dist, mark)
+    clocks = clk.summary()
+    launches = count[1] - count[0]
+    # the same steps with no clock sampler running (a check that sampling does not disturb the timed region)
+    ms_quiet, per_quiet = timed_steps(step_batched, args.steps, 1, stream, dist)
+    stage, parts = stage_means(pgz, ctx, jobs)
+    _, _, nph_parts = pgz.pgz_inspect_parts(ctx)
+    window_bytes = int((nph_parts > 0).sum()) * 32768
     batch.free()
 
-    # plain: one call per member on a context of its own at the library's default part size, which suits
-    # one member at a time better than the batch's tuned (larger) parts
-    ctx_p = pgz.pgz_create(pgz.pgz_config_init(device=0, cuda_stream=stream.cuda_stream,
-                                               chunk_bytes=CHUNK_BYTES))
+    # ---- plain: one pgz_decompress per member, the library's default part size
+    ctx_p = pgz.pgz_create(pgz.pgz_config_init(device=dev, cuda_stream=stream.cuda_stream, chunk_bytes=CHUNK_BYTES))
 
     def step_plain():
-        for k, (gp, gl, op, oc) in enumerate(jobs):
+        for gp, gl, op, oc in jobs:
             st, n, _ = pgz.pgz_decompress(ctx_p, gp, gl, op, oc)
             if st != 0:
                 raise RuntimeError(f"pgz_decompress failed: {pgz.pgz_strerror(st)}")
 
     step_plain()
-    check()
-    ms_p = timed(step_plain)
+    check("plain")
+    steps_plain = max(1, min(args.steps, 3))
+    ms_plain, _ = timed_steps(step_plain, steps_plain, 1, stream, dist)
     pgz.pgz_destroy(ctx_p)
+
+    # ---- end to end: pinned host memory in and out, through the C ABI's host-buffer batch call
+    pin_in = [torch.from_numpy(np.frombuffer(g, dtype=np.uint8).copy()).pin_memory() for _, g in files]
+    pin_out = [torch.zeros(len(r) + 4096, dtype=torch.uint8).pin_memory() for r, _ in files]
+    hjobs = [(pin_in[k].data_ptr(), len(g), pin_out[k].data_ptr(), pin_out[k].numel()) for k, (_, g) in enumerate(files)]
+
+    def e2e_step():
+        r, res, _ = pgz.pgz_decompress_batch_host(ctx, hjobs)
+        if r != 0:
+            raise RuntimeError(f"pgz_decompress_batch_host failed: {pgz.pgz_strerror(r)}")
+
+    e2e_step()
+    for k, (r, _) in enumerate(files):
+        if pin_out[k][:len(r)].numpy().tobytes() != r:
+            raise RuntimeError(f"e2e output mismatch (member {k})")
+    e2e = []
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        e2e_step()
+        if k >= args.warmup:
+            e2e.append((time.perf_counter() - t) * 1e3)
+    e2e_ms = statistics.median(e2e)
     pgz.pgz_destroy(ctx)
-    cpu, zl = cpu_baseline_parallel(files)
-    return {"workload": "512 synthetic members, log-uniform 64 KiB-64 MiB (seed 3), FASTQ/Markov, gzip -1/-6/-9",
-            "in_bytes": total_in, "out_bytes": total_out, "make_s": round(t_make, 1), "parts": s["chunks"],
-            "batched": {"value": round(total_out / (ms_b * 1e-3) / 1e9, 3), "ms_per_step": round(ms_b, 3),
-                        "form": "one graph-captured run, device work queue"},
-            "plain": {"value": round(total_out / (ms_p * 1e-3) / 1e9, 3), "ms_per_step": round(ms_p, 3),
-                      "form": "one pgz_decompress per member", "chunk_bytes": CHUNK_BYTES},
-            "unit": "GB/s", "stages_ms_batched": {k: round(v, 3) for k, v in s.items() if k.startswith("ms_")},
-            "autotune": tune, "cpu_baseline": cpu, "zlib_context": zl}
+    del pin_in, pin_out
+    if dist:
+        ms, ms_plain, e2e_ms = max_over_ranks([ms, ms_plain, e2e_ms], "cuda")
+
+    pk = _peaks()
+    hbm = pk.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    r1, r4, r5 = rooflines(stage, total_in, total_out, window_bytes, hbm,
+                           PASS1_TRAFFIC_PER_OUT_BYTE_BATCH512.get((chunk, wpb, xp)))
+    r1["peak_source"] = peak_src
+    gbs = whole_job_gbs(total_out, world, ms)
+    plain_gbs = whole_job_gbs(total_out, world, ms_plain)
+    line = {
+        "metric": METRIC,
+        "value": round(gbs, 3),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic",
+        "gpu_launches": int(launches),
+        "config": {"workload": HEADLINE_DESC, "members": len(files),
+                   "form": "batched: every member in one graph-captured run of the pass kernels",
+                   "out_bytes_per_step": total_out, "in_bytes_per_step": total_in, "chunk_bytes": chunk,
+                   "warps_per_block": wpb, "exec_pipelined": xp, "parts": parts,
+                   "l2": "inputs (%.1f GB) and outputs (%.1f GB) larger than L2" % (total_in / 1e9, total_out / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "compressed_MBps": round(world * total_in / (ms * 1e-3) / 1e6, 1),
+        "step_ms": {"median": round(statistics.median(per), 3), "min": round(min(per), 3), "max": round(max(per), 3),
+                    "without_clock_sampler": round(ms_quiet, 3)},
+        "plain": {"value": round(plain_gbs, 3), "unit": "GB/s", "ms_per_step": round(ms_plain, 3),
+                  "steps": steps_plain, "form": "one pgz_decompress per member", "chunk_bytes": CHUNK_BYTES},
+        "batched_over_plain": round(gbs / plain_gbs, 2),
+        "stages_ms": {k: round(v, 3) for k, v in stage.items()},
+        "roofline": r1, "roofline_translate": r4, "roofline_crc": r5,
+        "e2e": {"value": round(whole_job_gbs(total_out, world, e2e_ms), 3), "unit": "GB/s",
+                "h2d_bytes_per_step": total_in, "d2h_bytes_per_step": total_out,
+                "ms_per_step_median": round(e2e_ms, 3), "ms_per_step_min": round(min(e2e), 3),
+                "path": "pgz_decompress_batch_host (C ABI): pinned host input and output, the host-device copies "
+                        "inside the call, overlapped with decoding group by group; host clock around each call"},
+        "clocks": clocks,
+        "autotune": tune,
+        "make_s": round(t_make, 1),
+    }
+    if extras:
+        if files2:
+            line["fastq256"] = config2_legs(pgz, files2, dev, stream, args.steps, args.warmup, hbm)
+        if files5:
+            line["served"] = served_legs(pgz, files5, rng5, args.served_requests, CHUNK_BYTES, dev)
+        cpu, zl = cpu_baseline_parallel(files)
+        line["cpu_baseline"] = cpu
+        line["zlib_context"] = zl
+    return line
 
 
 def run_stream(args):
@@ -642,29 +875,29 @@ def run_stream(args):
             "timing": "host clock around each synchronous call, median of the steps after the warm-up"}
 
 
-def run_served(args):
-    """Served requests: a pool of 256 members, log-uniform 4 KiB .. 256 MiB (seed 4), half FASTQ and half
-    Markov text, levels 1/6/9; Poisson arrivals at offered loads of 1, 4 and 16 GB/s decompressed; 70 % whole
-    members and 30 % byte ranges (offset uniform, length log-uniform 4 KiB .. 1 MiB, clipped); 2000 requests per
-    load under a 64 GiB device-memory budget.  Latency: arrival to completion seen by the host."""
+def served_manifest():
+    """The served pool: 256 members, log-uniform 4 KiB .. 256 MiB (seed 4), half FASTQ and half Markov text,
+    levels 1/6/9.  Returns the manifest and the generator, which goes on to draw the requests."""
     import numpy as np
-    import torch
-    from paper_1905_07224_gb300 import build, pgz, synth
-    build.build()
-    torch.cuda.set_device(0)
+    from paper_1905_07224_gb300 import synth
     rng = np.random.default_rng(4)
     sizes = synth.log_uniform_sizes(256, 4 << 10, 256 << 20, rng)
     levels = rng.choice(np.array([1, 6, 9]), size=256)
     entries = [("fastq" if k % 2 == 0 else "markov", int(sizes[k]), int(levels[k]), 400003 + k) for k in range(256)]
-    t0 = time.perf_counter()
-    files = synth.make_files(entries)
-    t_make = time.perf_counter() - t0
+    return entries, rng
+
+
+def served_legs(pgz, files, rng, n_req: int, chunk_bytes: int, dev: int = 0):
+    """Poisson arrivals at offered loads of 1, 4 and 16 GB/s decompressed (rate = load / mean member size);
+    70 % whole members and 30 % byte ranges (offset uniform, length log-uniform 4 KiB .. 1 MiB, clipped);
+    n_req requests per load, 4 slots, a 64 GiB device-memory budget.  Latency runs from the scheduled arrival
+    to the completion seen by the host; 40 results per load are checked byte for byte."""
+    import numpy as np
+    import torch
     mean_d = float(np.mean([len(r) for r, _ in files]))
-    srv = pgz.Server(pgz.pgz_config_init(device=0, chunk_bytes=args.chunk_bytes or CHUNK_BYTES), slots=4,
-                     mem_budget=64 << 30)
+    srv = pgz.Server(pgz.pgz_config_init(device=dev, chunk_bytes=chunk_bytes), slots=4, mem_budget=64 << 30)
     d_in = [torch.from_numpy(np.frombuffer(g, dtype=np.uint8).copy()).cuda() for _, g in files]
     ids = [srv.add_file(d.data_ptr(), len(g)) for d, (_, g) in zip(d_in, files)]
-    n_req = int(os.environ.get("PGZ_SERVED_REQUESTS", "2000"))
     results = []
     for load in (1e9, 4e9, 16e9):
         lam = load / mean_d
@@ -704,9 +937,26 @@ def run_served(args):
                         "span_s": round(end - start, 3)})
         del outs
     srv.close()
-    return {"workload": "served: 256 synthetic members, log-uniform 4 KiB-256 MiB (seed 4), FASTQ/Markov, gzip -1/-6/-9; "
-                        "Poisson arrivals, 70 % whole / 30 % ranges, 64 GiB budget, 4 slots",
-            "make_s": round(t_make, 1), "mean_member_bytes": round(mean_d), "loads": results}
+    return {"workload": "served: 256 synthetic members, log-uniform 4 KiB-256 MiB (seed 4), FASTQ/Markov, "
+                        "gzip -1/-6/-9; Poisson arrivals, 70 % whole / 30 % ranges, 64 GiB budget, 4 slots",
+            "mean_member_bytes": round(mean_d), "chunk_bytes": chunk_bytes,
+            "latency": "scheduled arrival to completion seen by the host", "loads": results}
+
+
+def run_served(args):
+    """Served requests at the full request count (2000 per load unless PGZ_SERVED_REQUESTS says otherwise)."""
+    import torch
+    from paper_1905_07224_gb300 import build, pgz, synth
+    build.build()
+    torch.cuda.set_device(0)
+    entries, rng = served_manifest()
+    t0 = time.perf_counter()
+    files = synth.make_files(entries)
+    t_make = time.perf_counter() - t0
+    n_req = int(os.environ.get("PGZ_SERVED_REQUESTS", "2000"))
+    out = served_legs(pgz, files, rng, n_req, args.chunk_bytes or CHUNK_BYTES)
+    out["make_s"] = round(t_make, 1)
+    return out
 
 
 def cpu_baseline(files, budget_s: float = 20.0):
@@ -781,6 +1031,55 @@ def cpu_baseline_parallel(members, target_s: float = 10.0):
              "sample": f"oracle.gunzip, one member per thread on {cores} threads, over {desc}, {t_or:.1f} s"},
             {"value": round(done / t_z / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "host zlib (context)",
              "sample": f"zlib.decompress, one thread, over {desc}, {t_z:.1f} s"})
+
+
+def run_reference_batch512(args, budget_s: float = 150.0, oracle_gbs_per_core: float = 0.06):
+    """--impl reference on the 512 members: the CPU oracle, as it stands (oracle.gunzip, trailer checked), one
+    member per thread on every host core.  A step decodes the first members of the manifest up to about
+    budget_s / (W + K) seconds of the oracle's work at oracle_gbs_per_core GB/s per core (all 512 when they
+    fit), so the whole run ends within a few minutes."""
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle
+    from paper_1905_07224_gb300 import synth
+    oracle.build()
+    t0 = time.perf_counter()
+    files = synth.make_files(synth.batch_manifest(512, 3))
+    t_make = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0))
+    want = budget_s / (args.warmup + args.steps) * oracle_gbs_per_core * 1e9 * cores
+    sample, out = [], 0
+    for raw, gz in files:
+        if sample and out + len(raw) > want:
+            break
+        sample.append((raw, gz))
+        out += len(raw)
+
+    def one(m):
+        raw, gz = m
+        e, o, _, _ = oracle.gunzip(gz, cap=len(raw) + 1024)    # the C oracle releases the GIL
+        if e != 0 or len(o) != len(raw):
+            raise RuntimeError("oracle failed")
+        return len(raw)
+
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        def step():
+            return sum(ex.map(one, sorted(sample, key=lambda m: -len(m[0]))))
+        for _ in range(args.warmup):
+            step()
+        t0 = time.perf_counter()
+        done = sum(step() for _ in range(args.steps))
+        dt = time.perf_counter() - t0
+    v = done / dt / 1e9
+    what = "all 512 members" if len(sample) == len(files) else f"the first {len(sample)} of the 512 members"
+    desc = f"oracle.gunzip, one member per thread on {cores} threads, {what} ({out >> 20} MiB out) per step"
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GB/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": HEADLINE_DESC, "members": len(files),
+                       "out_bytes_per_step": out, "sample_members": len(sample)},
+            "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "make_s": round(t_make, 1)}
 
 
 def run_reference(args, budget_s: float = 150.0, oracle_gbs: float = 0.06):
@@ -932,16 +1231,21 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pgz", choices=["pgz", "reference"])
-    ap.add_argument("--workload", default="fastq256",
-                    choices=["fastq256", "fastq1m", "fastq4g", "batch512", "served", "stream"],
-                    help="fastq256: the benchmark; fastq4g: autotuner sweep on 4 GiB; batch512: 512 members; "
-                         "served: request loop at three offered loads; stream: the 4 GiB member streamed from host "
-                         "memory in 256 MiB segments")
+    ap.add_argument("--workload", default="batch512",
+                    choices=["batch512", "fastq256", "fastq1m", "fastq4g", "served", "stream"],
+                    help="batch512: the benchmark (512 members, batched vs plain, with the fastq256 files and the "
+                         "served loop as extra keys); fastq256: the two 256 MiB FASTQ files alone; fastq4g: "
+                         "autotuner sweep on 4 GiB; served: the request loop at the full request count; stream: "
+                         "the 4 GiB member streamed from host memory in 256 MiB segments")
     ap.add_argument("--chunk-bytes", type=int, default=0, help="fixed part size (default: autotuned)")
     ap.add_argument("--warps-per-block", type=int, default=4, choices=[2, 4, 8],
                     help="pass-1 CTA shape with a fixed --chunk-bytes or --profile-case")
     ap.add_argument("--exec-pipelined", type=int, default=0, choices=[0, 1],
                     help="pass-1 execution form with a fixed --chunk-bytes (default: autotuned)")
+    ap.add_argument("--served-requests", type=int, default=SERVED_REQUESTS,
+                    help="requests per offered load of the served extra (0: leave it out)")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="only the 512-member legs (no fastq256 files, served loop or CPU baseline)")
     ap.add_argument("--profile-case", default=None, metavar="MIB:LEVEL:CALLS|batch:CALLS|batchsweep:C/W/P,...",
                     help="run one checked case for an ncu capture and print its stage times: one FASTQ file, or "
                          "the benchmark's two files as one batch")
@@ -951,23 +1255,23 @@ def main():
                                           args.exec_pipelined)), flush=True)
         return
     args.warmup = max(3, args.warmup)
-    if args.workload in ("fastq4g", "batch512", "served", "stream") and args.impl == "pgz":
-        run = {"fastq4g": run_tune4g, "batch512": run_batch512, "served": run_served,
-               "stream": run_stream}[args.workload]
+    if args.workload in ("fastq4g", "served", "stream") and args.impl == "pgz":
+        run = {"fastq4g": run_tune4g, "served": run_served, "stream": run_stream}[args.workload]
         print(json.dumps(run(args)), flush=True)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         if rank == 0:
-            print(json.dumps(run_reference(args)), flush=True)
+            ref = run_reference_batch512(args) if args.workload == "batch512" else run_reference(args)
+            print(json.dumps(ref), flush=True)
         return
     if world > 1:
         import torch
         import torch.distributed as tdist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         tdist.init_process_group("nccl")
-    line = run_pgz(args, rank, world)
+    line = run_headline(args, rank, world) if args.workload == "batch512" else run_pgz(args, rank, world)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
