@@ -47,13 +47,14 @@ sys.path.insert(0, ROOT)
 
 L2_BYTES = 126 * (1 << 20)
 CHUNK_BYTES = 64 << 10        # compressed bytes per part when the autotuner is not run
-TUNE_CHUNKS = [32 << 10, 64 << 10, 128 << 10, 256 << 10, 512 << 10]   # the autotuner's part sizes ...
+TUNE_CHUNKS = [32 << 10, 64 << 10, 128 << 10, 256 << 10, 512 << 10]   # the autotuner's part sizes (and 1-2 waves) ...
 TUNE_WPB = [2, 4, 8]                                                # ... and pass-1 CTA shapes (warps)
 PLAIN_PARTS = 1024            # parts per file of the plain one-file-at-a-time form
 METRIC = "decompressed GB/s on 1 GB300 (batched vs plain), %HBM roofline; served p50/p99 ms"
 HEADLINE_DESC = ("512 synthetic gzip members, log-uniform 64 KiB-64 MiB (seed 3), FASTQ 150 bp / order-2 Markov "
                  "text, gzip -1/-6/-9")
-TUNE_CHUNKS_BATCH = [64 << 10, 128 << 10, 256 << 10, 512 << 10]   # the autotuner's part sizes on the 512 members
+TUNE_CHUNKS_BATCH = [128 << 10, 256 << 10, 512 << 10]   # the autotuner's part sizes on the 512 members
+                                                        # (and the sizes of 1-4 whole waves of pass-1 warps)
 TUNE_WPB_BATCH = [2, 4]
 SERVED_REQUESTS = 240         # requests per offered load in the default run (the full served run uses 2000)
 # DRAM bytes (read + write) of pass 1 (k_sync + k_inflate) per decompressed byte on this workload's batched
@@ -501,7 +502,8 @@ def config2_legs(pgz, files, dev, stream, steps: int, warmup: int, hbm: float):
             outs[k].zero_()
 
     ctx = pgz.pgz_create(pgz.pgz_config_init(device=dev, cuda_stream=stream.cuda_stream))
-    tune = autotune(pgz, ctx, jobs, TUNE_CHUNKS, TUNE_WPB)
+    tune = autotune(pgz, ctx, jobs, sorted(set(TUNE_CHUNKS) | set(wave_sizes(pgz, ctx, jobs, [4, 8], [1, 2]))),
+                    TUNE_WPB)
     chunk, wpb, xp = tune["best"]
     batch = pgz.Batch(ctx, jobs)
 
@@ -564,6 +566,18 @@ def _stage_line(stage, total_in, total_out, window_bytes, hbm):
                                    "frac": round((3 * total_out + window_bytes) / t / 1e9 / hbm, 4) if t else None},
             "roofline_crc": {"achieved": round(total_out / c / 1e9, 1) if c else None,
                              "frac": round(total_out / c / 1e9 / hbm, 4) if c else None}}
+
+
+def wave_sizes(pgz, ctx, jobs, wpbs, waves):
+    """Part sizes that give whole waves of the resident pass-1 warps over these jobs (pgz_wave_chunk_bytes),
+    for each CTA shape and wave count."""
+    out = set()
+    for w in wpbs:
+        for k in waves:
+            st, cb, _ = pgz.pgz_wave_chunk_bytes(ctx, jobs, w, k)
+            if st == 0:
+                out.add(cb)
+    return sorted(out)
 
 
 def autotune(pgz, ctx, jobs, chunks, wpbs):
@@ -662,7 +676,9 @@ def run_headline(args, rank, world):
                                              chunk_bytes=args.chunk_bytes or (256 << 10),
                                              warps_per_block=args.warps_per_block,
                                              exec_pipelined=args.exec_pipelined))
-    tune = None if args.chunk_bytes else autotune(pgz, ctx, jobs, TUNE_CHUNKS_BATCH, TUNE_WPB_BATCH)
+    tune = None if args.chunk_bytes else autotune(
+        pgz, ctx, jobs, sorted(set(TUNE_CHUNKS_BATCH) | set(wave_sizes(pgz, ctx, jobs, [4], [1, 2, 3, 4]))),
+        TUNE_WPB_BATCH)
     chunk, wpb, xp = tune["best"] if tune else (args.chunk_bytes, args.warps_per_block, args.exec_pipelined)
     batch = pgz.Batch(ctx, jobs)
 
@@ -1142,6 +1158,9 @@ def run_profile_case(spec: str, chunk_bytes: int, wpb: int = 4, xp: int = 0):
         return run_profile_batch(int(spec.split(":")[1]), chunk_bytes, wpb, xp)
     if spec.startswith("batchsweep:"):
         return run_profile_sweep(spec.split(":", 1)[1])
+    if spec.startswith("members:"):
+        _, nm, calls = spec.split(":")
+        return run_profile_members(int(nm), int(calls), chunk_bytes, wpb, xp)
     mib, level, calls = (int(x) for x in spec.split(":"))
     build.build()
     raw = synth.fastq(mib << 20, 150, 0.001, 1)
@@ -1160,6 +1179,35 @@ def run_profile_case(spec: str, chunk_bytes: int, wpb: int = 4, xp: int = 0):
         raise RuntimeError("output mismatch")
     pgz.pgz_destroy(ctx)
     return {"case": f"{mib} MiB FASTQ gzip -{level}", "in_bytes": len(gz), "out_bytes": len(raw),
+            **{k: (round(v, 3) if isinstance(v, float) else v) for k, v in s.items()}}
+
+
+def run_profile_members(n_members: int, calls: int, chunk_bytes: int, wpb: int, xp: int = 0):
+    """--profile-case members:N:CALLS -- the first N members of the 512-member manifest decoded together by
+    pgz_decompress_batch, CALLS times (a prefix small enough for an ncu capture); outputs checked."""
+    import numpy as np
+    import torch
+    from paper_1905_07224_gb300 import build, pgz, synth
+    build.build()
+    files = synth.make_files(synth.batch_manifest(512, 3)[:n_members])
+    stream = torch.cuda.current_stream()
+    ctx = pgz.pgz_create(pgz.pgz_config_init(device=0, cuda_stream=stream.cuda_stream, n_chunks=0,
+                                             chunk_bytes=chunk_bytes, warps_per_block=wpb, exec_pipelined=xp))
+    d_in = [torch.from_numpy(np.frombuffer(g, dtype=np.uint8).copy()).cuda() for _, g in files]
+    d_out = [torch.empty(len(r) + 4096, dtype=torch.uint8, device="cuda") for r, _ in files]
+    jobs = [(d_in[k].data_ptr(), len(g), d_out[k].data_ptr(), d_out[k].numel()) for k, (_, g) in enumerate(files)]
+    s = None
+    for _ in range(calls):
+        r, res, s = pgz.pgz_decompress_batch(ctx, jobs, stats=True)
+        if r != 0:
+            raise RuntimeError(f"pgz_decompress_batch failed: {pgz.pgz_strerror(r)}")
+    torch.cuda.synchronize()
+    for k, (raw, _) in enumerate(files):
+        if d_out[k][:len(raw)].cpu().numpy().tobytes() != raw:
+            raise RuntimeError("output mismatch")
+    pgz.pgz_destroy(ctx)
+    return {"case": f"the first {n_members} members of the 512-member manifest (batched)", "chunk_bytes": chunk_bytes,
+            "warps_per_block": wpb, "exec_pipelined": xp,
             **{k: (round(v, 3) if isinstance(v, float) else v) for k, v in s.items()}}
 
 

@@ -202,7 +202,10 @@ int pgz_decompress_batch(pgz_ctx* ctx, int n, pgz_job* jobs, pgz_stats* st);
    each job's gz and out are HOST pointers (page-locked memory lets the copies
    overlap the decoding; pageable memory works but copies synchronously).  The
    jobs are cut into up to 4 groups of consecutive jobs with about equal
-   compressed bytes (groups of at least 96 MiB).  Every group is copied to
+   compressed bytes (groups of at least 96 MiB); each group's part size is
+   the one nearest the context's that gives a whole number of waves of pass-1
+   warps (pgz_wave_chunk_bytes; the context's size as is with n_chunks set).
+   Every group is copied to
    device memory owned by the context, decoded by one run of the pass kernels
    as soon as its own copy has arrived, and its output copied back to the
    jobs' `out` while the next group decodes.  Statuses, out_len and the return
@@ -313,6 +316,18 @@ typedef struct pgz_tune_entry {
 int pgz_autotune(pgz_ctx* ctx, pgz_job* jobs, int n_jobs, const uint64_t* chunk_bytes, int n_chunk_bytes,
                  const int* warps_per_block, int n_wpb, int sweep_exec, int reps, pgz_tune_entry* entries,
                  pgz_tune_entry* best);
+
+/* The part size that cuts the jobs' members (gz_len of each; one member per
+   job, 10-byte gzip headers assumed) into about waves x R parts, where R is
+   the number of pass-1 warps the device holds at once with the given CTA
+   shape (*resident_warps, nullable): the pass-1 kernels are persistent grids
+   of R warps, one part per warp at a time, so a part count of whole waves
+   leaves no warp idle at the end of a launch.  *chunk_bytes: the smallest
+   size (>= 4096) whose part count does not exceed the target.  For the
+   autotuner's list of sizes; no device work.  PGZ_E_ARG for bad arguments
+   (warps_per_block not 2, 4 or 8; waves <= 0). */
+int pgz_wave_chunk_bytes(pgz_ctx* ctx, const pgz_job* jobs, int n_jobs, int warps_per_block, double waves,
+                         uint64_t* chunk_bytes, int* resident_warps);
 
 /* Sets the context's part size (n_chunks = 0), pass-1 CTA shape and pass-1
    execution form, as pgz_autotune does with its choice: for a configuration

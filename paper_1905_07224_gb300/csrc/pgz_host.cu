@@ -234,12 +234,13 @@ struct Plan {
     std::vector<ChunkDesc> chunks;
     std::vector<int32_t> g0, gn, gfile;
     std::vector<uint64_t> seg0;
+    std::vector<uint32_t> order;  // the parts in the order the pass-1 work queue hands them out
     uint64_t sym_total = 0, max_cap = 0, total_seg = 0;
     bool chain = true, translate = true, crc = true;
     bool results_valid = false;   // the device chunk array holds the last run's results
     int wpb = 4;                  // warps per block of the pass-1 kernels (sizes the token scratch)
     const uint8_t* fill = nullptr;   // device window of fill bytes (mode 1)
-    DBuf d_files, d_chunks, d_g0, d_gn, d_gfile, d_seg0, d_sym, d_windows, d_gmaps, d_wstart, d_tok, d_queue;
+    DBuf d_files, d_chunks, d_g0, d_gn, d_gfile, d_seg0, d_sym, d_windows, d_gmaps, d_wstart, d_tok, d_queue, d_order;
     PBuf h_files, h_chunks;
     cudaGraphExec_t graph = nullptr;
     void release() {
@@ -255,6 +256,7 @@ struct Plan {
         d_wstart.release();
         d_tok.release();
         d_queue.release();
+        d_order.release();
         h_files.release();
         h_chunks.release();
         if (graph) cudaGraphExecDestroy(graph);
@@ -405,6 +407,16 @@ int layout(Plan& P) {
         seg += F.nseg;
     }
     P.total_seg = seg;
+    // longest expected work first: a part's symbol capacity is planned from its member's expected output per
+    // part (ranges: the indexed part's length), so parts with more output to produce start earlier and the
+    // short ones fill the end of the persistent launches; parts that will not run go last
+    P.order.resize(P.chunks.size());
+    for (size_t c = 0; c < P.order.size(); ++c) P.order[c] = (uint32_t)c;
+    std::stable_sort(P.order.begin(), P.order.end(), [&](uint32_t a, uint32_t b) {
+        const ChunkDesc &A = P.chunks[a], &B = P.chunks[b];
+        const uint64_t wa = A.disabled ? 0 : A.cap, wb = B.disabled ? 0 : B.cap;
+        return wa > wb;
+    });
     const size_t nf = P.files.size(), nc = P.chunks.size(), ng = P.g0.size();
     cudaError_t e = cudaSuccess;
     if (!e) e = P.d_files.ensure(nf * sizeof(FileDesc));
@@ -416,6 +428,7 @@ int layout(Plan& P) {
     if (!e) e = P.d_sym.ensure(P.sym_total * sizeof(uint16_t));
     if (!e) e = P.d_tok.ensure((size_t)pass1_warps((int)nc, P.wpb) * token_words_per_part() * sizeof(uint32_t));
     if (!e) e = P.d_queue.ensure(2 * sizeof(uint32_t));
+    if (!e) e = P.d_order.ensure(nc * sizeof(uint32_t));
     if (!e && P.chain) e = P.d_windows.ensure(nc * (size_t)kWin);
     if (!e && P.chain) e = P.d_gmaps.ensure(ng * (size_t)kWin * sizeof(uint16_t));
     if (!e && P.chain) e = P.d_wstart.ensure(ng * (size_t)kWin);
@@ -432,6 +445,7 @@ void upload_static(Plan& P, cudaStream_t s) {
     cudaMemcpyAsync(P.d_gn.p, P.gn.data(), ng * sizeof(int32_t), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(P.d_gfile.p, P.gfile.data(), ng * sizeof(int32_t), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(P.d_seg0.p, P.seg0.data(), nf * sizeof(uint64_t), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(P.d_order.p, P.order.data(), P.order.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
 }
 
 int enqueue(pgz_ctx* ctx, Plan& P, cudaStream_t s, bool timed) {
@@ -445,10 +459,12 @@ int enqueue(pgz_ctx* ctx, Plan& P, cudaStream_t s, bool timed) {
     uint16_t* sym = P.d_sym.as<uint16_t>();
     int k = 0;
     if (timed) cudaEventRecord(ctx->ev[0], s);
-    launch_sync(df, dc, (int)nc, sym, P.d_tok.as<uint32_t>(), P.d_queue.as<uint32_t>(), ctx->kp, s);
+    launch_pass1(df, dc, (int)nc, sym, P.d_tok.as<uint32_t>(), P.d_queue.as<uint32_t>(), P.d_order.as<uint32_t>(),
+                ctx->kp, s);
     if (cudaPeekAtLastError() != cudaSuccess) return PGZ_E_CUDA;
     if (timed) cudaEventRecord(ctx->ev[1], s);
-    launch_inflate(df, dc, (int)nc, sym, P.d_tok.as<uint32_t>(), P.d_queue.as<uint32_t>() + 1, ctx->kp, s);
+    launch_pass1_finish(df, dc, (int)nc, sym, P.d_tok.as<uint32_t>(), P.d_queue.as<uint32_t>() + 1,
+                   P.d_order.as<uint32_t>(), ctx->kp, s);
     if (cudaPeekAtLastError() != cudaSuccess) return PGZ_E_CUDA;
     launch_plan(df, dc, (int)nf, s);
     k += 3;
@@ -1054,6 +1070,34 @@ void finish_slot(pgz_server* S, SrvSlot& sl, int* n_done) {
 }  // namespace
 
 
+namespace {
+
+// parts of members of the given compressed sizes (gzip header of 10 bytes) as plan_member cuts them
+uint64_t parts_for(const std::vector<uint64_t>& gz_len, uint64_t c) {
+    uint64_t total = 0;
+    for (const uint64_t L : gz_len) {
+        const uint64_t cs = L > 18 ? L - 18 : 1;
+        const uint64_t n = std::max<uint64_t>(1, (cs + c - 1) / c);
+        total += std::max<uint64_t>(1, std::min<uint64_t>(n, std::max<uint64_t>(1, cs / 64)));
+    }
+    return total;
+}
+
+// the smallest part size (>= 4096) whose part count over the members is at most `target`
+uint64_t size_for_parts(const std::vector<uint64_t>& gz_len, uint64_t target) {
+    uint64_t lo = 4096, hi = 4096;
+    for (const uint64_t L : gz_len) hi = std::max<uint64_t>(hi, L);
+    if (parts_for(gz_len, lo) <= target) return lo;
+    while (lo < hi) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (parts_for(gz_len, mid) <= target) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+}  // namespace
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -1350,12 +1394,24 @@ int pgz_decompress_batch_host(pgz_ctx* ctx, int n, pgz_job* jobs, pgz_stats* st)
     // a good member below 4 GiB, corrected below when the run says otherwise)
     int status = PGZ_OK;
     std::vector<char> started((size_t)ng, 0);
+    const pgz_config saved = ctx->cfg;
+    const uint64_t W = ctx->cfg.n_chunks > 0 ? 0 : (uint64_t)pass1_warps(1 << 30, ctx->kp.wpb);
     for (int g = 0; g < ng; ++g) {
         Plan& P = ctx->hb_plan[g];
         begin_plan(P);
+        if (W) {   // the group's parts in a whole number of waves of pass-1 warps, near the context's part size
+            std::vector<uint64_t> lens;
+            for (int k = gfirst[g]; k < gfirst[g + 1]; ++k)
+                if (valid[k]) lens.push_back(jobs[k].gz_len);
+            if (!lens.empty()) {
+                const uint64_t waves = std::max<uint64_t>(1, (parts_for(lens, saved.chunk_bytes) + W / 2) / W);
+                ctx->cfg.chunk_bytes = size_for_parts(lens, waves * W);
+            }
+        }
         for (int k = gfirst[g]; k < gfirst[g + 1]; ++k)
             if (valid[k])
                 plan_member(ctx, P, din + in_off[k], jobs[k].gz_len, dout + out_off[k], jobs[k].out_cap, mi[k], 0);
+        ctx->cfg = saved;
         if (P.files.empty()) continue;
         if (cudaStreamWaitEvent(ctx->stream, ctx->hb_ev_up[g], 0) != cudaSuccess) return PGZ_E_CUDA;
         const int e = start_run(ctx, P, false);
@@ -1559,6 +1615,21 @@ int pgz_inspect_window(pgz_ctx* ctx, int part, uint8_t* host_dst) {
 }
 
 uint64_t pgz_kernel_launches(const pgz_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int pgz_wave_chunk_bytes(pgz_ctx* ctx, const pgz_job* jobs, int n_jobs, int warps_per_block, double waves,
+                         uint64_t* chunk_bytes, int* resident_warps) {
+    if (!ctx || !jobs || n_jobs <= 0 || !chunk_bytes || !(waves > 0.0) ||
+        (warps_per_block != 2 && warps_per_block != 4 && warps_per_block != 8))
+        return PGZ_E_ARG;
+    cudaSetDevice(ctx->cfg.device);
+    const uint64_t W = (uint64_t)pass1_warps(1 << 30, warps_per_block);
+    if (resident_warps) *resident_warps = (int)W;
+    const uint64_t target = std::max<uint64_t>(1, (uint64_t)std::llround(waves * (double)W));
+    std::vector<uint64_t> lens((size_t)n_jobs);
+    for (int k = 0; k < n_jobs; ++k) lens[(size_t)k] = jobs[k].gz_len;
+    *chunk_bytes = size_for_parts(lens, target);
+    return PGZ_OK;
+}
 
 int pgz_set_tuning(pgz_ctx* ctx, uint64_t chunk_bytes, int warps_per_block, int exec_pipelined) {
     if (!ctx || chunk_bytes < 4096 || (warps_per_block != 2 && warps_per_block != 4 && warps_per_block != 8) ||

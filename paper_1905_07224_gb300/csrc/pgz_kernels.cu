@@ -2,25 +2,25 @@
 // (Kerbiriou & Chikhi, arXiv 1905.07224, Section "Full file decompression in
 // two passes (pugz)").
 //
-//   k_sync      pass 1a: per part, the first bit of [lo, hi) where a DEFLATE
-//               block starts (Section "Detection of DEFLATE block start
-//               positions", Appendix "DEFLATE block decompression checks"):
-//               a warp tests 1024 bit offsets per step (one 32-bit window per
-//               lane, bit-parallel header tests), __ballot_sync + __ffs elect
-//               the lowest candidate, and the candidate's whole block is then
-//               decoded as the final check -- into the part's own output, so
-//               pass 1 resumes after it.
-//   k_inflate   pass 1b: decode(C_i, w^_i) (Algorithm "DEFLATE decompression"
-//               with the symbolic context [U_0..U_32767]) up to the next
-//               part's block start.  One warp per part: all lanes run the
-//               Huffman decoder in lock step (shared-memory lookup tables),
-//               each lane keeping one of 32 tokens; the warp then writes the
-//               32 tokens' symbols cooperatively (prefix sum of lengths,
-//               parallel copies, in-order copies only where a copy reads
-//               symbols of its own batch).  The 32 KiB window is the part's
-//               own u16 output in global memory; a source before the part
-//               start p < 0 is the placeholder U_{32768+p}, computed, not
-//               stored.
+//   k_pass1     pass 1, one warp per part from a work queue: the first bit
+//               of [lo, hi) where a DEFLATE block starts (Section "Detection
+//               of DEFLATE block start positions", Appendix "DEFLATE block
+//               decompression checks"): a warp tests 1024 bit offsets per step
+//               (one 32-bit window per lane, bit-parallel header tests),
+//               __ballot_sync + __ffs elect the lowest candidate, and the
+//               candidate's whole block is decoded as the final check -- into
+//               the part's own output.  The start is published, and the warp
+//               goes on with decode(C_i, w^_i) (Algorithm "DEFLATE
+//               decompression" with the symbolic context [U_0..U_32767]) up
+//               to the next part's block start.  The warp's lanes decode
+//               segments of a block in parallel and meet (see par_block), then
+//               write the tokens' symbols cooperatively.  The 32 KiB window is
+//               the part's own u16 output in global memory; a source before
+//               the part start p < 0 is the placeholder U_{32768+p}, computed,
+//               not stored.  A part never waits for another: if the next
+//               part's start is not published when the decoding reaches that
+//               part's scan start, the part stops there;
+//   k_inflate   the finishing launch: those parts, up to their stop.
 //   k_plan      output offsets of the parts (prefix of their lengths), error
 //               aggregation, ISIZE and capacity checks.
 //   k_chain_*   pass 2a: w_{i+1} from w_i and the tail of D_i (Section "Full
@@ -69,6 +69,7 @@ __constant__ uint32_t c_crc_tab[4][256];   // [0][b]: register after byte b from
 __constant__ uint32_t c_x2k[64];           // x^(2^k) mod P
 __constant__ uint32_t c_lane_shift[32];    // x^(8*kPiece*k) mod P
 __constant__ uint32_t c_xseg;              // x^(8*kCrcSeg) mod P
+__constant__ uint32_t c_xhalf;             // x^(8*kPiece/2) mod P
 
 // literal/length lookup entry: bits 0-4 bits to drop, 8-16 value, 17-19
 // extra-bit count (K_LENX), 28-31 kind.  K_LEN carries the exact length
@@ -872,7 +873,7 @@ __device__ __forceinline__ PassMasks build_pass(uint32_t* masks, const uint32_t*
 // (overlapping copies included, with no division).
 // PIPE: the passes are pipelined (the next pass's final sources copied
 // asynchronously while a pass resolves); else one pass at a time with direct
-// loads.  k_sync always takes the second (its block-start search leaves fewer
+// loads.  A part's first block always takes the second (the block-start search leaves fewer
 // registers); k_inflate takes either (KParams::pipe): which is faster depends
 // on the data (how far back the sources lie), so the autotuner can choose.
 template <bool PIPE>
@@ -1273,7 +1274,7 @@ __device__ int one_block(WarpSmem& S, uint32_t* tokbuf, BitIn& br, OutState& o, 
 //     from a 512-entry table of three-field sums;
 //  3. the whole dynamic header is valid (the checks of read_dynamic<true>),
 //     32 listed offsets at a time, one per lane (hdr_ok_lane).
-// The full block decode then follows in k_sync, lowest offset first.  Stages
+// The full block decode then follows in k_pass1, lowest offset first.  Stages
 // 1-3 are implied by the complete checks, so no offset that passes those is
 // dropped here.
 // ---------------------------------------------------------------------------
@@ -1500,10 +1501,12 @@ __device__ __forceinline__ void init_smem(WarpSmem& S, const KParams& p, int lan
 // budget is set for (about 20 resident warps per SM, 96 registers a thread)
 constexpr int pass1_min_blocks(int wpb) { return wpb == 2 ? 10 : (wpb == 4 ? 5 : 2); }
 
-// Work queue of the pass-1 kernels: each resident warp takes the next part
-// index until the parts run out, so parts of uneven work (many members of
-// different sizes in one launch) balance over the warps.  Parts are taken in
-// increasing order.  The counter is zeroed on the stream before each launch.
+// Work queue of the pass-1 kernels: each resident warp takes the next queue
+// position until the parts run out, so parts of uneven work (many members of
+// different sizes in one launch) balance over the warps.  Position q holds
+// part order[q] (the parts with the most expected output first, so that the
+// short ones fill the end of the launch), or part q without an order.  The
+// counter is zeroed on the stream before each launch.
 __device__ __forceinline__ int next_part(uint32_t* queue, int lane) {
     uint32_t c = 0;
     if (lane == 0) c = atomicAdd(queue, 1u);
@@ -1511,24 +1514,13 @@ __device__ __forceinline__ int next_part(uint32_t* queue, int lane) {
 }
 
 // ---------------------------------------------------------------------------
-// k_sync: block start of each part and its first block
+// k_pass1: block start of each part, its first block, then the rest of the part
 // ---------------------------------------------------------------------------
-template <int WPB>
-__global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
-    k_sync(const FileDesc* __restrict__ files, ChunkDesc* chunks, int nchunks, uint16_t* symbuf, uint32_t* tokbuf,
-           uint32_t* queue, KParams p) {
-    __shared__ uint16_t kraft3[512];
-    for (uint32_t v = threadIdx.x; v < 512; v += blockDim.x)
-        kraft3[v] = (uint16_t)(kraft1(v & 7) + kraft1((v >> 3) & 7) + kraft1(v >> 6));
-    __syncthreads();
-    WarpSmem& S = warp_smem();
-    const int lane = threadIdx.x & 31;
-    uint32_t* tok = tokbuf + (uint64_t)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kTokPerPart;
-    for (;;) {
-    const int c = next_part(queue, lane);
-    if (c >= nchunks) return;
-    ChunkDesc& C = chunks[c];
-    const FileDesc& F = files[C.file];
+// The block start of part c and its first block (Section "Detection of DEFLATE block start positions").  The
+// results go to C with the state written last, after a fence: a warp of the same launch that reads a state
+// other than CS_PENDING (with a volatile load, then a fence) reads this part's final start.
+__device__ void sync_part(const uint16_t* kraft3, WarpSmem& S, uint32_t* tok, const FileDesc& F, ChunkDesc& C,
+                          uint16_t* symbuf, const KParams& p, int lane) {
     init_smem(S, p, lane);
     OutState o{symbuf + C.sym_base, C.cap, 0, C.index == 0 && C.lo <= F.s0_bit, false};
     BitIn br;
@@ -1575,7 +1567,6 @@ __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
     }
     const bool neg = __any_sync(FULL, o.neg);
     if (lane == 0) {
-        C.state = state;
         C.err = err;
         C.sync = sync;
         C.resume = resume;
@@ -1587,25 +1578,48 @@ __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
         C.final = final && state == CS_FOUND;
         C.confirmed = (state == CS_FOUND && (o.known || C.given || final || p.confirm_blocks == 0)) ? 1u : 0u;
         C.end = resume;
+        __threadfence();
+        *reinterpret_cast<volatile uint32_t*>(&C.state) = state;
     }
+    __syncwarp();
+}
+
+// Where part c's decoding stops: the start of the next part that holds one.  With `launch` (the launch that
+// also searches the block starts), a later part whose search is not finished bounds the decoding instead:
+// *limit receives its scan start (its start, if it has one, lies at or after it), and the decoding may not
+// pass that bit until the search is known.  Parts merged into their predecessor hold no start.
+__device__ __forceinline__ void find_stop(const FileDesc& F, const ChunkDesc* chunks, int c, uint64_t stop_hint,
+                                          bool launch, uint64_t& stop, uint64_t& limit) {
+    stop = stop_hint;
+    limit = kNone;
+    for (int j = c + 1; j < F.chunk0 + F.nchunks; ++j) {
+        const ChunkDesc& J = chunks[j];
+        if (J.disabled) continue;
+        if (launch) {
+            const uint32_t st = *reinterpret_cast<const volatile uint32_t*>(&J.state);
+            if (st == CS_PENDING) {
+                limit = J.lo;
+                return;
+            }
+            __threadfence();
+        }
+        const uint64_t sj = *reinterpret_cast<const volatile uint64_t*>(&J.sync);
+        if (sj != kNone) {
+            stop = sj;
+            return;
+        }
     }
 }
 
-// ---------------------------------------------------------------------------
-// k_inflate: pass 1 of each part up to the next part's block start
-// ---------------------------------------------------------------------------
-template <int WPB, bool PIPE>
-__global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
-    k_inflate(const FileDesc* __restrict__ files, ChunkDesc* chunks, int nchunks, uint16_t* symbuf, uint32_t* tokbuf,
-              uint32_t* queue, KParams p) {
-    WarpSmem& S = warp_smem();
-    const int lane = threadIdx.x & 31;
-    uint32_t* tok = tokbuf + (uint64_t)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kTokPerPart;
-    for (;;) {
-    const int c = next_part(queue, lane);
-    if (c >= nchunks) return;
+// Pass 1 of part c from the end of its first block up to the next part's block start.  In the launch that
+// also searches block starts (`launch`), a part whose successor's search is not finished when the decoding
+// reaches that successor's scan start stops there, at a block boundary, and keeps its state CS_FOUND with
+// its progress (symbols, resume bit, blocks): the finishing launch (k_inflate) continues it.  No warp waits.
+template <bool PIPE>
+__device__ void inflate_part(WarpSmem& S, uint32_t* tok, const FileDesc* __restrict__ files, ChunkDesc* chunks, int c,
+                             uint16_t* symbuf, const KParams& p, int lane, bool launch) {
     ChunkDesc& C = chunks[c];
-    if (C.state != CS_FOUND) continue;
+    if (C.state != CS_FOUND) return;
     if (C.probe) {                    // a streamed segment's end: the block start found is all it gives
         if (lane == 0) {
             C.state = CS_DONE;
@@ -1616,27 +1630,24 @@ __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
             C.confirmed = 0;
             C.end = C.sync;
         }
-        continue;
+        __syncwarp();
+        return;
     }
     const FileDesc& F = files[C.file];
-    // the next part that holds a block start.  `sync` is final after k_sync
-    // and never written here (other warps of this kernel rewrite `state`).
-    uint64_t stop = C.stop_hint;
-    for (int j = c + 1; j < F.chunk0 + F.nchunks; ++j) {
-        const uint64_t sj = chunks[j].sync;
-        if (sj != kNone) {
-            stop = sj;
-            break;
-        }
-    }
+    uint64_t stop, limit;
+    find_stop(F, chunks, c, C.stop_hint, launch, stop, limit);
     OutState o{symbuf + C.sym_base, C.cap, C.n, C.index == 0 && C.sync == F.s0_bit, false};
     uint32_t blocks = C.blocks, final = C.final, err = CE_OK, confirmed = C.confirmed;
     uint64_t end = C.resume;
+    bool paused = false;
     // the confirmation (Section "Detection of DEFLATE block start positions") covers the start's block and
     // the confirm_blocks blocks after it; they are decoded with the literal checks
     const uint32_t window = (uint32_t)p.confirm_blocks + 1u;
     if (final) {
-        if (stop != kNone && !F.open_end) err = CE_CHAIN;
+        if (limit != kNone) paused = true;
+        else if (stop != kNone && !F.open_end) err = CE_CHAIN;
+    } else if (limit != kNone && C.resume >= limit) {
+        paused = true;
     } else if (!(stop != kNone && C.resume == stop) || (C.confirm_ext && !confirmed)) {
         init_smem(S, p, lane);
         BitIn br;
@@ -1649,6 +1660,13 @@ __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
         uint64_t n_stop = 0, end_stop = 0;
         for (;;) {
             const uint64_t pos = br.pos();
+            if (!past && limit != kNone && pos >= limit) {        // a later part's search may have ended since
+                find_stop(F, chunks, c, C.stop_hint, launch, stop, limit);
+                if (limit != kNone && pos >= limit) {
+                    paused = true;
+                    break;
+                }
+            }
             if (!past && stop != kNone && pos >= stop) {
                 err_stop = pos != stop ? (uint32_t)CE_CHAIN : (uint32_t)CE_OK;
                 if (!C.confirm_ext || blocks >= window) {
@@ -1672,6 +1690,13 @@ __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
                 if (blocks <= window) confirmed = 1;
                 if (past) break;
                 final = 1;
+                if (limit != kNone) {             // whether a later part holds a start decides CE_CHAIN
+                    find_stop(F, chunks, c, C.stop_hint, launch, stop, limit);
+                    if (limit != kNone) {         // not known yet: the finishing launch decides
+                        paused = true;
+                        break;
+                    }
+                }
                 if (stop != kNone && !F.open_end) err = CE_CHAIN;   // an open member may end before the next part
                 break;
             }
@@ -1686,10 +1711,23 @@ __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
             }
         }
     }
+    const bool neg = __any_sync(FULL, o.neg);
+    if (paused) {                         // progress kept for the finishing launch; the state stays CS_FOUND
+        if (lane == 0) {
+            C.n = o.n;
+            C.resume = end;
+            C.end = end;
+            C.blocks = blocks;
+            C.final = final;
+            C.confirmed = confirmed;
+            C.anyph = C.anyph | (neg ? 1u : 0u);
+        }
+        __syncwarp();
+        return;
+    }
     if (err == CE_OK && final && F.mode != 2 && !F.open_end) {   // the trailer must follow the final block
         if (((end + 7) >> 3) + 8 != F.gz_len) err = CE_TRAIL;
     }
-    const bool neg = __any_sync(FULL, o.neg);
     if (lane == 0) {
         C.state = err ? CS_ERROR : CS_DONE;
         C.err = err;
@@ -1700,6 +1738,45 @@ __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
         C.confirmed = confirmed;
         C.end = end;
     }
+    __syncwarp();
+}
+
+// One launch of pass 1: every part's block start and first block, then the rest of the part (parts from
+// the work queue, one per warp at a time).
+template <int WPB, bool PIPE>
+__global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
+    k_pass1(const FileDesc* __restrict__ files, ChunkDesc* chunks, int nchunks, uint16_t* symbuf, uint32_t* tokbuf,
+            uint32_t* queue, const uint32_t* __restrict__ order, KParams p) {
+    __shared__ uint16_t kraft3[512];
+    for (uint32_t v = threadIdx.x; v < 512; v += blockDim.x)
+        kraft3[v] = (uint16_t)(kraft1(v & 7) + kraft1((v >> 3) & 7) + kraft1(v >> 6));
+    __syncthreads();
+    WarpSmem& S = warp_smem();
+    const int lane = threadIdx.x & 31;
+    uint32_t* tok = tokbuf + (uint64_t)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kTokPerPart;
+    for (;;) {
+        const int q = next_part(queue, lane);
+        if (q >= nchunks) return;
+        const int c = order ? (int)__ldg(order + q) : q;
+        ChunkDesc& C = chunks[c];
+        sync_part(kraft3, S, tok, files[C.file], C, symbuf, p, lane);
+        inflate_part<PIPE>(S, tok, files, chunks, c, symbuf, p, lane, true);
+    }
+}
+
+// The finishing launch: the parts the first launch left at a later part's scan start, up to their stop.
+template <int WPB, bool PIPE>
+__global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
+    k_inflate(const FileDesc* __restrict__ files, ChunkDesc* chunks, int nchunks, uint16_t* symbuf, uint32_t* tokbuf,
+              uint32_t* queue, const uint32_t* __restrict__ order, KParams p) {
+    WarpSmem& S = warp_smem();
+    const int lane = threadIdx.x & 31;
+    uint32_t* tok = tokbuf + (uint64_t)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kTokPerPart;
+    for (;;) {
+        const int q = next_part(queue, lane);
+        if (q >= nchunks) return;
+        const int c = order ? (int)__ldg(order + q) : q;
+        inflate_part<PIPE>(S, tok, files, chunks, c, symbuf, p, lane, false);
     }
 }
 
@@ -2136,44 +2213,43 @@ __device__ __forceinline__ uint32_t crc_word(const uint32_t* Tl, uint32_t r, uin
            Tl[32u * (256u + ((x >> 16) & 0xffu))] ^ Tl[32u * (x >> 24)];
 }
 
-// raw CRC register (zero start) of n bytes at p; Tl is the lane's table copy
-__device__ __forceinline__ uint32_t crc_bytes(const uint32_t* Tl, const uint8_t* p, uint64_t n) {
-    uint32_t r = 0;
+// raw CRC register (zero start) of n bytes at p; Tl is the lane's table copy.  A whole 16-byte aligned piece
+// runs as two independent chains over its halves (their lookups overlap), joined by one shift of the first
+// half's register over the second half's length: R(A||B) = R(A) x^(8|B|) + R(B).
+__device__ __forceinline__ uint32_t crc_bytes(const uint32_t* Tl, const uint8_t* p, uint64_t n, uint32_t xhalf) {
     if (n == kPiece && ((reinterpret_cast<uintptr_t>(p) & 15) == 0)) {
         const uint4* v = reinterpret_cast<const uint4*>(p);
         constexpr int H = kPiece / 32;                    // 16-byte loads per half piece
-        uint4 x[H];
+        uint4 a[H], b[H];
 #pragma unroll
-        for (int q = 0; q < H; ++q) x[q] = v[q];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            uint4 y[H];
-            if (h == 0) {
-#pragma unroll
-                for (int q = 0; q < H; ++q) y[q] = v[H + q];   // the second half in flight meanwhile
-            }
-#pragma unroll
-            for (int q = 0; q < H; ++q) {
-                r = crc_word(Tl, r, x[q].x);
-                r = crc_word(Tl, r, x[q].y);
-                r = crc_word(Tl, r, x[q].z);
-                r = crc_word(Tl, r, x[q].w);
-            }
-            if (h == 0) {
-#pragma unroll
-                for (int q = 0; q < H; ++q) x[q] = y[q];
-            }
+        for (int q = 0; q < H; ++q) {
+            a[q] = v[q];
+            b[q] = v[H + q];
         }
-    } else {
-        for (uint64_t i = 0; i < n; ++i) r = Tl[32u * ((r ^ p[i]) & 0xffu)] ^ (r >> 8);
+        uint32_t ra = 0, rb = 0;
+#pragma unroll
+        for (int q = 0; q < H; ++q) {
+            ra = crc_word(Tl, ra, a[q].x);
+            rb = crc_word(Tl, rb, b[q].x);
+            ra = crc_word(Tl, ra, a[q].y);
+            rb = crc_word(Tl, rb, b[q].y);
+            ra = crc_word(Tl, ra, a[q].z);
+            rb = crc_word(Tl, rb, b[q].z);
+            ra = crc_word(Tl, ra, a[q].w);
+            rb = crc_word(Tl, rb, b[q].w);
+        }
+        return gf2_mul(ra, xhalf) ^ rb;
     }
+    uint32_t r = 0;
+    for (uint64_t i = 0; i < n; ++i) r = Tl[32u * ((r ^ p[i]) & 0xffu)] ^ (r >> 8);
     return r;
 }
 
 // Each warp takes a contiguous run of segments: the 32 lanes' pieces of a
 // segment are combined by their shift to the segment end, segments are
 // folded in order (R(A||B) = R(A) x^(8|B|) + R(B)), and a run is shifted to
-// the end of its member once and XOR-accumulated there.
+// the end of its member once and XOR-accumulated there.  The member of a
+// segment is found once per run, then followed forward.
 __global__ void __launch_bounds__(kCrcThreads, 1) k_crc(FileDesc* files, int nfiles, uint64_t total_seg,
                                                         const uint64_t* seg0, uint64_t segs_per_warp) {
     extern __shared__ uint32_t T[];                       // 4 x 256 x 32 words
@@ -2183,40 +2259,58 @@ __global__ void __launch_bounds__(kCrcThreads, 1) k_crc(FileDesc* files, int nfi
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const uint32_t* Tl = T + lane;
+    const uint32_t xhalf = c_xhalf;
     const uint64_t w = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const uint64_t s_begin = w * segs_per_warp;
     if (s_begin >= total_seg) return;
     const uint64_t s_end = s_begin + segs_per_warp < total_seg ? s_begin + segs_per_warp : total_seg;
-    int f = -1;
+    int f;
+    {
+        int lo = 0, hi = nfiles - 1;                      // member holding the run's first segment
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (seg0[mid] <= s_begin) lo = mid;
+            else hi = mid - 1;
+        }
+        f = lo;
+    }
+    uint64_t next_seg0 = f + 1 < nfiles ? seg0[f + 1] : ~0ull;
     uint32_t acc = 0;
     uint64_t run_end = 0;
     auto flush = [&]() {
-        if (f >= 0 && lane == 0 && run_end > 0) atomicXor(&files[f].crc_acc, gf2_mul(acc, xpow8(files[f].total - run_end)));
+        if (lane == 0 && run_end > 0) atomicXor(&files[f].crc_acc, gf2_mul(acc, xpow8(files[f].total - run_end)));
     };
+    bool skip = false;
+    uint64_t D = 0, base_seg = 0;
+    const uint8_t* out = nullptr;
+    auto enter = [&]() {                                  // the member's fields, once per member of the run
+        const FileDesc& F = files[f];
+        skip = F.status != PGZ_OK || (F.mode != 0 && F.mode != 3);
+        D = F.total;
+        out = F.out;
+        base_seg = seg0[f];
+        acc = 0;
+        run_end = 0;
+    };
+    enter();
     for (uint64_t sg = s_begin; sg < s_end; ++sg) {
-        int lo = 0, hi = nfiles - 1;                      // member holding segment sg
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (seg0[mid] <= sg) lo = mid;
-            else hi = mid - 1;
-        }
-        if (lo != f) {
+        if (sg >= next_seg0) {                            // the next member (members with no segment skipped)
             flush();
-            f = lo;
-            acc = 0;
-            run_end = 0;
+            do {
+                ++f;
+                next_seg0 = f + 1 < nfiles ? seg0[f + 1] : ~0ull;
+            } while (sg >= next_seg0);
+            enter();
         }
-        FileDesc& F = files[f];
-        if (F.status != PGZ_OK || (F.mode != 0 && F.mode != 3)) continue;
-        const uint64_t D = F.total;
-        const uint64_t a = (sg - seg0[f]) * kCrcSeg;
+        if (skip) continue;
+        const uint64_t a = (sg - base_seg) * kCrcSeg;
         if (a >= D) continue;
         const uint64_t se = a + kCrcSeg < D ? a + kCrcSeg : D;
         const uint64_t pa = a + (uint64_t)kPiece * lane;
         const uint64_t pb = pa + kPiece < se ? pa + kPiece : se;
         uint32_t r = 0;
         if (pa < pb) {
-            r = crc_bytes(Tl, F.out + pa, pb - pa);
+            r = crc_bytes(Tl, out + pa, pb - pa, xhalf);
             r = (se - a == kCrcSeg) ? gf2_mul(r, LS[31 - lane]) : gf2_mul(r, xpow8(se - pb));
         }
         for (int d = 16; d; d >>= 1) r ^= __shfl_xor_sync(FULL, r, d);
@@ -2341,16 +2435,22 @@ static int pass1_resident_blocks_t() {
     const int slot = dev >= 0 && dev < 64 ? dev : 0;
     if (!cached[slot]) {
         const int smem = (int)(WPB * warp_smem_bytes());
-        int sms = 0, per_sm_sync = 0, per_sm_inflate = 0;
+        int sms = 0, per_sm_a = 0, per_sm_b = 0, per_sm_c = 0;
         const bool ok =
-            cudaFuncSetAttribute(k_sync<WPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
+            cudaFuncSetAttribute(k_pass1<WPB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+                cudaSuccess &&
+            cudaFuncSetAttribute(k_pass1<WPB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
             cudaFuncSetAttribute(k_inflate<WPB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
                 cudaSuccess &&
             cudaFuncSetAttribute(k_inflate<WPB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_sync, k_sync<WPB>, 32 * WPB, smem) == cudaSuccess &&
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_inflate, k_inflate<WPB, false>, 32 * WPB, smem) ==
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, k_pass1<WPB, false>, 32 * WPB, smem) ==
+                cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, k_pass1<WPB, true>, 32 * WPB, smem) ==
+                cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_c, k_inflate<WPB, false>, 32 * WPB, smem) ==
                 cudaSuccess;
+        const int per_sm_sync = std::min(per_sm_a, per_sm_b), per_sm_inflate = per_sm_c;
         const int v = std::max(1, sms) * std::max(1, std::min(per_sm_sync, per_sm_inflate));
         if (!ok) {
             cudaGetLastError();
@@ -2377,34 +2477,37 @@ int pass1_warps(int nchunks, int wpb) {
 }
 
 template <int WPB>
-static void launch_pass1(bool sync, const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym,
-                         uint32_t* tok, uint32_t* queue, const KParams& p, cudaStream_t s) {
+static void launch_pass1_t(bool sync, const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym,
+                         uint32_t* tok, uint32_t* queue, const uint32_t* order, const KParams& p, cudaStream_t s) {
     const int grid = pass1_warps(nchunks, WPB) / WPB;
     const size_t smem = WPB * warp_smem_bytes();
-    if (sync) k_sync<WPB><<<grid, 32 * WPB, smem, s>>>(files, chunks, nchunks, sym, tok, queue, p);
-    else if (p.pipe) k_inflate<WPB, true><<<grid, 32 * WPB, smem, s>>>(files, chunks, nchunks, sym, tok, queue, p);
-    else k_inflate<WPB, false><<<grid, 32 * WPB, smem, s>>>(files, chunks, nchunks, sym, tok, queue, p);
+    if (sync && p.pipe) k_pass1<WPB, true><<<grid, 32 * WPB, smem, s>>>(files, chunks, nchunks, sym, tok, queue, order, p);
+    else if (sync) k_pass1<WPB, false><<<grid, 32 * WPB, smem, s>>>(files, chunks, nchunks, sym, tok, queue, order, p);
+    else if (p.pipe)
+        k_inflate<WPB, true><<<grid, 32 * WPB, smem, s>>>(files, chunks, nchunks, sym, tok, queue, order, p);
+    else k_inflate<WPB, false><<<grid, 32 * WPB, smem, s>>>(files, chunks, nchunks, sym, tok, queue, order, p);
 }
 
 static void launch_pass1_any(bool sync, const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym,
-                             uint32_t* tok, uint32_t* queue, const KParams& p, cudaStream_t s) {
+                             uint32_t* tok, uint32_t* queue, const uint32_t* order, const KParams& p,
+                             cudaStream_t s) {
     if (nchunks <= 0) return;
     cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
     switch (wpb_slot(wpb_of(p))) {
-        case 0: launch_pass1<2>(sync, files, chunks, nchunks, sym, tok, queue, p, s); break;
-        case 1: launch_pass1<4>(sync, files, chunks, nchunks, sym, tok, queue, p, s); break;
-        default: launch_pass1<8>(sync, files, chunks, nchunks, sym, tok, queue, p, s); break;
+        case 0: launch_pass1_t<2>(sync, files, chunks, nchunks, sym, tok, queue, order, p, s); break;
+        case 1: launch_pass1_t<4>(sync, files, chunks, nchunks, sym, tok, queue, order, p, s); break;
+        default: launch_pass1_t<8>(sync, files, chunks, nchunks, sym, tok, queue, order, p, s); break;
     }
 }
 
-void launch_sync(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, uint32_t* tok,
-                 uint32_t* queue, const KParams& p, cudaStream_t s) {
-    launch_pass1_any(true, files, chunks, nchunks, sym, tok, queue, p, s);
+void launch_pass1(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, uint32_t* tok,
+                  uint32_t* queue, const uint32_t* order, const KParams& p, cudaStream_t s) {
+    launch_pass1_any(true, files, chunks, nchunks, sym, tok, queue, order, p, s);
 }
 
-void launch_inflate(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, uint32_t* tok,
-                    uint32_t* queue, const KParams& p, cudaStream_t s) {
-    launch_pass1_any(false, files, chunks, nchunks, sym, tok, queue, p, s);
+void launch_pass1_finish(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, uint32_t* tok,
+                         uint32_t* queue, const uint32_t* order, const KParams& p, cudaStream_t s) {
+    launch_pass1_any(false, files, chunks, nchunks, sym, tok, queue, order, p, s);
 }
 
 uint64_t token_words_per_part() { return kTokPerPart; }
@@ -2528,7 +2631,14 @@ void upload_crc_tables() {
     cudaMemcpyToSymbol(c_crc_tab, tab, sizeof tab);
     cudaMemcpyToSymbol(c_x2k, x2k, sizeof x2k);
     cudaMemcpyToSymbol(c_lane_shift, ls, sizeof ls);
+    uint32_t xhalf = 0x80000000u;
+    {
+        uint64_t e = 8ull * (kPiece / 2);
+        for (int k = 0; e; ++k, e >>= 1)
+            if (e & 1) xhalf = h_mul(xhalf, x2k[k]);
+    }
     cudaMemcpyToSymbol(c_xseg, &xseg, sizeof xseg);
+    cudaMemcpyToSymbol(c_xhalf, &xhalf, sizeof xhalf);
 }
 
 }  // namespace pgz

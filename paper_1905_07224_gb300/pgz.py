@@ -85,6 +85,8 @@ def _load():
         "pgz_decompress_at": (ctypes.c_int, [VP, VP, U64, U64, VP, VP, ctypes.c_uint8, U64, P(U64), P(U64), P(U64)]),
         "pgz_decompress_batch": (ctypes.c_int, [VP, ctypes.c_int, P(pgz_job), P(pgz_stats)]),
         "pgz_decompress_batch_host": (ctypes.c_int, [VP, ctypes.c_int, P(pgz_job), P(pgz_stats)]),
+        "pgz_wave_chunk_bytes": (ctypes.c_int, [VP, P(pgz_job), ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                P(U64), P(ctypes.c_int)]),
         "pgz_batch_prepare": (ctypes.c_int, [VP, ctypes.c_int, P(pgz_job), P(VP)]),
         "pgz_batch_run": (ctypes.c_int, [VP, P(pgz_job), P(pgz_stats)]),
         "pgz_batch_free": (None, [VP]),
@@ -133,7 +135,7 @@ EXPORTED = ["pgz_config_init", "pgz_create", "pgz_destroy", "pgz_decompress", "p
             "pgz_inspect_symbols", "pgz_inspect_window", "pgz_kernel_launches", "pgz_strerror",
             "pgz_decompress_noalloc", "pgz_autotune", "pgz_server_create", "pgz_server_add_file",
             "pgz_server_submit", "pgz_server_poll", "pgz_server_drain", "pgz_server_pending", "pgz_server_destroy",
-            "pgz_extract_sequences", "pgz_decompress_stream", "pgz_set_tuning"]
+            "pgz_extract_sequences", "pgz_decompress_stream", "pgz_set_tuning", "pgz_wave_chunk_bytes"]
 
 
 def pgz_strerror(status: int) -> str:
@@ -248,6 +250,16 @@ def pgz_decompress_batch_host(ctx: int, jobs, stats: bool = False):
     st = pgz_stats() if stats else None
     r = lib().pgz_decompress_batch_host(ctx, len(jobs), arr, ctypes.byref(st) if st is not None else None)
     return r, [(arr[k].status, arr[k].out_len) for k in range(len(jobs))], (st.as_dict() if st is not None else None)
+
+
+def pgz_wave_chunk_bytes(ctx: int, jobs, warps_per_block: int, waves: float):
+    """(status, chunk_bytes, resident_warps): the part size giving about `waves` whole waves of the pass-1
+    warps over the jobs' members (jobs: list of (gz_ptr, gz_len, out_ptr, out_cap))."""
+    arr = _jobs(jobs)
+    cb, rw = U64(0), ctypes.c_int(0)
+    r = lib().pgz_wave_chunk_bytes(ctx, arr, len(jobs), warps_per_block, float(waves), ctypes.byref(cb),
+                                   ctypes.byref(rw))
+    return r, cb.value, rw.value
 
 
 class Batch:
