@@ -459,11 +459,11 @@ int enqueue(pgz_ctx* ctx, Plan& P, cudaStream_t s, bool timed) {
     uint16_t* sym = P.d_sym.as<uint16_t>();
     int k = 0;
     if (timed) cudaEventRecord(ctx->ev[0], s);
-    launch_pass1(df, dc, (int)nc, sym, P.d_tok.as<uint32_t>(), P.d_queue.as<uint32_t>(), P.d_order.as<uint32_t>(),
+    launch_sync(df, dc, (int)nc, sym, P.d_tok.as<uint32_t>(), P.d_queue.as<uint32_t>(), P.d_order.as<uint32_t>(),
                 ctx->kp, s);
     if (cudaPeekAtLastError() != cudaSuccess) return PGZ_E_CUDA;
     if (timed) cudaEventRecord(ctx->ev[1], s);
-    launch_pass1_finish(df, dc, (int)nc, sym, P.d_tok.as<uint32_t>(), P.d_queue.as<uint32_t>() + 1,
+    launch_inflate(df, dc, (int)nc, sym, P.d_tok.as<uint32_t>(), P.d_queue.as<uint32_t>() + 1,
                    P.d_order.as<uint32_t>(), ctx->kp, s);
     if (cudaPeekAtLastError() != cudaSuccess) return PGZ_E_CUDA;
     launch_plan(df, dc, (int)nf, s);

@@ -115,13 +115,10 @@ struct ChunkDesc {
 //      pass1_warps(nchunks, p.wpb) warps (at most nchunks rounded up to p.wpb);
 // queue: one u32 work counter per kernel (zeroed by the launcher on the stream);
 // order (nullable): the parts in the order the work queue hands them out (nchunks entries).
-// launch_pass1: every part's block start, first block and the rest of the part (k_pass1); a part whose
-// successor's block start is not known when its decoding reaches the successor's scan start stops there;
-// launch_pass1_finish (k_inflate) continues those parts to their stop.
-void launch_pass1(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, uint32_t* tok,
-                  uint32_t* queue, const uint32_t* order, const KParams& p, cudaStream_t s);
-void launch_pass1_finish(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, uint32_t* tok,
-                         uint32_t* queue, const uint32_t* order, const KParams& p, cudaStream_t s);
+void launch_sync(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, uint32_t* tok,
+                 uint32_t* queue, const uint32_t* order, const KParams& p, cudaStream_t s);
+void launch_inflate(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, uint32_t* tok,
+                    uint32_t* queue, const uint32_t* order, const KParams& p, cudaStream_t s);
 uint64_t token_words_per_part();
 int pass1_warps(int nchunks, int wpb);
 void launch_plan(FileDesc* files, ChunkDesc* chunks, int nfiles, cudaStream_t s);

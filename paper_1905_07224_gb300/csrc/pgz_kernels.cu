@@ -2,25 +2,22 @@
 // (Kerbiriou & Chikhi, arXiv 1905.07224, Section "Full file decompression in
 // two passes (pugz)").
 //
-//   k_pass1     pass 1, one warp per part from a work queue: the first bit
-//               of [lo, hi) where a DEFLATE block starts (Section "Detection
-//               of DEFLATE block start positions", Appendix "DEFLATE block
-//               decompression checks"): a warp tests 1024 bit offsets per step
-//               (one 32-bit window per lane, bit-parallel header tests),
-//               __ballot_sync + __ffs elect the lowest candidate, and the
-//               candidate's whole block is decoded as the final check -- into
-//               the part's own output.  The start is published, and the warp
-//               goes on with decode(C_i, w^_i) (Algorithm "DEFLATE
-//               decompression" with the symbolic context [U_0..U_32767]) up
-//               to the next part's block start.  The warp's lanes decode
+//   k_sync      pass 1a: per part, the first bit of [lo, hi) where a DEFLATE
+//               block starts (Section "Detection of DEFLATE block start
+//               positions", Appendix "DEFLATE block decompression checks"):
+//               a warp tests 1024 bit offsets per step (one 32-bit window per
+//               lane, bit-parallel header tests), __ballot_sync + __ffs elect
+//               the lowest candidate, and the candidate's whole block is then
+//               decoded as the final check -- into the part's own output, so
+//               pass 1 resumes after it.
+//   k_inflate   pass 1b: decode(C_i, w^_i) (Algorithm "DEFLATE decompression"
+//               with the symbolic context [U_0..U_32767]) up to the next
+//               part's block start.  One warp per part: the lanes decode
 //               segments of a block in parallel and meet (see par_block), then
 //               write the tokens' symbols cooperatively.  The 32 KiB window is
 //               the part's own u16 output in global memory; a source before
 //               the part start p < 0 is the placeholder U_{32768+p}, computed,
-//               not stored.  A part never waits for another: if the next
-//               part's start is not published when the decoding reaches that
-//               part's scan start, the part stops there;
-//   k_inflate   the finishing launch: those parts, up to their stop.
+//               not stored.
 //   k_plan      output offsets of the parts (prefix of their lengths), error
 //               aggregation, ISIZE and capacity checks.
 //   k_chain_*   pass 2a: w_{i+1} from w_i and the tail of D_i (Section "Full
@@ -873,7 +870,7 @@ __device__ __forceinline__ PassMasks build_pass(uint32_t* masks, const uint32_t*
 // (overlapping copies included, with no division).
 // PIPE: the passes are pipelined (the next pass's final sources copied
 // asynchronously while a pass resolves); else one pass at a time with direct
-// loads.  A part's first block always takes the second (the block-start search leaves fewer
+// loads.  k_sync always takes the second (its block-start search leaves fewer
 // registers); k_inflate takes either (KParams::pipe): which is faster depends
 // on the data (how far back the sources lie), so the autotuner can choose.
 template <bool PIPE>
@@ -1274,7 +1271,7 @@ __device__ int one_block(WarpSmem& S, uint32_t* tokbuf, BitIn& br, OutState& o, 
 //     from a 512-entry table of three-field sums;
 //  3. the whole dynamic header is valid (the checks of read_dynamic<true>),
 //     32 listed offsets at a time, one per lane (hdr_ok_lane).
-// The full block decode then follows in k_pass1, lowest offset first.  Stages
+// The full block decode then follows in k_sync, lowest offset first.  Stages
 // 1-3 are implied by the complete checks, so no offset that passes those is
 // dropped here.
 // ---------------------------------------------------------------------------
@@ -1514,11 +1511,9 @@ __device__ __forceinline__ int next_part(uint32_t* queue, int lane) {
 }
 
 // ---------------------------------------------------------------------------
-// k_pass1: block start of each part, its first block, then the rest of the part
+// k_sync: block start of each part and its first block; k_inflate: the rest of each part
 // ---------------------------------------------------------------------------
-// The block start of part c and its first block (Section "Detection of DEFLATE block start positions").  The
-// results go to C with the state written last, after a fence: a warp of the same launch that reads a state
-// other than CS_PENDING (with a volatile load, then a fence) reads this part's final start.
+// The block start of part c and its first block (Section "Detection of DEFLATE block start positions").
 __device__ void sync_part(const uint16_t* kraft3, WarpSmem& S, uint32_t* tok, const FileDesc& F, ChunkDesc& C,
                           uint16_t* symbuf, const KParams& p, int lane) {
     init_smem(S, p, lane);
@@ -1578,46 +1573,26 @@ __device__ void sync_part(const uint16_t* kraft3, WarpSmem& S, uint32_t* tok, co
         C.final = final && state == CS_FOUND;
         C.confirmed = (state == CS_FOUND && (o.known || C.given || final || p.confirm_blocks == 0)) ? 1u : 0u;
         C.end = resume;
-        __threadfence();
-        *reinterpret_cast<volatile uint32_t*>(&C.state) = state;
+        C.state = state;
     }
     __syncwarp();
 }
 
-// Where part c's decoding stops: the start of the next part that holds one.  With `launch` (the launch that
-// also searches the block starts), a later part whose search is not finished bounds the decoding instead:
-// *limit receives its scan start (its start, if it has one, lies at or after it), and the decoding may not
-// pass that bit until the search is known.  Parts merged into their predecessor hold no start.
-__device__ __forceinline__ void find_stop(const FileDesc& F, const ChunkDesc* chunks, int c, uint64_t stop_hint,
-                                          bool launch, uint64_t& stop, uint64_t& limit) {
-    stop = stop_hint;
-    limit = kNone;
+// Where part c's decoding stops: the start of the next part that holds one (`sync` is final after k_sync and
+// never written by k_inflate, whose other warps rewrite `state`); parts merged into their predecessor hold
+// none.
+__device__ __forceinline__ uint64_t find_stop(const FileDesc& F, const ChunkDesc* chunks, int c, uint64_t stop_hint) {
     for (int j = c + 1; j < F.chunk0 + F.nchunks; ++j) {
-        const ChunkDesc& J = chunks[j];
-        if (J.disabled) continue;
-        if (launch) {
-            const uint32_t st = *reinterpret_cast<const volatile uint32_t*>(&J.state);
-            if (st == CS_PENDING) {
-                limit = J.lo;
-                return;
-            }
-            __threadfence();
-        }
-        const uint64_t sj = *reinterpret_cast<const volatile uint64_t*>(&J.sync);
-        if (sj != kNone) {
-            stop = sj;
-            return;
-        }
+        const uint64_t sj = chunks[j].sync;
+        if (sj != kNone) return sj;
     }
+    return stop_hint;
 }
 
-// Pass 1 of part c from the end of its first block up to the next part's block start.  In the launch that
-// also searches block starts (`launch`), a part whose successor's search is not finished when the decoding
-// reaches that successor's scan start stops there, at a block boundary, and keeps its state CS_FOUND with
-// its progress (symbols, resume bit, blocks): the finishing launch (k_inflate) continues it.  No warp waits.
+// Pass 1 of part c from the end of its first block up to the next part's block start.
 template <bool PIPE>
 __device__ void inflate_part(WarpSmem& S, uint32_t* tok, const FileDesc* __restrict__ files, ChunkDesc* chunks, int c,
-                             uint16_t* symbuf, const KParams& p, int lane, bool launch) {
+                             uint16_t* symbuf, const KParams& p, int lane) {
     ChunkDesc& C = chunks[c];
     if (C.state != CS_FOUND) return;
     if (C.probe) {                    // a streamed segment's end: the block start found is all it gives
@@ -1634,20 +1609,15 @@ __device__ void inflate_part(WarpSmem& S, uint32_t* tok, const FileDesc* __restr
         return;
     }
     const FileDesc& F = files[C.file];
-    uint64_t stop, limit;
-    find_stop(F, chunks, c, C.stop_hint, launch, stop, limit);
+    const uint64_t stop = find_stop(F, chunks, c, C.stop_hint);
     OutState o{symbuf + C.sym_base, C.cap, C.n, C.index == 0 && C.sync == F.s0_bit, false};
     uint32_t blocks = C.blocks, final = C.final, err = CE_OK, confirmed = C.confirmed;
     uint64_t end = C.resume;
-    bool paused = false;
     // the confirmation (Section "Detection of DEFLATE block start positions") covers the start's block and
     // the confirm_blocks blocks after it; they are decoded with the literal checks
     const uint32_t window = (uint32_t)p.confirm_blocks + 1u;
     if (final) {
-        if (limit != kNone) paused = true;
-        else if (stop != kNone && !F.open_end) err = CE_CHAIN;
-    } else if (limit != kNone && C.resume >= limit) {
-        paused = true;
+        if (stop != kNone && !F.open_end) err = CE_CHAIN;
     } else if (!(stop != kNone && C.resume == stop) || (C.confirm_ext && !confirmed)) {
         init_smem(S, p, lane);
         BitIn br;
@@ -1660,13 +1630,6 @@ __device__ void inflate_part(WarpSmem& S, uint32_t* tok, const FileDesc* __restr
         uint64_t n_stop = 0, end_stop = 0;
         for (;;) {
             const uint64_t pos = br.pos();
-            if (!past && limit != kNone && pos >= limit) {        // a later part's search may have ended since
-                find_stop(F, chunks, c, C.stop_hint, launch, stop, limit);
-                if (limit != kNone && pos >= limit) {
-                    paused = true;
-                    break;
-                }
-            }
             if (!past && stop != kNone && pos >= stop) {
                 err_stop = pos != stop ? (uint32_t)CE_CHAIN : (uint32_t)CE_OK;
                 if (!C.confirm_ext || blocks >= window) {
@@ -1690,13 +1653,6 @@ __device__ void inflate_part(WarpSmem& S, uint32_t* tok, const FileDesc* __restr
                 if (blocks <= window) confirmed = 1;
                 if (past) break;
                 final = 1;
-                if (limit != kNone) {             // whether a later part holds a start decides CE_CHAIN
-                    find_stop(F, chunks, c, C.stop_hint, launch, stop, limit);
-                    if (limit != kNone) {         // not known yet: the finishing launch decides
-                        paused = true;
-                        break;
-                    }
-                }
                 if (stop != kNone && !F.open_end) err = CE_CHAIN;   // an open member may end before the next part
                 break;
             }
@@ -1712,19 +1668,6 @@ __device__ void inflate_part(WarpSmem& S, uint32_t* tok, const FileDesc* __restr
         }
     }
     const bool neg = __any_sync(FULL, o.neg);
-    if (paused) {                         // progress kept for the finishing launch; the state stays CS_FOUND
-        if (lane == 0) {
-            C.n = o.n;
-            C.resume = end;
-            C.end = end;
-            C.blocks = blocks;
-            C.final = final;
-            C.confirmed = confirmed;
-            C.anyph = C.anyph | (neg ? 1u : 0u);
-        }
-        __syncwarp();
-        return;
-    }
     if (err == CE_OK && final && F.mode != 2 && !F.open_end) {   // the trailer must follow the final block
         if (((end + 7) >> 3) + 8 != F.gz_len) err = CE_TRAIL;
     }
@@ -1741,12 +1684,11 @@ __device__ void inflate_part(WarpSmem& S, uint32_t* tok, const FileDesc* __restr
     __syncwarp();
 }
 
-// One launch of pass 1: every part's block start and first block, then the rest of the part (parts from
-// the work queue, one per warp at a time).
-template <int WPB, bool PIPE>
+// Work queue over the parts (one per warp at a time), for both kernels.
+template <int WPB>
 __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
-    k_pass1(const FileDesc* __restrict__ files, ChunkDesc* chunks, int nchunks, uint16_t* symbuf, uint32_t* tokbuf,
-            uint32_t* queue, const uint32_t* __restrict__ order, KParams p) {
+    k_sync(const FileDesc* __restrict__ files, ChunkDesc* chunks, int nchunks, uint16_t* symbuf, uint32_t* tokbuf,
+           uint32_t* queue, const uint32_t* __restrict__ order, KParams p) {
     __shared__ uint16_t kraft3[512];
     for (uint32_t v = threadIdx.x; v < 512; v += blockDim.x)
         kraft3[v] = (uint16_t)(kraft1(v & 7) + kraft1((v >> 3) & 7) + kraft1(v >> 6));
@@ -1758,13 +1700,10 @@ __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
         const int q = next_part(queue, lane);
         if (q >= nchunks) return;
         const int c = order ? (int)__ldg(order + q) : q;
-        ChunkDesc& C = chunks[c];
-        sync_part(kraft3, S, tok, files[C.file], C, symbuf, p, lane);
-        inflate_part<PIPE>(S, tok, files, chunks, c, symbuf, p, lane, true);
+        sync_part(kraft3, S, tok, files[chunks[c].file], chunks[c], symbuf, p, lane);
     }
 }
 
-// The finishing launch: the parts the first launch left at a later part's scan start, up to their stop.
 template <int WPB, bool PIPE>
 __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
     k_inflate(const FileDesc* __restrict__ files, ChunkDesc* chunks, int nchunks, uint16_t* symbuf, uint32_t* tokbuf,
@@ -1776,7 +1715,7 @@ __global__ void __launch_bounds__(32 * WPB, pass1_min_blocks(WPB))
         const int q = next_part(queue, lane);
         if (q >= nchunks) return;
         const int c = order ? (int)__ldg(order + q) : q;
-        inflate_part<PIPE>(S, tok, files, chunks, c, symbuf, p, lane, false);
+        inflate_part<PIPE>(S, tok, files, chunks, c, symbuf, p, lane);
     }
 }
 
@@ -2437,20 +2376,17 @@ static int pass1_resident_blocks_t() {
         const int smem = (int)(WPB * warp_smem_bytes());
         int sms = 0, per_sm_a = 0, per_sm_b = 0, per_sm_c = 0;
         const bool ok =
-            cudaFuncSetAttribute(k_pass1<WPB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
-                cudaSuccess &&
-            cudaFuncSetAttribute(k_pass1<WPB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
+            cudaFuncSetAttribute(k_sync<WPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
             cudaFuncSetAttribute(k_inflate<WPB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
                 cudaSuccess &&
             cudaFuncSetAttribute(k_inflate<WPB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, k_pass1<WPB, false>, 32 * WPB, smem) ==
-                cudaSuccess &&
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, k_pass1<WPB, true>, 32 * WPB, smem) ==
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, k_sync<WPB>, 32 * WPB, smem) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, k_inflate<WPB, true>, 32 * WPB, smem) ==
                 cudaSuccess &&
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_c, k_inflate<WPB, false>, 32 * WPB, smem) ==
                 cudaSuccess;
-        const int per_sm_sync = std::min(per_sm_a, per_sm_b), per_sm_inflate = per_sm_c;
+        const int per_sm_sync = per_sm_a, per_sm_inflate = std::min(per_sm_b, per_sm_c);
         const int v = std::max(1, sms) * std::max(1, std::min(per_sm_sync, per_sm_inflate));
         if (!ok) {
             cudaGetLastError();
@@ -2481,8 +2417,7 @@ static void launch_pass1_t(bool sync, const FileDesc* files, ChunkDesc* chunks, 
                          uint32_t* tok, uint32_t* queue, const uint32_t* order, const KParams& p, cudaStream_t s) {
     const int grid = pass1_warps(nchunks, WPB) / WPB;
     const size_t smem = WPB * warp_smem_bytes();
-    if (sync && p.pipe) k_pass1<WPB, true><<<grid, 32 * WPB, smem, s>>>(files, chunks, nchunks, sym, tok, queue, order, p);
-    else if (sync) k_pass1<WPB, false><<<grid, 32 * WPB, smem, s>>>(files, chunks, nchunks, sym, tok, queue, order, p);
+    if (sync) k_sync<WPB><<<grid, 32 * WPB, smem, s>>>(files, chunks, nchunks, sym, tok, queue, order, p);
     else if (p.pipe)
         k_inflate<WPB, true><<<grid, 32 * WPB, smem, s>>>(files, chunks, nchunks, sym, tok, queue, order, p);
     else k_inflate<WPB, false><<<grid, 32 * WPB, smem, s>>>(files, chunks, nchunks, sym, tok, queue, order, p);
@@ -2500,13 +2435,13 @@ static void launch_pass1_any(bool sync, const FileDesc* files, ChunkDesc* chunks
     }
 }
 
-void launch_pass1(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, uint32_t* tok,
-                  uint32_t* queue, const uint32_t* order, const KParams& p, cudaStream_t s) {
+void launch_sync(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, uint32_t* tok,
+                 uint32_t* queue, const uint32_t* order, const KParams& p, cudaStream_t s) {
     launch_pass1_any(true, files, chunks, nchunks, sym, tok, queue, order, p, s);
 }
 
-void launch_pass1_finish(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, uint32_t* tok,
-                         uint32_t* queue, const uint32_t* order, const KParams& p, cudaStream_t s) {
+void launch_inflate(const FileDesc* files, ChunkDesc* chunks, int nchunks, uint16_t* sym, uint32_t* tok,
+                    uint32_t* queue, const uint32_t* order, const KParams& p, cudaStream_t s) {
     launch_pass1_any(false, files, chunks, nchunks, sym, tok, queue, order, p, s);
 }
 

@@ -230,8 +230,8 @@ extern "C" int pgz_decompress_noalloc(const uint8_t* gz, uint64_t gz_len, uint8_
         cudaMemcpyAsync(d_gn, gn, ng * sizeof(int32_t), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(d_gfile, gfile, ng * sizeof(int32_t), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(d_seg0, &seg0, sizeof seg0, cudaMemcpyHostToDevice, s);
-        launch_pass1(d_files, d_chunks, (int)n, d_sym, d_tok, d_queue, nullptr, kp, s);
-        launch_pass1_finish(d_files, d_chunks, (int)n, d_sym, d_tok, d_queue + 1, nullptr, kp, s);
+        launch_sync(d_files, d_chunks, (int)n, d_sym, d_tok, d_queue, nullptr, kp, s);
+        launch_inflate(d_files, d_chunks, (int)n, d_sym, d_tok, d_queue + 1, nullptr, kp, s);
         launch_plan(d_files, d_chunks, 1, s);
         launch_chain(d_files, d_chunks, 1, ng, d_g0, d_gn, d_gfile, d_sym, d_gmaps, d_wstart, d_windows, s);
         launch_translate(d_files, d_chunks, (int)n, plan[0].cap, d_sym, d_windows, nullptr, s);
