@@ -78,6 +78,10 @@ typedef struct pgz_config {
     int exec_pipelined;         /* 1: pass 1 executes tokens in pipelined passes, 0: one pass at a time
                                    (default); which is faster depends on the data and the part size, and
                                    pgz_autotune can choose */
+    int determined_tail;        /* 1: once a part's last 32 KiB of output hold no placeholder (none can
+                                   follow), pass 1 stores the rest of the part as bytes and the translation
+                                   copies them; 0: u16 symbols throughout (default).  The output is the same
+                                   either way; which is faster depends on how soon placeholders die out */
 } pgz_config;
 
 /* per-call statistics; the ms_* fields are CUDA-event times of the stages */
@@ -90,6 +94,9 @@ typedef struct pgz_stats {
     uint64_t placeholders;      /* placeholder symbols produced by pass 1 */
     uint64_t symbols;           /* symbols produced by pass 1 (= out_bytes) */
     float ms_sync, ms_inflate, ms_chain, ms_translate, ms_crc, ms_total;
+    uint64_t determined;        /* symbols pass 1 stored as bytes: those after a point where the part's last
+                                   32 KiB of output held no placeholder (none can follow; Section
+                                   "Undetermined context propagation technique"), translated by a copy */
 } pgz_stats;
 
 /* One entry of a batch: device pointers; results are written back. */

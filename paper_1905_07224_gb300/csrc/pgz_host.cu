@@ -524,6 +524,7 @@ void reset_results(Plan& P) {
         C.state = CS_PENDING;
         C.err = 0;
         C.n = C.nph = C.last_ph = C.end = C.out_off = C.resume = 0;
+        C.det = kNone;
         C.blocks = C.final = 0;
     }
     for (auto& F : P.files) {
@@ -552,6 +553,7 @@ void fill_stats(pgz_ctx* ctx, const Plan& P, pgz_stats* st, uint64_t retries, ui
             if (res[c].state == CS_EMPTY) st->empty_chunks++;
             st->placeholders += res[c].nph;
             st->symbols += res[c].n;
+            if (res[c].state == CS_DONE && res[c].det < res[c].n) st->determined += res[c].n - res[c].det;
         }
     }
     if (timed) {
@@ -818,6 +820,7 @@ void add_stats(pgz_stats* acc, const pgz_stats& s) {
     acc->ms_translate += s.ms_translate;
     acc->ms_crc += s.ms_crc;
     acc->ms_total += s.ms_total;
+    acc->determined += s.determined;
 }
 
 // Every member of gz (device memory, 4-byte aligned), outputs concatenated in out (RFC 1952 2.2: a gzip
@@ -1131,6 +1134,7 @@ int pgz_create(pgz_ctx** out, const pgz_config* cfg) {
         cfg->warps_per_block != 8)
         return PGZ_E_ARG;
     if (cfg->exec_pipelined != 0 && cfg->exec_pipelined != 1) return PGZ_E_ARG;
+    if (cfg->determined_tail != 0 && cfg->determined_tail != 1) return PGZ_E_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) return PGZ_E_CUDA;
     if (cudaSetDevice(cfg->device) != cudaSuccess) return PGZ_E_CUDA;
@@ -1146,6 +1150,7 @@ int pgz_create(pgz_ctx** out, const pgz_config* cfg) {
     ctx->kp.confirm_blocks = cfg->confirm_blocks;
     ctx->kp.wpb = cfg->warps_per_block ? cfg->warps_per_block : 4;
     ctx->kp.pipe = cfg->exec_pipelined;
+    ctx->kp.tail = cfg->determined_tail;
     upload_crc_tables();
     for (int k = 0; k < 8; ++k) cudaEventCreate(&ctx->ev[k]);
     if (cudaGetLastError() != cudaSuccess) {
@@ -1597,9 +1602,17 @@ int pgz_inspect_symbols(pgz_ctx* ctx, int part, uint16_t* host_dst, uint64_t cap
     if (nsym) *nsym = n;
     if (!host_dst || n == 0) return PGZ_OK;
     if (cap < n) return PGZ_E_CAPACITY;
-    if (cudaMemcpy(host_dst, ctx->plan.d_sym.as<uint16_t>() + C.sym_base, n * sizeof(uint16_t),
-                   cudaMemcpyDeviceToHost) != cudaSuccess)
-        return PGZ_E_CUDA;
+    // u16 symbols before the determined tail; the tail's bytes (symbol k at byte det + k) widened
+    const uint64_t nw = C.det < n ? C.det : n;
+    const uint16_t* d = ctx->plan.d_sym.as<uint16_t>() + C.sym_base;
+    if (nw && cudaMemcpy(host_dst, d, nw * sizeof(uint16_t), cudaMemcpyDeviceToHost) != cudaSuccess) return PGZ_E_CUDA;
+    if (nw < n) {
+        std::vector<uint8_t> t((size_t)(n - nw));
+        if (cudaMemcpy(t.data(), reinterpret_cast<const uint8_t*>(d) + C.det + nw, n - nw, cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+            return PGZ_E_CUDA;
+        for (uint64_t k = nw; k < n; ++k) host_dst[k] = t[(size_t)(k - nw)];
+    }
     return PGZ_OK;
 }
 

@@ -41,7 +41,7 @@ struct KParams {
     int confirm_blocks;
     int wpb;               // warps per block of the pass-1 kernels: 2, 4 or 8 (0: 4)
     int pipe;              // k_inflate executes tokens in pipelined passes (1) or one pass at a time (0)
-    int pad;
+    int tail;              // k_inflate stores a part's determined tail as bytes (1) or keeps u16 symbols (0)
 };
 
 // one gzip member
@@ -95,7 +95,10 @@ struct ChunkDesc {
     uint64_t resume;       // bit after the first block
     uint64_t n;            // symbols produced
     uint64_t nph;          // placeholder symbols produced (counted by the translation)
-    uint64_t last_ph;      // one past the last placeholder symbol (idem)
+    uint64_t last_ph;      // one past the last placeholder symbol (pass 1 keeps it up to date; the statistics
+                           // kernel recounts it)
+    uint64_t det;          // the determined tail: symbols from det on are stored as bytes (u8 at byte offset
+                           // det + k of the part's buffer for symbol k), kNone if the part has no such tail
     uint64_t end;          // bit where pass 1 stopped
     uint64_t out_off;      // output offset of the part
     uint32_t state;

@@ -431,7 +431,15 @@ struct OutState {
     uint64_t n;        // symbols so far (uniform)
     bool known;        // the context before the part is empty (member start)
     bool neg;          // this lane copied from before the part start (a placeholder source)
+    // The determined tail (Section "Undetermined context propagation technique": a placeholder is only ever
+    // copied, so once the last 32 KiB of output hold none, no later symbol can be one): symbols from det on
+    // are stored as bytes, symbol k at byte det + k of the part's buffer (det is a multiple of 8, so a lane's
+    // 8 positions are all below it or all at or above it).  ~0: no tail yet.
+    uint32_t det = 0xffffffffu;
+    uint32_t last_ph = 0;   // at or after one past the last placeholder written (uniform; kept in kTrack mode)
 };
+
+__device__ __forceinline__ uint8_t* tail_bytes(const OutState& o) { return reinterpret_cast<uint8_t*>(o.sym) + o.det; }
 
 __device__ __forceinline__ void cp_async4(uint32_t dst_shared, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst_shared), "l"(src) : "memory");
@@ -444,6 +452,19 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // positions are 32-bit (a part holds fewer than 2^31 symbols).
 __device__ __forceinline__ uint16_t sym_at(const uint16_t* out, int32_t q) {
     return q >= 0 ? out[(uint32_t)q] : (uint16_t)(kPH | (uint32_t)((int32_t)kWin + q));
+}
+// the same with the determined tail: a position at or after o.det is a byte
+__device__ __forceinline__ uint16_t sym_get(const OutState& o, int32_t q) {
+    if (q >= 0 && (uint32_t)q >= o.det) return tail_bytes(o)[(uint32_t)q];
+    return sym_at(o.sym, q);
+}
+// an upper bound on one past the part's last placeholder: the end of any pass of 256 positions (from A) that
+// wrote one (uniform)
+__device__ __forceinline__ void track_placeholders(OutState& o, const uint32_t* e, uint32_t A, uint32_t end) {
+    uint32_t any = 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) any |= e[u];
+    if (__any_sync(0xffffffffu, (any & kPH) != 0)) o.last_ph = max(o.last_ph, min(A + 256u, end));
 }
 
 // Writes the symbols of a batch of tokens (lane t holds token t < ntok):
@@ -798,15 +819,17 @@ constexpr uint32_t kEntryRes = 0x10000u, kEntryCross = 0x20000u;
 struct PassMasks {
     uint32_t am, hm, cm, om;   // bit u: async copy, its upper half, cross entry, open in-pass pointer
     uint32_t neg;              // a source lies before the part start (a placeholder)
+    uint32_t bm, bx;           // bit u: the async copy holds a tail byte; bits 2u, 2u+1: its byte in the word
 };
 
 // The entries of the pass at A (positions A + 8 lane .. + 7) into stage buffer
 // b; positions before fin are final in the part's output and are copied
 // asynchronously into their entries (the 32-bit word holding the symbol).
+template <bool TAIL>
 __device__ __forceinline__ PassMasks build_pass(uint32_t* masks, const uint32_t* tokS, const uint32_t* stS,
                                                 uint32_t ntok, uint32_t base, uint32_t end, const uint16_t* out,
-                                                uint32_t A, uint32_t fin, int b, int lane) {
-    PassMasks m{0, 0, 0, 0, 0};
+                                                uint32_t det, uint32_t A, uint32_t fin, int b, int lane) {
+    PassMasks m{0, 0, 0, 0, 0, 0, 0};
     uint32_t* buf = masks + 256 * b;
     const uint32_t p0 = A + 8u * (uint32_t)lane;
     if (!(p0 + 8u > base && p0 < end)) {
@@ -847,9 +870,16 @@ __device__ __forceinline__ PassMasks build_pass(uint32_t* masks, const uint32_t*
             m.neg = 1;
             buf[slot] = kEntryRes | sym_at(out, src);
         } else if ((uint32_t)src < fin) {                  // final: copy its word into the entry
-            cp_async4(sh + 4u * slot, reinterpret_cast<const uint32_t*>(out) + ((uint32_t)src >> 1));
+            if (TAIL && (uint32_t)src >= det) {            // a byte of the determined tail
+                const uint32_t bo = det + (uint32_t)src;
+                cp_async4(sh + 4u * slot, reinterpret_cast<const uint8_t*>(out) + (bo & ~3u));
+                m.bm |= 1u << u;
+                m.bx |= (bo & 3u) << (2 * u);
+            } else {
+                cp_async4(sh + 4u * slot, reinterpret_cast<const uint32_t*>(out) + ((uint32_t)src >> 1));
+                m.hm |= ((uint32_t)src & 1u) << u;
+            }
             m.am |= 1u << u;
-            m.hm |= ((uint32_t)src & 1u) << u;
         } else if ((uint32_t)src < A) {                    // inside the previous pass
             buf[slot] = kEntryCross | ((uint32_t)src - (A - 256u));
             m.cm |= 1u << u;
@@ -859,6 +889,49 @@ __device__ __forceinline__ PassMasks build_pass(uint32_t* masks, const uint32_t*
         }
     }
     return m;
+}
+
+// Execution modes of a part's blocks: kPlain, u16 symbols only (no tail); kTrack, the same while keeping
+// an upper bound on the part's last placeholder (the tail may start later); kTail, the determined tail has
+// started (positions at or after OutState::det are bytes).  Separate instantiations keep the tail's checks
+// out of the plain decoding loop.
+enum : int { kPlain = 0, kTrack = 1, kTail = 2 };
+
+// A lane's 8 resolved entries (positions p0 .. p0 + 7; the low 16 bits are the symbols) into the part's
+// output, the positions inside [base, end) only: one 16-byte store of u16 symbols, or one 8-byte store of
+// bytes in the determined tail.
+template <bool TAIL>
+__device__ __forceinline__ void store8(const OutState& o, uint16_t* out, const uint32_t* e, uint32_t p0, uint32_t base,
+                                       uint32_t end) {
+    const bool all = p0 >= base && p0 + 8u <= end;
+    if (TAIL && p0 >= o.det) {
+        uint8_t* t = tail_bytes(o);
+        if (all) {
+            uint2 v;
+            v.x = (e[0] & 0xffu) | ((e[1] & 0xffu) << 8) | ((e[2] & 0xffu) << 16) | (e[3] << 24);
+            v.y = (e[4] & 0xffu) | ((e[5] & 0xffu) << 8) | ((e[6] & 0xffu) << 16) | (e[7] << 24);
+            *reinterpret_cast<uint2*>(t + p0) = v;
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t P = p0 + (uint32_t)u;
+                if (P >= base && P < end) t[P] = (uint8_t)e[u];
+            }
+        }
+    } else if (all) {
+        uint4 v;
+        v.x = (e[0] & 0xffffu) | (e[1] << 16);
+        v.y = (e[2] & 0xffffu) | (e[3] << 16);
+        v.z = (e[4] & 0xffffu) | (e[5] << 16);
+        v.w = (e[6] & 0xffffu) | (e[7] << 16);
+        *reinterpret_cast<uint4*>(out + p0) = v;
+    } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const uint32_t P = p0 + (uint32_t)u;
+            if (P >= base && P < end) out[P] = (uint16_t)e[u];
+        }
+    }
 }
 
 // Writes up to 256 consecutive tokens of the block (lane j loads tokens
@@ -873,7 +946,7 @@ __device__ __forceinline__ PassMasks build_pass(uint32_t* masks, const uint32_t*
 // loads.  k_sync always takes the second (its block-start search leaves fewer
 // registers); k_inflate takes either (KParams::pipe): which is faster depends
 // on the data (how far back the sources lie), so the autotuner can choose.
-template <bool PIPE>
+template <bool PIPE, int MODE>
 __device__ __forceinline__ int exec_range(WarpSmem& S, OutState& o, const uint32_t* tks, uint32_t ntok, bool check,
                                           uint64_t& block_n, int lane) {
     uint32_t t[8], L[8], sum = 0;
@@ -914,8 +987,11 @@ __device__ __forceinline__ int exec_range(WarpSmem& S, OutState& o, const uint32
             // a match's source before the batch is final already: bring its line toward L2 now, so the
             // passes below find it there
             const int32_t src = (int32_t)(base + s0) - (int32_t)((t[i] & 0xffffu) + 1u);
-            if ((t[i] >> 31) && src >= 0 && (uint32_t)src < base)
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(out + src));
+            if ((t[i] >> 31) && src >= 0 && (uint32_t)src < base) {
+                const void* a = (MODE == kTail && (uint32_t)src >= o.det) ? (const void*)(tail_bytes(o) + src)
+                                                                         : (const void*)(out + src);
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+            }
         }
         s0 += L[i];
     }
@@ -934,14 +1010,17 @@ __device__ __forceinline__ int exec_range(WarpSmem& S, OutState& o, const uint32
     constexpr uint32_t kRes = kEntryRes;
     int cur = 0;
     uint32_t A = base & ~7u;
-    PassMasks m = build_pass(S.masks, tokS, stS, ntok, base, end, out, A, base, cur, lane);
+    const uint32_t det = o.det;
+    PassMasks m = build_pass<MODE == kTail>(S.masks, tokS, stS, ntok, base, end, out, det, A, base, cur, lane);
     uint32_t neg = m.neg;
     cp_async_commit();
     for (;;) {
         const uint32_t A1 = A + 256u;
         const bool more = A1 < end;
-        PassMasks m1{0, 0, 0, 0, 0};
-        if (more) m1 = build_pass(S.masks, tokS, stS, ntok, base, end, out, A1, A > base ? A : base, cur ^ 1, lane);
+        PassMasks m1{0, 0, 0, 0, 0, 0, 0};
+        if (more)
+            m1 = build_pass<MODE == kTail>(S.masks, tokS, stS, ntok, base, end, out, det, A1, A > base ? A : base,
+                                           cur ^ 1, lane);
         neg |= m1.neg;
         cp_async_commit();
         cp_async_wait<1>();                                // this pass's copies (this lane's) have landed
@@ -951,7 +1030,10 @@ __device__ __forceinline__ int exec_range(WarpSmem& S, OutState& o, const uint32
         for (int u = 0; u < 8; ++u)
             if ((m.am >> u) & 1u) {
                 const uint32_t w = buf[8u * lane + u];
-                buf[8u * lane + u] = kRes | (((m.hm >> u) & 1u) ? (w >> 16) : (w & 0xffffu));
+                const uint32_t v = (MODE == kTail && ((m.bm >> u) & 1u))
+                                       ? ((w >> (8u * ((m.bx >> (2 * u)) & 3u))) & 0xffu)
+                                       : (((m.hm >> u) & 1u) ? (w >> 16) : (w & 0xffffu));
+                buf[8u * lane + u] = kRes | v;
             }
         __syncwarp();
         uint32_t e[8];
@@ -976,20 +1058,8 @@ __device__ __forceinline__ int exec_range(WarpSmem& S, OutState& o, const uint32
             for (int u = 0; u < 8; ++u)
                 if ((m1.cm >> u) & 1u) nb[8u * lane + u] = buf[nb[8u * lane + u] & 0xffu];
         }
-        if (p0 >= base && p0 + 8u <= end) {                // all 8 mine: one 16-byte store
-            uint4 v;
-            v.x = (e[0] & 0xffffu) | (e[1] << 16);
-            v.y = (e[2] & 0xffffu) | (e[3] << 16);
-            v.z = (e[4] & 0xffffu) | (e[5] << 16);
-            v.w = (e[6] & 0xffffu) | (e[7] << 16);
-            *reinterpret_cast<uint4*>(out + p0) = v;
-        } else {
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const uint32_t P = p0 + (uint32_t)u;
-                if (P >= base && P < end) out[P] = (uint16_t)e[u];
-            }
-        }
+        store8<MODE == kTail>(o, out, e, p0, base, end);
+        if (MODE == kTrack) track_placeholders(o, e, A, end);
         __syncwarp();                                      // this pass is final; its buffer may be reused
         if (!more) break;
         A = A1;
@@ -1044,7 +1114,7 @@ __device__ __forceinline__ int exec_range(WarpSmem& S, OutState& o, const uint32
                         if (o.known) bad = true;
                         o.neg = true;
                     }
-                    e[u] = 0x10000u | sym_at(out, src);
+                    e[u] = 0x10000u | (MODE == kTail ? sym_get(o, src) : sym_at(out, src));
                 } else {
                     e[u] = (uint32_t)src - A;
                     open |= 1u << u;
@@ -1069,20 +1139,8 @@ __device__ __forceinline__ int exec_range(WarpSmem& S, OutState& o, const uint32
                 }
             __syncwarp();
         }
-        if (p0 >= base && p0 + 8u <= end) {                // all 8 mine: one 16-byte store
-            uint4 v;
-            v.x = (e[0] & 0xffffu) | (e[1] << 16);
-            v.y = (e[2] & 0xffffu) | (e[3] << 16);
-            v.z = (e[4] & 0xffffu) | (e[5] << 16);
-            v.w = (e[6] & 0xffffu) | (e[7] << 16);
-            *reinterpret_cast<uint4*>(out + p0) = v;
-        } else {
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const uint32_t P = p0 + (uint32_t)u;
-                if (P >= base && P < end) out[P] = (uint16_t)e[u];
-            }
-        }
+        store8<MODE == kTail>(o, out, e, p0, base, end);
+        if (MODE == kTrack) track_placeholders(o, e, A, end);
         __syncwarp();                                      // this pass is final for the next one
     }
     }
@@ -1092,7 +1150,7 @@ __device__ __forceinline__ int exec_range(WarpSmem& S, OutState& o, const uint32
     return CE_OK;
 }
 
-template <bool PIPE>
+template <bool PIPE, int MODE>
 __device__ int par_block(WarpSmem& S, uint32_t* tokbuf, BitIn& br, OutState& o, bool check, uint64_t max_block,
                          uint64_t end_bit, uint64_t& block_n, int lane) {
     uint32_t* tb = tokbuf + (uint64_t)lane * kTokCap;
@@ -1181,7 +1239,7 @@ __device__ int par_block(WarpSmem& S, uint32_t* tokbuf, BitIn& br, OutState& o, 
             const uint32_t vs = __shfl_sync(FULL, my_vs, k), ve = __shfl_sync(FULL, my_ve, k);
             const uint32_t* rng = tokbuf + (uint64_t)k * kTokCap;
             for (uint32_t x = vs; x < ve; x += 256) {
-                const int e = exec_range<PIPE>(S, o, rng + x, ve - x < 256 ? ve - x : 256, check, block_n, lane);
+                const int e = exec_range<PIPE, MODE>(S, o, rng + x, ve - x < 256 ? ve - x : 256, check, block_n, lane);
                 if (e) return e;
                 if (max_block && block_n >= max_block) return CE_SIZE;
             }
@@ -1208,7 +1266,9 @@ __device__ int stored_block(BitIn& br, OutState& o, bool check, const uint32_t* 
     for (uint32_t j = lane; j < len; j += 32) {
         const uint32_t v = __ldg(g + byte + 4 + j);
         if (check && !allowed_has(allowed, v)) bad = true;
-        o.sym[o.n + j] = (uint16_t)v;
+        const uint64_t P = o.n + j;
+        if (P >= o.det) tail_bytes(o)[P] = (uint8_t)v;
+        else o.sym[P] = (uint16_t)v;
     }
     if (__any_sync(FULL, bad)) return CE_BYTE;
     o.n += len;
@@ -1223,7 +1283,7 @@ __device__ int stored_block(BitIn& br, OutState& o, bool check, const uint32_t* 
 // be allowed bytes.  Huffman blocks are decoded by the whole warp in parallel
 // (par_block); a candidate block start first runs a short serial prefix, so
 // that false candidates fail after a few tokens.
-template <bool PIPE>
+template <bool PIPE, int MODE = kPlain>
 __device__ int one_block(WarpSmem& S, uint32_t* tokbuf, BitIn& br, OutState& o, bool check, uint64_t min_block,
                          uint64_t max_block, bool candidate, uint64_t end_bit, uint32_t& final, int lane) {
     br.refill();
@@ -1254,7 +1314,7 @@ __device__ int one_block(WarpSmem& S, uint32_t* tokbuf, BitIn& br, OutState& o, 
             st = st == CE_MORE ? CE_MORE : (st == CE_OK ? CE_OK + 1000 : st);
         }
         if (st == CE_OK || st == CE_MORE)
-            st = par_block<PIPE>(S, tokbuf, br, o, check, max_block, end_bit, block_n, lane);
+            st = par_block<PIPE, MODE>(S, tokbuf, br, o, check, max_block, end_bit, block_n, lane);
         else if (st == CE_OK + 1000)
             st = CE_OK;
     }
@@ -1567,7 +1627,9 @@ __device__ void sync_part(const uint16_t* kraft3, WarpSmem& S, uint32_t* tok, co
         C.resume = resume;
         C.n = state == CS_FOUND ? o.n : 0;
         C.nph = 0;
-        C.last_ph = 0;
+        // a bound on one past the last placeholder: the first block's end (the member start has none)
+        C.last_ph = (state == CS_FOUND && !o.known) ? o.n : 0;
+        C.det = kNone;
         C.anyph = neg && state == CS_FOUND;
         C.blocks = state == CS_FOUND ? 1u : 0u;
         C.final = final && state == CS_FOUND;
@@ -1611,6 +1673,11 @@ __device__ void inflate_part(WarpSmem& S, uint32_t* tok, const FileDesc* __restr
     const FileDesc& F = files[C.file];
     const uint64_t stop = find_stop(F, chunks, c, C.stop_hint);
     OutState o{symbuf + C.sym_base, C.cap, C.n, C.index == 0 && C.sync == F.s0_bit, false};
+    o.det = C.det == kNone ? 0xffffffffu : (uint32_t)C.det;
+    o.last_ph = (uint32_t)C.last_ph;
+    // the determined tail when the configuration asks for it; decoding from a bit offset keeps every symbol
+    // as u16 (its caller asks for the symbols themselves)
+    const bool tail_ok = p.tail && F.mode != 1;
     uint32_t blocks = C.blocks, final = C.final, err = CE_OK, confirmed = C.confirmed;
     uint64_t end = C.resume;
     // the confirmation (Section "Detection of DEFLATE block start positions") covers the start's block and
@@ -1641,9 +1708,15 @@ __device__ void inflate_part(WarpSmem& S, uint32_t* tok, const FileDesc* __restr
                 end_stop = pos;
             }
             if (past && blocks >= window) break;
+            // no placeholder among the last 32 KiB: none can follow; the rest goes out as bytes
+            if (tail_ok && !past && o.det == 0xffffffffu && o.n >= (uint64_t)o.last_ph + kWin)
+                o.det = (uint32_t)((o.n + 7) & ~7ull);
             const bool check = !o.known && blocks < window;
             uint32_t fin = 0;
-            const int st = one_block<PIPE>(S, tok, br, o, check, 0, 0, false, F.end_bit, fin, lane);
+            int st;
+            if (!tail_ok) st = one_block<PIPE, kPlain>(S, tok, br, o, check, 0, 0, false, F.end_bit, fin, lane);
+            else if (o.det != 0xffffffffu) st = one_block<PIPE, kTail>(S, tok, br, o, check, 0, 0, false, F.end_bit, fin, lane);
+            else st = one_block<PIPE, kTrack>(S, tok, br, o, check, 0, 0, false, F.end_bit, fin, lane);
             if (st) {
                 err = (check && st != CE_OVERFLOW) ? (uint32_t)CE_CONFIRM : (uint32_t)st;
                 break;
@@ -1680,6 +1753,8 @@ __device__ void inflate_part(WarpSmem& S, uint32_t* tok, const FileDesc* __restr
         C.final = final;
         C.confirmed = confirmed;
         C.end = end;
+        C.last_ph = o.last_ph;
+        C.det = o.det < o.n ? (uint64_t)o.det : kNone;
     }
     __syncwarp();
 }
@@ -1810,9 +1885,10 @@ __global__ void __launch_bounds__(1024) k_plan(FileDesc* files, ChunkDesc* chunk
 // map of part c: entry k of w_{c+1} is D_c[n-32768+k] if that exists (a byte
 // or U_j -> w_c[j]), else w_c[k+n]
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint16_t map_entry(const uint16_t* d, uint64_t n, uint32_t k) {
+__device__ __forceinline__ uint16_t map_entry(const uint16_t* d, uint64_t n, uint64_t det, uint32_t k) {
     const int64_t t = (int64_t)n - (int64_t)kWin + (int64_t)k;
-    return t >= 0 ? d[t] : (uint16_t)(kPH | (uint32_t)(k + n));
+    if (t < 0) return (uint16_t)(kPH | (uint32_t)(k + n));
+    return (uint64_t)t >= det ? reinterpret_cast<const uint8_t*>(d)[det + (uint64_t)t] : d[t];   // det: the tail
 }
 
 // Every thread handles entries tid + 1024*j; eight loads are in flight at once.
@@ -1835,7 +1911,7 @@ __global__ void __launch_bounds__(1024) k_chain_compose(const FileDesc* __restri
         for (uint32_t j0 = 0; j0 < kWin / 1024; j0 += 8) {
             uint16_t m[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) m[u] = map_entry(d, n, tid + 1024u * (j0 + u));
+            for (int u = 0; u < 8; ++u) m[u] = map_entry(d, n, C.det, tid + 1024u * (j0 + u));
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 uint16_t e = m[u];
@@ -1909,7 +1985,7 @@ __global__ void __launch_bounds__(1024) k_chain_expand(const FileDesc* __restric
         for (uint32_t j0 = 0; j0 < kWin / 1024; j0 += 8) {
             uint16_t m[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) m[u] = map_entry(d, n, tid + 1024u * (j0 + u));
+            for (int u = 0; u < 8; ++u) m[u] = map_entry(d, n, C.det, tid + 1024u * (j0 + u));
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const uint16_t e = m[u];
@@ -1982,6 +2058,12 @@ __device__ __forceinline__ uint64_t translate8(const uint8_t* T, uint4 q, uint32
     return (uint64_t)b0 | ((uint64_t)b1 << 32);
 }
 
+// 8 bytes of the determined tail as they are (bytes past nv taken as 0)
+__device__ __forceinline__ uint64_t tail8(uint4 q, uint32_t nv) {
+    const uint64_t v = (uint64_t)q.x | ((uint64_t)q.y << 32);
+    return nv >= 8 ? v : (nv ? v & (~0ull >> (64 - 8 * nv)) : 0ull);
+}
+
 __global__ void __launch_bounds__(kTransThreads, 2) k_translate(const FileDesc* __restrict__ files, ChunkDesc* chunks,
                                                                 int nchunks, const uint16_t* __restrict__ sym,
                                                                 const uint8_t* __restrict__ windows,
@@ -2024,11 +2106,25 @@ __global__ void __launch_bounds__(kTransThreads, 2) k_translate(const FileDesc* 
         const uint32_t n32 = (uint32_t)C.n;
         const uint32_t nsl = (n32 + kTransSlice - 1) / kTransSlice, per = (nsl + nwarp - 1) / nwarp;
         const uint32_t j0 = min(nsl, per * (uint32_t)warp), j1 = min(nsl, per * (uint32_t)(warp + 1));
+        // the determined tail (symbols from det32 on are bytes at byte det32 + k; det32 is a multiple of 8, so
+        // each 8-symbol half lies wholly before or wholly inside it): copied, not translated
+        const uint32_t det32 = C.det < (uint64_t)n32 ? (uint32_t)C.det : 0xffffffffu;
+        const uint8_t* tb = reinterpret_cast<const uint8_t*>(s) + (det32 == 0xffffffffu ? 0u : det32);
+        auto load_half = [&](uint32_t j, uint32_t i0, uint4& a) {
+            if (!(j < j1 && i0 < n32)) {
+                a = make_uint4(0, 0, 0, 0);
+            } else if (i0 >= det32) {
+                const uint2 v = *reinterpret_cast<const uint2*>(tb + i0);
+                a = make_uint4(v.x, v.y, 0, 0);
+            } else {
+                a = *reinterpret_cast<const uint4*>(s + i0);
+            }
+        };
         // loads of slice j + 1 are in flight while slice j is translated
         auto load = [&](uint32_t j, uint4& a, uint4& b) {
             const uint32_t i = j * kTransSlice + 16u * (uint32_t)lane;
-            a = (j < j1 && i < n32) ? *reinterpret_cast<const uint4*>(s + i) : make_uint4(0, 0, 0, 0);
-            b = (j < j1 && i + 8 < n32) ? *reinterpret_cast<const uint4*>(s + i + 8) : make_uint4(0, 0, 0, 0);
+            load_half(j, i, a);
+            load_half(j, i + 8, b);
         };
         uint4 n0, n1;
         load(j0, n0, n1);
@@ -2039,8 +2135,9 @@ __global__ void __launch_bounds__(kTransThreads, 2) k_translate(const FileDesc* 
             const uint32_t i = j * kTransSlice + 16u * (uint32_t)lane;
             const bool full = (j + 1) * kTransSlice <= n32;   // uniform: every lane holds 16 symbols
             const uint32_t nv = full ? 16u : (i < n32 ? min(n32 - i, 16u) : 0u);
-            const uint64_t v0 = translate8(W, q0, nv < 8 ? nv : 8u, ph);
-            const uint64_t v1 = translate8(W, q1, nv > 8 ? nv - 8 : 0u, ph);
+            const uint64_t v0 = i >= det32 ? tail8(q0, nv < 8 ? nv : 8u) : translate8(W, q0, nv < 8 ? nv : 8u, ph);
+            const uint64_t v1 = i + 8 >= det32 ? tail8(q1, nv > 8 ? nv - 8 : 0u)
+                                               : translate8(W, q1, nv > 8 ? nv - 8 : 0u, ph);
             const uint64_t P = C.out_off + i;
             if (!vec || !full) {          // each lane stores its own bytes (clipped to [lo, hi) when !vec)
                 for (uint32_t k = 0; k < nv; ++k) {
@@ -2090,7 +2187,8 @@ __global__ void __launch_bounds__(256) k_count_ph(ChunkDesc* chunks, int nchunks
             s_last = 0;
         }
         __syncthreads();
-        const uint64_t n = C.state == CS_DONE ? C.n : 0;
+        const uint64_t n0 = C.state == CS_DONE ? C.n : 0;
+        const uint64_t n = n0 < C.det ? n0 : C.det;        // a determined tail holds no placeholder
         const uint16_t* p = sym + C.sym_base;
         unsigned long long cnt = 0, last = 0;
         for (uint64_t i = threadIdx.x; i < n; i += blockDim.x)

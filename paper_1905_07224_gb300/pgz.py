@@ -31,14 +31,15 @@ class pgz_config(ctypes.Structure):
                 ("threads_per_chunk", ctypes.c_int), ("allowed", ctypes.c_uint8 * 32),
                 ("confirm_blocks", ctypes.c_int), ("min_block", ctypes.c_uint32), ("max_block", ctypes.c_uint32),
                 ("dev_mem_budget", U64), ("spin_cap", U64), ("warps_per_block", ctypes.c_int),
-                ("exec_pipelined", ctypes.c_int)]
+                ("exec_pipelined", ctypes.c_int), ("determined_tail", ctypes.c_int)]
 
 
 class pgz_stats(ctypes.Structure):
     _fields_ = [("in_bytes", U64), ("out_bytes", U64), ("chunks", U64), ("empty_chunks", U64),
                 ("false_syncs", U64), ("retries", U64), ("placeholders", U64), ("symbols", U64),
                 ("ms_sync", ctypes.c_float), ("ms_inflate", ctypes.c_float), ("ms_chain", ctypes.c_float),
-                ("ms_translate", ctypes.c_float), ("ms_crc", ctypes.c_float), ("ms_total", ctypes.c_float)]
+                ("ms_translate", ctypes.c_float), ("ms_crc", ctypes.c_float), ("ms_total", ctypes.c_float),
+                ("determined", U64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

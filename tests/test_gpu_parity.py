@@ -84,18 +84,67 @@ def test_part_counts(cfg1, nparts):
         ctx.close()
 
 
+@pytest.mark.parametrize("tail", [0, 1])
 @pytest.mark.parametrize("pipe", [0, 1])
 @pytest.mark.parametrize("level", [1, 6, 9])
 @pytest.mark.parametrize("kind", ["fastq", "markov"])
-def test_levels_and_kinds(level, kind, pipe):
+def test_levels_and_kinds(level, kind, pipe, tail):
     data = synth.fastq(3 << 20, 150, 0.01, 5) if kind == "fastq" else synth.markov(3 << 20, 6)
     gz = synth.gzip_compress(data, level)
-    ctx = Ctx(n_chunks=24, exec_pipelined=pipe)
+    ctx = Ctx(n_chunks=24, exec_pipelined=pipe, determined_tail=tail)
     try:
         st, out, n, _ = ctx.decompress(gz)
         assert st == 0, ctx.pgz.pgz_strerror(st)
         assert out == data
         _check_parts(ctx, data, gz, 24)
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("pipe", [0, 1])
+@pytest.mark.parametrize("kind,level", [("markov", 6), ("markov", 1), ("fastq", 9)])
+def test_determined_tail(kind, level, pipe):
+    """Once a part's last 32 KiB of output hold no placeholder, none can follow (Section "Undetermined context
+    propagation technique"), and pass 1 (with the determined_tail option) stores the rest of the part as bytes.  The pass-1 symbols read back
+    through the inspection call equal the oracle's symbolic decode, the windows and the output are exact, and
+    the count of symbols stored as bytes is at most each part's symbols past its last placeholder plus
+    32 KiB (positive for Markov text, whose matches rarely reach back to a part's start).  Byte ranges through
+    the index read the tails too."""
+    data = synth.markov(6 << 20, 41) if kind == "markov" else synth.fastq(6 << 20, 150, 0.001, 41)
+    gz = synth.gzip_compress(data, level)
+    n = 12
+    ctx = Ctx(n_chunks=n, exec_pipelined=pipe, determined_tail=1)
+    try:
+        st, out, _, s = ctx.decompress(gz, stats=True)
+        assert st == 0, ctx.pgz.pgz_strerror(st)
+        assert out == data
+        _check_parts(ctx, data, gz, n)
+        ref = oracle.two_pass(gz, n)
+        bits = [int(b) for b in ref["part_bits"]]
+        used = [i for i, b in enumerate(bits) if b != oracle.NONE]
+        end = (len(gz) - 8) * 8
+        bound = 0
+        for k, i in enumerate(used):
+            stop = bits[used[k + 1]] if k + 1 < len(used) else 0
+            sym = oracle.inflate_from(gz, end, bits[i], stop, known=(i == 0))["sym"]
+            ph = np.nonzero(sym & 0x8000)[0]
+            last = int(ph[-1]) + 1 if ph.size else 0
+            bound += max(0, sym.size - (last + 32768))
+        assert s["determined"] <= bound
+        if kind == "markov":
+            assert s["determined"] > 0
+        P = ctx.pgz
+        d = to_device(gz)
+        idx = P.pgz_index_build(ctx.h, d.data_ptr(), len(gz))
+        try:
+            rng = np.random.default_rng(level + 10 * pipe)
+            for off, ln in [(0, len(data)), (len(data) - 5000, 5000)] + \
+                    [(int(o), 200000) for o in rng.integers(0, len(data) - 200000, 6)]:
+                o = empty(ln)
+                assert P.pgz_decompress_range(ctx.h, idx, off, ln, o.data_ptr()) == 0
+                assert o[:ln].cpu().numpy().tobytes() == data[off:off + ln], (off, ln)
+        finally:
+            P.pgz_index_free(idx)
     finally:
         ctx.close()
 
