@@ -57,20 +57,18 @@ TUNE_CHUNKS_BATCH = [128 << 10, 256 << 10, 512 << 10]   # the autotuner's part s
                                                         # (and the sizes of 1-4 whole waves of pass-1 warps)
 TUNE_WPB_BATCH = [2, 4]
 SERVED_REQUESTS = 240         # requests per offered load in the default run (the full served run uses 2000)
-# DRAM bytes (read + write) of pass 1 (k_sync + k_inflate) per decompressed byte on this workload's batched
-# run, by (part size, warps per block, pipelined execution): ncu captures of the configurations the autotuner
-# picks here (profiles/pass1_traffic_fastq256_batched.md).  A configuration without a capture reports null.
-# The same for the 512-member batch, by the configuration the autotuner picks there (empty: no capture yet).
-PASS1_TRAFFIC_PER_OUT_BYTE_BATCH512 = {}
+# DRAM bytes (read + write) of pass 1 (k_sync + k_inflate) per decompressed byte, from one-pass ncu captures
+# of the current kernels.  The two 256 MiB FASTQ files as one batch, by (part size, warps per block, pipelined
+# execution) (profiles/pass1_traffic_fastq256.md) ...
 PASS1_TRAFFIC_PER_OUT_BYTE = {
-    (65536, 2, 0): 5.0866e9 / 536870912,
-    (65536, 2, 1): 5.0049e9 / 536870912,
-    (65536, 4, 0): 5.0821e9 / 536870912,
-    (65536, 4, 1): 5.0035e9 / 536870912,
-    (131072, 4, 0): 4.4942e9 / 536870912,
-    (131072, 4, 1): 4.3808e9 / 536870912,
-    (131072, 8, 0): 4.4814e9 / 536870912,
-    (131072, 8, 1): 4.3636e9 / 536870912,
+    (88162, 2, 0): (0.8541e9 + 0.5243e9 + 3.0353e9 + 1.3165e9) / 536870912,
+    (88162, 4, 0): (0.8526e9 + 0.5236e9 + 3.0376e9 + 1.3172e9) / 536870912,
+}
+# ... and the 512-member batch, by (part size, warps per block, pipelined execution, determined tail)
+# (profiles/pass1_traffic_batch512.md).  Other configurations report null.
+PASS1_TRAFFIC_PER_OUT_BYTE_BATCH512 = {
+    (499078, 4, 0, 0): (0.965091840e9 + 0.952751872e9 + 39.928896000e9 + 23.369684224e9) / 4467581835,
+    (499078, 2, 0, 0): (0.9631e9 + 0.9521e9 + 39.9500e9 + 23.3771e9) / 4467581835,
 }
 
 
