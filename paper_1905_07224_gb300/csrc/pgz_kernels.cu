@@ -436,7 +436,7 @@ struct OutState {
     // are stored as bytes, symbol k at byte det + k of the part's buffer (det is a multiple of 8, so a lane's
     // 8 positions are all below it or all at or above it).  ~0: no tail yet.
     uint32_t det = 0xffffffffu;
-    uint32_t last_ph = 0;   // at or after one past the last placeholder written (uniform; kept in kTrack mode)
+    uint32_t last_ph = 0;   // at or after one past the last placeholder written (uniform; kept in kTail mode)
 };
 
 __device__ __forceinline__ uint8_t* tail_bytes(const OutState& o) { return reinterpret_cast<uint8_t*>(o.sym) + o.det; }
@@ -891,11 +891,11 @@ __device__ __forceinline__ PassMasks build_pass(uint32_t* masks, const uint32_t*
     return m;
 }
 
-// Execution modes of a part's blocks: kPlain, u16 symbols only (no tail); kTrack, the same while keeping
-// an upper bound on the part's last placeholder (the tail may start later); kTail, the determined tail has
-// started (positions at or after OutState::det are bytes).  Separate instantiations keep the tail's checks
-// out of the plain decoding loop.
-enum : int { kPlain = 0, kTrack = 1, kTail = 2 };
+// Execution modes of a part's blocks: kPlain, u16 symbols only; kTail, with the determined tail: an upper
+// bound on the part's last placeholder is kept, and positions at or after OutState::det (once set) are
+// bytes.  Two instantiations keep the tail's checks out of the plain decoding loop; one instantiation serves
+// every block of the tail option, so warps in different parts run the same code.
+enum : int { kPlain = 0, kTail = 1 };
 
 // A lane's 8 resolved entries (positions p0 .. p0 + 7; the low 16 bits are the symbols) into the part's
 // output, the positions inside [base, end) only: one 16-byte store of u16 symbols, or one 8-byte store of
@@ -1059,7 +1059,7 @@ __device__ __forceinline__ int exec_range(WarpSmem& S, OutState& o, const uint32
                 if ((m1.cm >> u) & 1u) nb[8u * lane + u] = buf[nb[8u * lane + u] & 0xffu];
         }
         store8<MODE == kTail>(o, out, e, p0, base, end);
-        if (MODE == kTrack) track_placeholders(o, e, A, end);
+        if (MODE == kTail && o.det == 0xffffffffu) track_placeholders(o, e, A, end);
         __syncwarp();                                      // this pass is final; its buffer may be reused
         if (!more) break;
         A = A1;
@@ -1140,7 +1140,7 @@ __device__ __forceinline__ int exec_range(WarpSmem& S, OutState& o, const uint32
             __syncwarp();
         }
         store8<MODE == kTail>(o, out, e, p0, base, end);
-        if (MODE == kTrack) track_placeholders(o, e, A, end);
+        if (MODE == kTail && o.det == 0xffffffffu) track_placeholders(o, e, A, end);
         __syncwarp();                                      // this pass is final for the next one
     }
     }
@@ -1713,10 +1713,8 @@ __device__ void inflate_part(WarpSmem& S, uint32_t* tok, const FileDesc* __restr
                 o.det = (uint32_t)((o.n + 7) & ~7ull);
             const bool check = !o.known && blocks < window;
             uint32_t fin = 0;
-            int st;
-            if (!tail_ok) st = one_block<PIPE, kPlain>(S, tok, br, o, check, 0, 0, false, F.end_bit, fin, lane);
-            else if (o.det != 0xffffffffu) st = one_block<PIPE, kTail>(S, tok, br, o, check, 0, 0, false, F.end_bit, fin, lane);
-            else st = one_block<PIPE, kTrack>(S, tok, br, o, check, 0, 0, false, F.end_bit, fin, lane);
+            const int st = tail_ok ? one_block<PIPE, kTail>(S, tok, br, o, check, 0, 0, false, F.end_bit, fin, lane)
+                                   : one_block<PIPE, kPlain>(S, tok, br, o, check, 0, 0, false, F.end_bit, fin, lane);
             if (st) {
                 err = (check && st != CE_OVERFLOW) ? (uint32_t)CE_CONFIRM : (uint32_t)st;
                 break;
