@@ -65,8 +65,7 @@ __constant__ uint8_t c_clorder[19] = {16, 17, 18, 0, 8, 7, 9, 6, 10, 5, 11, 4, 1
 __constant__ uint32_t c_crc_tab[4][256];   // [0][b]: register after byte b from a zero register; [k]: k more zero bytes
 __constant__ uint32_t c_x2k[64];           // x^(2^k) mod P
 __constant__ uint32_t c_lane_shift[32];    // x^(8*kPiece*k) mod P
-__constant__ uint32_t c_xseg;              // x^(8*kCrcSeg) mod P
-__constant__ uint32_t c_xhalf;             // x^(8*kPiece/2) mod P
+__constant__ uint32_t c_seg_shift[4][256]; // [j][b]: (byte b at byte j of a register) x^(8*kCrcSeg) mod P
 
 // literal/length lookup entry: bits 0-4 bits to drop, 8-16 value, 17-19
 // extra-bit count (K_LENX), 28-31 kind.  K_LEN carries the exact length
@@ -2231,10 +2230,12 @@ __device__ uint32_t xpow8(uint64_t n) {       // x^(8n) mod P
     return r;
 }
 
-constexpr uint32_t kCrcSeg = 8192;    // bytes per warp step
-constexpr uint32_t kPiece = 256;      // bytes per lane (kCrcSeg / 32)
+constexpr uint32_t kPiece = 32;       // bytes per lane and segment
+constexpr uint32_t kCrcSeg = 32 * kPiece;   // bytes per warp step (one piece per lane)
+constexpr int kCrcAhead = 3;          // segments whose loads are in flight while one is folded
 constexpr int kCrcThreads = 1024;     // one block per SM
-constexpr size_t kCrcSmem = 4 * 256 * 32 * sizeof(uint32_t);   // 128 KiB: four tables, one copy per lane
+// four byte tables with one copy per lane (128 KiB), then the segment shift's four byte tables, shared (4 KiB)
+constexpr size_t kCrcSmem = (4 * 256 * 32 + 4 * 256) * sizeof(uint32_t);
 
 // Slicing by four (four table lookups per 32-bit word, RFC 1952 CRC in the
 // reflected form): with x = r ^ w, the register after the word's four bytes
@@ -2248,53 +2249,54 @@ __device__ __forceinline__ uint32_t crc_word(const uint32_t* Tl, uint32_t r, uin
            Tl[32u * (256u + ((x >> 16) & 0xffu))] ^ Tl[32u * (x >> 24)];
 }
 
-// raw CRC register (zero start) of n bytes at p; Tl is the lane's table copy.  A whole 16-byte aligned piece
-// runs as two independent chains over its halves (their lookups overlap), joined by one shift of the first
-// half's register over the second half's length: R(A||B) = R(A) x^(8|B|) + R(B).
-__device__ __forceinline__ uint32_t crc_bytes(const uint32_t* Tl, const uint8_t* p, uint64_t n, uint32_t xhalf) {
-    if (n == kPiece && ((reinterpret_cast<uintptr_t>(p) & 15) == 0)) {
-        const uint4* v = reinterpret_cast<const uint4*>(p);
-        constexpr int H = kPiece / 32;                    // 16-byte loads per half piece
-        uint4 a[H], b[H];
+// raw CRC register (zero start) of a whole piece held in registers
+__device__ __forceinline__ uint32_t crc_piece(const uint32_t* Tl, const uint4 (&v)[kPiece / 16]) {
+    uint32_t r = 0;
 #pragma unroll
-        for (int q = 0; q < H; ++q) {
-            a[q] = v[q];
-            b[q] = v[H + q];
-        }
-        uint32_t ra = 0, rb = 0;
-#pragma unroll
-        for (int q = 0; q < H; ++q) {
-            ra = crc_word(Tl, ra, a[q].x);
-            rb = crc_word(Tl, rb, b[q].x);
-            ra = crc_word(Tl, ra, a[q].y);
-            rb = crc_word(Tl, rb, b[q].y);
-            ra = crc_word(Tl, ra, a[q].z);
-            rb = crc_word(Tl, rb, b[q].z);
-            ra = crc_word(Tl, ra, a[q].w);
-            rb = crc_word(Tl, rb, b[q].w);
-        }
-        return gf2_mul(ra, xhalf) ^ rb;
+    for (int q = 0; q < (int)(kPiece / 16); ++q) {
+        r = crc_word(Tl, r, v[q].x);
+        r = crc_word(Tl, r, v[q].y);
+        r = crc_word(Tl, r, v[q].z);
+        r = crc_word(Tl, r, v[q].w);
     }
+    return r;
+}
+
+// raw CRC register (zero start) of n bytes at p, byte by byte
+__device__ __forceinline__ uint32_t crc_bytes(const uint32_t* Tl, const uint8_t* p, uint64_t n) {
     uint32_t r = 0;
     for (uint64_t i = 0; i < n; ++i) r = Tl[32u * ((r ^ p[i]) & 0xffu)] ^ (r >> 8);
     return r;
 }
 
-// Each warp takes a contiguous run of segments: the 32 lanes' pieces of a
-// segment are combined by their shift to the segment end, segments are
-// folded in order (R(A||B) = R(A) x^(8|B|) + R(B)), and a run is shifted to
-// the end of its member once and XOR-accumulated there.  The member of a
-// segment is found once per run, then followed forward.
+// r times x^(8 kCrcSeg) mod P: by linearity, the XOR of the products of r's four bytes, each looked up in
+// its own table (Y + 256 j: byte j of the register, in place, times the constant)
+__device__ __forceinline__ uint32_t crc_shift_seg(const uint32_t* Y, uint32_t r) {
+    return Y[r & 0xffu] ^ Y[256u + ((r >> 8) & 0xffu)] ^ Y[512u + ((r >> 16) & 0xffu)] ^ Y[768u + (r >> 24)];
+}
+
+// Each warp takes a contiguous run of segments and walks the members it
+// covers.  Within a member, lane l's pieces (bytes 32 l .. 32 l + 31 of each
+// segment) are folded across the run's full segments by Horner's rule,
+// acc_l <- acc_l x^(8 kCrcSeg) + R(piece), so that at the end acc_l
+// x^(8 kPiece (31 - l)), summed over the lanes, is the raw CRC of those
+// segments (R(A||B) = R(A) x^(8|B|) + R(B)); that sum is shifted to the end
+// of the member once and XOR-accumulated there.  The loads of the next
+// kCrcAhead segments are in flight while a segment is folded (a warp's
+// 32-byte pieces are one 1 KiB stretch, so each load instruction reads few
+// lines).  A member's last segment, when shorter, is done byte by byte with
+// per-lane shifts, and so is a member whose output is not 16-byte aligned.
 __global__ void __launch_bounds__(kCrcThreads, 1) k_crc(FileDesc* files, int nfiles, uint64_t total_seg,
                                                         const uint64_t* seg0, uint64_t segs_per_warp) {
-    extern __shared__ uint32_t T[];                       // 4 x 256 x 32 words
+    extern __shared__ uint32_t T[];                       // 4 x 256 x 32 words, then 4 x 256 (the segment shift)
     __shared__ uint32_t LS[32];
     for (int k = threadIdx.x; k < 4 * 256 * 32; k += blockDim.x) T[k] = c_crc_tab[k >> 13][(k >> 5) & 255];
+    uint32_t* Y = T + 4 * 256 * 32;
+    for (int k = threadIdx.x; k < 4 * 256; k += blockDim.x) Y[k] = c_seg_shift[k >> 8][k & 255];
     if (threadIdx.x < 32) LS[threadIdx.x] = c_lane_shift[threadIdx.x];
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const uint32_t* Tl = T + lane;
-    const uint32_t xhalf = c_xhalf;
     const uint64_t w = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const uint64_t s_begin = w * segs_per_warp;
     if (s_begin >= total_seg) return;
@@ -2309,50 +2311,64 @@ __global__ void __launch_bounds__(kCrcThreads, 1) k_crc(FileDesc* files, int nfi
         }
         f = lo;
     }
-    uint64_t next_seg0 = f + 1 < nfiles ? seg0[f + 1] : ~0ull;
-    uint32_t acc = 0;
-    uint64_t run_end = 0;
-    auto flush = [&]() {
-        if (lane == 0 && run_end > 0) atomicXor(&files[f].crc_acc, gf2_mul(acc, xpow8(files[f].total - run_end)));
-    };
-    bool skip = false;
-    uint64_t D = 0, base_seg = 0;
-    const uint8_t* out = nullptr;
-    auto enter = [&]() {                                  // the member's fields, once per member of the run
-        const FileDesc& F = files[f];
-        skip = F.status != PGZ_OK || (F.mode != 0 && F.mode != 3);
-        D = F.total;
-        out = F.out;
-        base_seg = seg0[f];
-        acc = 0;
-        run_end = 0;
-    };
-    enter();
-    for (uint64_t sg = s_begin; sg < s_end; ++sg) {
-        if (sg >= next_seg0) {                            // the next member (members with no segment skipped)
-            flush();
-            do {
-                ++f;
-                next_seg0 = f + 1 < nfiles ? seg0[f + 1] : ~0ull;
-            } while (sg >= next_seg0);
-            enter();
-        }
-        if (skip) continue;
-        const uint64_t a = (sg - base_seg) * kCrcSeg;
-        if (a >= D) continue;
-        const uint64_t se = a + kCrcSeg < D ? a + kCrcSeg : D;
-        const uint64_t pa = a + (uint64_t)kPiece * lane;
-        const uint64_t pb = pa + kPiece < se ? pa + kPiece : se;
-        uint32_t r = 0;
-        if (pa < pb) {
-            r = crc_bytes(Tl, out + pa, pb - pa, xhalf);
-            r = (se - a == kCrcSeg) ? gf2_mul(r, LS[31 - lane]) : gf2_mul(r, xpow8(se - pb));
-        }
+    // this lane's part of a raw CRC that ends `shift` bytes before the end of member f: summed over the warp,
+    // shifted to the end, accumulated
+    auto add = [&](uint32_t r, uint64_t shift) {
         for (int d = 16; d; d >>= 1) r ^= __shfl_xor_sync(FULL, r, d);
-        acc = (run_end == 0 ? 0u : gf2_mul(acc, se - a == kCrcSeg ? c_xseg : xpow8(se - a))) ^ r;
-        run_end = se;
+        if (lane == 0) atomicXor(&files[f].crc_acc, shift ? gf2_mul(r, xpow8(shift)) : r);
+    };
+    for (uint64_t sg = s_begin; sg < s_end; ++f) {        // one member of the run per step
+        const uint64_t m_end = f + 1 < nfiles ? seg0[f + 1] : ~0ull;
+        if (sg >= m_end) continue;                        // a member with no segment
+        const uint64_t g_end = m_end < s_end ? m_end : s_end;
+        const FileDesc& F = files[f];
+        const uint64_t i0 = sg - seg0[f], i1 = g_end - seg0[f];   // the member's segments [i0, i1) in this run
+        sg = g_end;
+        if (F.status != PGZ_OK || (F.mode != 0 && F.mode != 3)) continue;
+        const uint64_t D = F.total;
+        const uint8_t* out = F.out;
+        const uint64_t nfull = D / kCrcSeg;
+        const uint64_t ie = i1 < nfull ? i1 : nfull;      // full segments [i0, ie)
+        const uint8_t* base = out + (uint64_t)kPiece * lane;
+        if (i0 < ie) {
+            uint32_t acc = 0;
+            if ((reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+                uint4 v[kCrcAhead + 1][kPiece / 16];
+                auto load = [&](uint64_t i, uint4 (&dst)[kPiece / 16]) {
+                    if (i < ie) {
+                        const uint4* p = reinterpret_cast<const uint4*>(base + i * kCrcSeg);
+#pragma unroll
+                        for (int q = 0; q < (int)(kPiece / 16); ++q) dst[q] = p[q];
+                    }
+                };
+#pragma unroll
+                for (int k = 0; k < kCrcAhead; ++k) load(i0 + k, v[k]);
+                for (uint64_t i = i0; i < ie; i += kCrcAhead + 1) {
+#pragma unroll
+                    for (int k = 0; k <= kCrcAhead; ++k) {
+                        if (i + k < ie) {
+                            load(i + k + kCrcAhead, v[(k + kCrcAhead) % (kCrcAhead + 1)]);
+                            const uint32_t r = crc_piece(Tl, v[k]);
+                            acc = i + k > i0 ? crc_shift_seg(Y, acc) ^ r : r;
+                        }
+                    }
+                }
+            } else {
+                for (uint64_t i = i0; i < ie; ++i) {
+                    const uint32_t r = crc_bytes(Tl, base + i * kCrcSeg, kPiece);
+                    acc = i > i0 ? crc_shift_seg(Y, acc) ^ r : r;
+                }
+            }
+            add(gf2_mul(acc, LS[31 - lane]), D - ie * kCrcSeg);
+        }
+        if (i0 <= nfull && nfull < i1 && D > nfull * kCrcSeg) {   // the member's last segment, shorter
+            const uint64_t pa = nfull * kCrcSeg + (uint64_t)kPiece * lane;
+            const uint64_t pb = pa + kPiece < D ? pa + kPiece : D;
+            uint32_t r = 0;
+            if (pa < pb) r = gf2_mul(crc_bytes(Tl, out + pa, pb - pa), xpow8(D - pb));
+            add(r, 0);
+        }
     }
-    flush();
 }
 
 __global__ void k_finalize(FileDesc* files, int nfiles) {
@@ -2659,17 +2675,13 @@ void upload_crc_tables() {
         for (int k = 0; e; ++k, e >>= 1)
             if (e & 1) xseg = h_mul(xseg, x2k[k]);
     }
+    uint32_t seg[4][256];                      // multiplication by x^(8*kCrcSeg), byte by byte (it is linear)
+    for (int j = 0; j < 4; ++j)
+        for (uint32_t b = 0; b < 256; ++b) seg[j][b] = h_mul(b << (8 * j), xseg);
     cudaMemcpyToSymbol(c_crc_tab, tab, sizeof tab);
     cudaMemcpyToSymbol(c_x2k, x2k, sizeof x2k);
     cudaMemcpyToSymbol(c_lane_shift, ls, sizeof ls);
-    uint32_t xhalf = 0x80000000u;
-    {
-        uint64_t e = 8ull * (kPiece / 2);
-        for (int k = 0; e; ++k, e >>= 1)
-            if (e & 1) xhalf = h_mul(xhalf, x2k[k]);
-    }
-    cudaMemcpyToSymbol(c_xseg, &xseg, sizeof xseg);
-    cudaMemcpyToSymbol(c_xhalf, &xhalf, sizeof xhalf);
+    cudaMemcpyToSymbol(c_seg_shift, seg, sizeof seg);
 }
 
 }  // namespace pgz
