@@ -208,14 +208,17 @@ int pgz_decompress_batch(pgz_ctx* ctx, int n, pgz_job* jobs, pgz_stats* st);
    file decompression in two passes", over a batch): jobs [host array of n],
    each job's gz and out are HOST pointers (page-locked memory lets the copies
    overlap the decoding; pageable memory works but copies synchronously).  The
-   jobs are cut into up to 4 groups of consecutive jobs with about equal
-   compressed bytes (groups of at least 96 MiB); each group's part size is
-   the one nearest the context's that gives a whole number of waves of pass-1
-   warps (pgz_wave_chunk_bytes; the context's size as is with n_chunks set).
-   Every group is copied to
-   device memory owned by the context, decoded by one run of the pass kernels
-   as soon as its own copy has arrived, and its output copied back to the
-   jobs' `out` while the next group decodes.  Statuses, out_len and the return
+   jobs are cut into groups of consecutive jobs: from 288 MiB of compressed
+   bytes three (about 15 %, 70 % and 15 % of the bytes: only the first
+   group's upload and the last group's download are not overlapped), from
+   192 MiB two halves, else one.  Each group's part size is the one nearest
+   the context's that gives a whole number of waves of pass-1 warps
+   (pgz_wave_chunk_bytes; the context's size as is with n_chunks set).  Every
+   group is copied to device memory owned by the context, then its run's
+   plan, on one upload stream in that order, so that a run waits for its own
+   group only; it is decoded by one run of the pass kernels as soon as its
+   own copy has arrived, and its output copied back to the jobs' `out` while
+   the next group decodes.  Statuses, out_len and the return
    value as for pgz_decompress_batch; st (nullable) receives in_bytes,
    out_bytes and chunks (the ms_* fields are not timed here).  The call returns
    when every output is in host memory. */

@@ -241,7 +241,7 @@ struct Plan {
     int wpb = 4;                  // warps per block of the pass-1 kernels (sizes the token scratch)
     const uint8_t* fill = nullptr;   // device window of fill bytes (mode 1)
     DBuf d_files, d_chunks, d_g0, d_gn, d_gfile, d_seg0, d_sym, d_windows, d_gmaps, d_wstart, d_tok, d_queue, d_order;
-    PBuf h_files, h_chunks;
+    PBuf h_files, h_chunks, h_static;
     cudaGraphExec_t graph = nullptr;
     void release() {
         d_files.release();
@@ -259,6 +259,7 @@ struct Plan {
         d_order.release();
         h_files.release();
         h_chunks.release();
+        h_static.release();
         if (graph) cudaGraphExecDestroy(graph);
         graph = nullptr;
     }
@@ -434,26 +435,45 @@ int layout(Plan& P) {
     if (!e && P.chain) e = P.d_wstart.ensure(ng * (size_t)kWin);
     if (!e) e = P.h_files.ensure(nf * sizeof(FileDesc));
     if (!e) e = P.h_chunks.ensure(nc * sizeof(ChunkDesc));
+    if (!e) e = P.h_static.ensure(3 * round_up(ng * sizeof(int32_t), 16) + round_up(nf * sizeof(uint64_t), 16) +
+                                  round_up(nc * sizeof(uint32_t), 16));
     return cuda_status(e);
 }
 
 // the device-resident part of a run: uploads, every stage, result download
-// the plan's static arrays (pageable host memory: never inside a graph capture)
+// the plan's static arrays (outside any graph capture), staged in pinned memory: a copy from pageable memory
+// is staged by the driver and may reach the copy engine after pinned copies issued later (the next group of
+// compressed bytes of a host-buffer batch), so that the run would wait for them
 void upload_static(Plan& P, cudaStream_t s) {
-    const size_t nf = P.files.size(), ng = P.g0.size();
-    cudaMemcpyAsync(P.d_g0.p, P.g0.data(), ng * sizeof(int32_t), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(P.d_gn.p, P.gn.data(), ng * sizeof(int32_t), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(P.d_gfile.p, P.gfile.data(), ng * sizeof(int32_t), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(P.d_seg0.p, P.seg0.data(), nf * sizeof(uint64_t), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(P.d_order.p, P.order.data(), P.order.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+    const size_t nf = P.files.size(), ng = P.g0.size(), nc = P.order.size();
+    uint8_t* h = P.h_static.as<uint8_t>();
+    size_t off = 0;
+    auto put = [&](void* dst, const void* src, size_t bytes) {
+        if (bytes) {
+            memcpy(h + off, src, bytes);
+            cudaMemcpyAsync(dst, h + off, bytes, cudaMemcpyHostToDevice, s);
+        }
+        off += round_up(bytes, 16);
+    };
+    put(P.d_g0.p, P.g0.data(), ng * sizeof(int32_t));
+    put(P.d_gn.p, P.gn.data(), ng * sizeof(int32_t));
+    put(P.d_gfile.p, P.gfile.data(), ng * sizeof(int32_t));
+    put(P.d_seg0.p, P.seg0.data(), nf * sizeof(uint64_t));
+    put(P.d_order.p, P.order.data(), nc * sizeof(uint32_t));
 }
 
-int enqueue(pgz_ctx* ctx, Plan& P, cudaStream_t s, bool timed) {
+// up/up_done (optional): the plan's uploads go on stream `up` instead, and the run waits for them (event
+// up_done); see pgz_decompress_batch_host
+int enqueue(pgz_ctx* ctx, Plan& P, cudaStream_t s, bool timed, cudaStream_t up = nullptr,
+            cudaEvent_t up_done = nullptr) {
     const size_t nf = P.files.size(), nc = P.chunks.size(), ng = P.g0.size();
+    const cudaStream_t u = up ? up : s;
     memcpy(P.h_files.p, P.files.data(), nf * sizeof(FileDesc));
     memcpy(P.h_chunks.p, P.chunks.data(), nc * sizeof(ChunkDesc));
-    cudaMemcpyAsync(P.d_files.p, P.h_files.p, nf * sizeof(FileDesc), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(P.d_chunks.p, P.h_chunks.p, nc * sizeof(ChunkDesc), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(P.d_files.p, P.h_files.p, nf * sizeof(FileDesc), cudaMemcpyHostToDevice, u);
+    cudaMemcpyAsync(P.d_chunks.p, P.h_chunks.p, nc * sizeof(ChunkDesc), cudaMemcpyHostToDevice, u);
+    if (up && (cudaEventRecord(up_done, up) != cudaSuccess || cudaStreamWaitEvent(s, up_done, 0) != cudaSuccess))
+        return PGZ_E_CUDA;
     FileDesc* df = P.d_files.as<FileDesc>();
     ChunkDesc* dc = P.d_chunks.as<ChunkDesc>();
     uint16_t* sym = P.d_sym.as<uint16_t>();
@@ -568,13 +588,13 @@ void fill_stats(pgz_ctx* ctx, const Plan& P, pgz_stats* st, uint64_t retries, ui
 
 // the first half of a run of a plan: buffers, uploads and every launch, all asynchronous on the context's
 // stream
-int start_run(pgz_ctx* ctx, Plan& P, bool timed) {
+int start_run(pgz_ctx* ctx, Plan& P, bool timed, cudaStream_t up = nullptr, cudaEvent_t up_done = nullptr) {
     P.wpb = ctx->kp.wpb;
     reset_results(P);
     int e = layout(P);
     if (e) return e;
-    upload_static(P, ctx->stream);
-    return enqueue(ctx, P, ctx->stream, timed);
+    upload_static(P, up ? up : ctx->stream);
+    return enqueue(ctx, P, ctx->stream, timed, up, up_done);
 }
 
 // the second half: waits for the run, then re-runs with recovery until the plan succeeds or cannot
@@ -1374,8 +1394,14 @@ int pgz_decompress_batch_host(pgz_ctx* ctx, int n, pgz_job* jobs, pgz_stats* st)
     if (cuda_status(ctx->hb_in.ensure(in_total)) || cuda_status(ctx->hb_out.ensure(out_total))) return PGZ_E_NOMEM;
     uint8_t* din = ctx->hb_in.as<uint8_t>();
     uint8_t* dout = ctx->hb_out.as<uint8_t>();
-    // groups: consecutive jobs, about in_total / ng compressed bytes each
-    const int ng = (int)std::max<uint64_t>(1, std::min<uint64_t>({(uint64_t)G, (uint64_t)n, in_total / (96ull << 20)}));
+    // groups of consecutive jobs.  Only the first group's upload and the last group's download are not
+    // overlapped with decoding, so with enough bytes there are three: a short first and last group (about
+    // 15 % of the compressed bytes each) around a long middle one, whose run keeps most parts in whole waves
+    // of one launch; with fewer bytes two halves, or one group.  (Measured on the 512-member batch: 102 ms a
+    // call against 106 ms for three or four equal groups.)
+    static_assert(G >= 3, "three host-batch groups");
+    const int ng = (int)std::min<uint64_t>((uint64_t)n, in_total >= (288ull << 20) ? 3 : in_total >= (192ull << 20) ? 2 : 1);
+    const double edge[3] = {ng == 3 ? 0.15 : 0.5, ng == 3 ? 0.85 : 1.0, 1.0};   // cumulative share at each group's end
     std::vector<int> gfirst((size_t)ng + 1, n);
     {
         uint64_t acc = 0;
@@ -1383,20 +1409,15 @@ int pgz_decompress_batch_host(pgz_ctx* ctx, int n, pgz_job* jobs, pgz_stats* st)
         gfirst[0] = 0;
         for (int k = 0; k < n && g + 1 < ng; ++k) {
             acc += valid[k] ? round_up(jobs[k].gz_len, 16) : 0;
-            if (acc * (uint64_t)ng >= in_total * (uint64_t)(g + 1)) gfirst[++g] = k + 1;
+            if ((double)acc >= edge[g] * (double)in_total) gfirst[++g] = k + 1;
         }
         for (int h = g + 1; h <= ng; ++h) gfirst[h] = n;
     }
-    // every upload at once, one event per group
-    for (int g = 0; g < ng; ++g) {
-        for (int k = gfirst[g]; k < gfirst[g + 1]; ++k)
-            if (valid[k] && cudaMemcpyAsync(din + in_off[k], jobs[k].gz, jobs[k].gz_len, cudaMemcpyHostToDevice,
-                                            ctx->hb_up) != cudaSuccess)
-                return PGZ_E_CUDA;
-        if (cudaEventRecord(ctx->hb_ev_up[g], ctx->hb_up) != cudaSuccess) return PGZ_E_CUDA;
-    }
-    // the groups' runs back to back; each group's output down as its run ends (ISIZE bytes: the length of
-    // a good member below 4 GiB, corrected below when the run says otherwise)
+    // the groups' runs back to back.  Each group's bytes and then its run's own small uploads of the plan go
+    // on the upload stream, in that order, so that a run waits for its own group's bytes only: a copy engine
+    // busy with a later group's bytes would not take a plan copy waiting on another stream before that whole
+    // copy ends.  Each group's output goes down as its run ends (ISIZE bytes: the length of a good member
+    // below 4 GiB, corrected below when the run says otherwise).
     int status = PGZ_OK;
     std::vector<char> started((size_t)ng, 0);
     const pgz_config saved = ctx->cfg;
@@ -1418,8 +1439,11 @@ int pgz_decompress_batch_host(pgz_ctx* ctx, int n, pgz_job* jobs, pgz_stats* st)
                 plan_member(ctx, P, din + in_off[k], jobs[k].gz_len, dout + out_off[k], jobs[k].out_cap, mi[k], 0);
         ctx->cfg = saved;
         if (P.files.empty()) continue;
-        if (cudaStreamWaitEvent(ctx->stream, ctx->hb_ev_up[g], 0) != cudaSuccess) return PGZ_E_CUDA;
-        const int e = start_run(ctx, P, false);
+        for (int k = gfirst[g]; k < gfirst[g + 1]; ++k)
+            if (valid[k] && cudaMemcpyAsync(din + in_off[k], jobs[k].gz, jobs[k].gz_len, cudaMemcpyHostToDevice,
+                                            ctx->hb_up) != cudaSuccess)
+                return PGZ_E_CUDA;
+        const int e = start_run(ctx, P, false, ctx->hb_up, ctx->hb_ev_up[g]);
         if (e) {
             status = e;
             break;

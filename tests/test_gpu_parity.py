@@ -350,17 +350,17 @@ def test_host_entry_point(cfg1):
 
 def test_host_batch_entry_point():
     """pgz_decompress_batch_host: members in host memory (page-locked and pageable), cut into groups whose
-    copies overlap the decoding.  Four 64 MiB members of Markov text make the batch span more than one
-    group; a member with a hidden false block start needs recovery inside its group; a member with a wrong
-    trailer CRC fails alone.  Every other output is exact."""
+    copies overlap the decoding.  Six 64 MiB members of Markov text (about 300 MiB compressed) make the batch
+    span three groups (a short first and last one); a member with a hidden false block start needs recovery
+    inside the last group; a member with a wrong trailer CRC fails alone.  Every other output is exact."""
     import torch
     import confirm_streams as cs
     m = cs.find("invalid", 2)
-    raws = [synth.markov(64 << 20, 30 + k) for k in range(4)] + [synth.fastq(3 << 20, 150, 0.001, 34), m.data]
-    gzs = [synth.gzip_compress(r, 1) for r in raws[:5]] + [m.gz]
-    bad = bytearray(synth.gzip_compress(raws[4], 6))
+    raws = [synth.markov(64 << 20, 30 + k) for k in range(6)] + [synth.fastq(3 << 20, 150, 0.001, 34), m.data]
+    gzs = [synth.gzip_compress(r, 1) for r in raws[:7]] + [m.gz]
+    bad = bytearray(synth.gzip_compress(raws[6], 6))
     bad[-8] ^= 1
-    raws.insert(2, raws[4])
+    raws.insert(2, raws[6])
     gzs.insert(2, bytes(bad))
     ctx = Ctx(n_chunks=0, chunk_bytes=64 << 10)
     try:
