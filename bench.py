@@ -67,8 +67,8 @@ PASS1_TRAFFIC_PER_OUT_BYTE = {
 # ... and the 512-member batch, by (part size, warps per block, pipelined execution, determined tail)
 # (profiles/pass1_traffic_batch512.md).  Other configurations report null.
 PASS1_TRAFFIC_PER_OUT_BYTE_BATCH512 = {
-    (499078, 4, 0, 0): (0.965091840e9 + 0.952751872e9 + 39.928896000e9 + 23.369684224e9) / 4467581835,
-    (499078, 2, 0, 0): (0.9631e9 + 0.9521e9 + 39.9500e9 + 23.3771e9) / 4467581835,
+    (499078, 4, 0, 0): (0.964350464e9 + 0.952157696e9 + 39.964783360e9 + 23.372040960e9) / 4467581835,
+    (499078, 2, 0, 0): (0.966032640e9 + 0.953315840e9 + 39.960246528e9 + 23.372556288e9) / 4467581835,
 }
 
 
