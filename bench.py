@@ -61,8 +61,8 @@ SERVED_REQUESTS = 240         # requests per offered load in the default run (th
 # of the current kernels.  The two 256 MiB FASTQ files as one batch, by (part size, warps per block, pipelined
 # execution) (profiles/pass1_traffic_fastq256.md) ...
 PASS1_TRAFFIC_PER_OUT_BYTE = {
-    (88162, 2, 0): (0.8541e9 + 0.5243e9 + 3.0353e9 + 1.3165e9) / 536870912,
-    (88162, 4, 0): (0.8526e9 + 0.5236e9 + 3.0376e9 + 1.3172e9) / 536870912,
+    (88162, 2, 0): (0.852781568e9 + 0.524115712e9 + 3.037636864e9 + 1.317603072e9) / 536870912,
+    (88162, 4, 0): (0.854030592e9 + 0.524192512e9 + 3.039483648e9 + 1.317075712e9) / 536870912,
 }
 # ... and the 512-member batch, by (part size, warps per block, pipelined execution, determined tail)
 # (profiles/pass1_traffic_batch512.md).  Other configurations report null.
