@@ -398,6 +398,59 @@ void pgz_server_destroy(pgz_server* srv);
 /* Number of kernels this library launched on ctx since it was created. */
 uint64_t pgz_kernel_launches(const pgz_ctx* ctx);
 
+/* For tests of the host logic (no device work; works without a GPU): one
+   step of the recovery the library runs after a pass-1 run of one member,
+   on a description of its parts.  The rules are those of Section "Detection
+   of DEFLATE block start positions" and Section "Full file decompression in
+   two passes": a searched start whose block, or one of the confirm_blocks
+   blocks after it, fails the checks is dropped and the search goes on from
+   the bit after it (a part that ends exactly on the next part's start
+   before its window is complete continues its window with that part's
+   checked blocks); a part that does not end exactly on the next part's start
+   shows that start to be false: the next part is merged into it when its
+   own confirmation passed, decoded past its stop when the run left the
+   confirmation open, searched on from the bit after it when it ends a
+   streamed segment; a part whose symbols overflowed needs more capacity.
+   parts [host array of n, part i of the member in order]: the plan fields
+   and the run's results on input; on return the plan fields (lo, disabled,
+   confirm_ext) hold the next run's plan.  s0_bit: the member's first DEFLATE
+   bit (part 0 with lo <= s0_bit is the member start); mode and last_seg as
+   for the member's description (0: a whole member; 3 with last_seg 0: a
+   streamed segment that does not reach the member's end).  Returns
+   PGZ_RECOVER_STOP (the parts' errors are final), PGZ_RECOVER_RERUN or
+   PGZ_RECOVER_GROW (*grow: the part that needs more symbol capacity), or -1
+   for bad arguments; *false_syncs is increased by one for every start the
+   step drops as false without searching on from it. */
+typedef enum pgz_part_status {
+    PGZ_PART_FOUND = 1, PGZ_PART_EMPTY = 2, PGZ_PART_DONE = 3, PGZ_PART_ERROR = 4
+} pgz_part_status;
+typedef enum pgz_part_error {
+    PGZ_PART_OK = 0, PGZ_PART_DATA = 1, PGZ_PART_TRUNC = 2, PGZ_PART_DIST = 3, PGZ_PART_OVERFLOW = 4,
+    PGZ_PART_CHAIN = 5,    /* did not end exactly on the next part's block start */
+    PGZ_PART_CONFIRM = 6,  /* a block of the start's confirmation window failed its checks */
+    PGZ_PART_TRAIL = 7     /* data after the member's final block */
+} pgz_part_error;
+typedef enum pgz_recover_action {
+    PGZ_RECOVER_STOP = 0, PGZ_RECOVER_RERUN = 1, PGZ_RECOVER_GROW = 2
+} pgz_recover_action;
+typedef struct pgz_part_state {
+    /* plan */
+    uint64_t lo;           /* first bit of the block-start search */
+    int32_t given;         /* lo is a known block start (no search) */
+    int32_t probe;         /* only the block start is searched (the end of a streamed segment) */
+    int32_t disabled;      /* merged into the previous part */
+    int32_t confirm_ext;   /* decodes past its stop until its confirmation is settled */
+    /* results of the run */
+    int32_t state;         /* pgz_part_status */
+    int32_t err;           /* pgz_part_error when state is PGZ_PART_ERROR */
+    uint64_t sync;         /* block start taken (UINT64_MAX: none) */
+    uint64_t end;          /* bit where the part's decoding stopped */
+    uint32_t blocks;       /* blocks the part decoded (its own start's block first) */
+    uint32_t confirmed;    /* its start's confirmation window passed */
+} pgz_part_state;
+int pgz_recover_step(int n, pgz_part_state* parts, uint64_t s0_bit, int mode, int last_seg, int confirm_blocks,
+                     uint64_t* false_syncs, int* grow);
+
 const char* pgz_strerror(int status);
 
 #ifdef __cplusplus

@@ -1653,6 +1653,55 @@ int pgz_inspect_window(pgz_ctx* ctx, int part, uint8_t* host_dst) {
 
 uint64_t pgz_kernel_launches(const pgz_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+// the header's part states, error codes and actions are the library's own
+static_assert(PGZ_PART_FOUND == CS_FOUND && PGZ_PART_EMPTY == CS_EMPTY && PGZ_PART_DONE == CS_DONE &&
+                  PGZ_PART_ERROR == CS_ERROR, "part states");
+static_assert(PGZ_PART_OK == CE_OK && PGZ_PART_DATA == CE_DATA && PGZ_PART_TRUNC == CE_TRUNC &&
+                  PGZ_PART_DIST == CE_DIST && PGZ_PART_OVERFLOW == CE_OVERFLOW && PGZ_PART_CHAIN == CE_CHAIN &&
+                  PGZ_PART_CONFIRM == CE_CONFIRM && PGZ_PART_TRAIL == CE_TRAIL, "part errors");
+static_assert(PGZ_RECOVER_STOP == kRecoverStop && PGZ_RECOVER_RERUN == kRecoverRerun &&
+                  PGZ_RECOVER_GROW == kRecoverGrow, "recovery actions");
+
+int pgz_recover_step(int n, pgz_part_state* parts, uint64_t s0_bit, int mode, int last_seg, int confirm_blocks,
+                     uint64_t* false_syncs, int* grow) {
+    if (n <= 0 || !parts || !false_syncs || !grow || confirm_blocks < 0 || mode < 0 || mode > 3) return -1;
+    FileDesc F{};
+    F.chunk0 = 0;
+    F.nchunks = n;
+    F.s0_bit = s0_bit;
+    F.mode = (uint32_t)mode;
+    F.last_seg = last_seg ? 1u : 0u;
+    std::vector<ChunkDesc> plan((size_t)n), res((size_t)n);
+    for (int k = 0; k < n; ++k) {
+        const pgz_part_state& q = parts[k];
+        ChunkDesc& C = plan[(size_t)k];
+        C = ChunkDesc{};
+        C.lo = q.lo;
+        C.index = k;
+        C.given = q.given ? 1u : 0u;
+        C.probe = q.probe ? 1u : 0u;
+        C.disabled = q.disabled ? 1u : 0u;
+        C.confirm_ext = q.confirm_ext ? 1u : 0u;
+        ChunkDesc& R = res[(size_t)k];
+        R = C;
+        R.state = (uint32_t)q.state;
+        R.err = (uint32_t)q.err;
+        R.sync = q.sync;
+        R.end = q.end;
+        R.blocks = q.blocks;
+        R.confirmed = q.confirmed;
+    }
+    int g = -1;
+    const int a = recover_member(F, plan.data(), res.data(), confirm_blocks, false_syncs, &g);
+    for (int k = 0; k < n; ++k) {
+        parts[k].lo = plan[(size_t)k].lo;
+        parts[k].disabled = (int32_t)plan[(size_t)k].disabled;
+        parts[k].confirm_ext = (int32_t)plan[(size_t)k].confirm_ext;
+    }
+    *grow = g;
+    return a;
+}
+
 int pgz_wave_chunk_bytes(pgz_ctx* ctx, const pgz_job* jobs, int n_jobs, int warps_per_block, double waves,
                          uint64_t* chunk_bytes, int* resident_warps) {
     if (!ctx || !jobs || n_jobs <= 0 || !chunk_bytes || !(waves > 0.0) ||

@@ -64,6 +64,18 @@ class pgz_job(ctypes.Structure):
                 ("status", ctypes.c_int)]
 
 
+class pgz_part_state(ctypes.Structure):
+    _fields_ = [("lo", U64), ("given", ctypes.c_int32), ("probe", ctypes.c_int32), ("disabled", ctypes.c_int32),
+                ("confirm_ext", ctypes.c_int32), ("state", ctypes.c_int32), ("err", ctypes.c_int32),
+                ("sync", U64), ("end", U64), ("blocks", ctypes.c_uint32), ("confirmed", ctypes.c_uint32)]
+
+
+PGZ_PART_FOUND, PGZ_PART_EMPTY, PGZ_PART_DONE, PGZ_PART_ERROR = 1, 2, 3, 4
+(PGZ_PART_OK, PGZ_PART_DATA, PGZ_PART_TRUNC, PGZ_PART_DIST, PGZ_PART_OVERFLOW, PGZ_PART_CHAIN, PGZ_PART_CONFIRM,
+ PGZ_PART_TRAIL) = range(8)
+PGZ_RECOVER_STOP, PGZ_RECOVER_RERUN, PGZ_RECOVER_GROW = 0, 1, 2
+
+
 class PgzError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -112,6 +124,8 @@ def _load():
         "pgz_server_destroy": (None, [VP]),
         "pgz_extract_sequences": (ctypes.c_int, [VP, VP, U64, ctypes.c_uint32, VP, U64, P(U64), P(U64)]),
         "pgz_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "pgz_recover_step": (ctypes.c_int, [ctypes.c_int, P(pgz_part_state), U64, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, P(U64), P(ctypes.c_int)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -136,7 +150,8 @@ EXPORTED = ["pgz_config_init", "pgz_create", "pgz_destroy", "pgz_decompress", "p
             "pgz_inspect_symbols", "pgz_inspect_window", "pgz_kernel_launches", "pgz_strerror",
             "pgz_decompress_noalloc", "pgz_autotune", "pgz_server_create", "pgz_server_add_file",
             "pgz_server_submit", "pgz_server_poll", "pgz_server_drain", "pgz_server_pending", "pgz_server_destroy",
-            "pgz_extract_sequences", "pgz_decompress_stream", "pgz_set_tuning", "pgz_wave_chunk_bytes"]
+            "pgz_extract_sequences", "pgz_decompress_stream", "pgz_set_tuning", "pgz_wave_chunk_bytes",
+            "pgz_recover_step"]
 
 
 def pgz_strerror(status: int) -> str:
@@ -414,6 +429,26 @@ def pgz_inspect_window(ctx: int, part: int) -> np.ndarray:
 
 def pgz_kernel_launches(ctx: int) -> int:
     return int(lib().pgz_kernel_launches(ctx))
+
+
+_PART_FIELDS = [f for f, _ in pgz_part_state._fields_]
+
+
+def pgz_recover_step(parts, s0_bit: int, mode: int = 0, last_seg: int = 1, confirm_blocks: int = 5):
+    """parts: list of dicts with the pgz_part_state fields (missing ones 0; sync defaults to none).  Returns
+    (action, parts after the step as dicts, false starts counted, part to grow or -1)."""
+    arr = (pgz_part_state * len(parts))()
+    for k, d in enumerate(parts):
+        arr[k].sync = (1 << 64) - 1
+        for f, v in d.items():
+            if f not in _PART_FIELDS:
+                raise KeyError(f)
+            setattr(arr[k], f, v)
+    fs = U64(0)
+    g = ctypes.c_int(-1)
+    a = lib().pgz_recover_step(len(parts), arr, s0_bit, mode, last_seg, confirm_blocks, ctypes.byref(fs),
+                               ctypes.byref(g))
+    return a, [{f: getattr(arr[k], f) for f in _PART_FIELDS} for k in range(len(parts))], fs.value, g.value
 
 
 def pgz_decompress_noalloc(gz_ptr: int, gz_len: int, out_ptr: int, out_cap: int, stream: int | None = None):
