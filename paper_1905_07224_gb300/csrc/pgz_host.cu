@@ -1654,13 +1654,17 @@ int pgz_inspect_window(pgz_ctx* ctx, int part, uint8_t* host_dst) {
 uint64_t pgz_kernel_launches(const pgz_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 // the header's part states, error codes and actions are the library's own
-static_assert(PGZ_PART_FOUND == CS_FOUND && PGZ_PART_EMPTY == CS_EMPTY && PGZ_PART_DONE == CS_DONE &&
-                  PGZ_PART_ERROR == CS_ERROR, "part states");
-static_assert(PGZ_PART_OK == CE_OK && PGZ_PART_DATA == CE_DATA && PGZ_PART_TRUNC == CE_TRUNC &&
-                  PGZ_PART_DIST == CE_DIST && PGZ_PART_OVERFLOW == CE_OVERFLOW && PGZ_PART_CHAIN == CE_CHAIN &&
-                  PGZ_PART_CONFIRM == CE_CONFIRM && PGZ_PART_TRAIL == CE_TRAIL, "part errors");
-static_assert(PGZ_RECOVER_STOP == kRecoverStop && PGZ_RECOVER_RERUN == kRecoverRerun &&
-                  PGZ_RECOVER_GROW == kRecoverGrow, "recovery actions");
+static_assert((int)PGZ_PART_FOUND == (int)CS_FOUND && (int)PGZ_PART_EMPTY == (int)CS_EMPTY &&
+                  (int)PGZ_PART_DONE == (int)CS_DONE && (int)PGZ_PART_ERROR == (int)CS_ERROR,
+              "part states");
+static_assert((int)PGZ_PART_OK == (int)CE_OK && (int)PGZ_PART_DATA == (int)CE_DATA &&
+                  (int)PGZ_PART_TRUNC == (int)CE_TRUNC && (int)PGZ_PART_DIST == (int)CE_DIST &&
+                  (int)PGZ_PART_OVERFLOW == (int)CE_OVERFLOW && (int)PGZ_PART_CHAIN == (int)CE_CHAIN &&
+                  (int)PGZ_PART_CONFIRM == (int)CE_CONFIRM && (int)PGZ_PART_TRAIL == (int)CE_TRAIL,
+              "part errors");
+static_assert((int)PGZ_RECOVER_STOP == kRecoverStop && (int)PGZ_RECOVER_RERUN == kRecoverRerun &&
+                  (int)PGZ_RECOVER_GROW == kRecoverGrow,
+              "recovery actions");
 
 int pgz_recover_step(int n, pgz_part_state* parts, uint64_t s0_bit, int mode, int last_seg, int confirm_blocks,
                      uint64_t* false_syncs, int* grow) {
